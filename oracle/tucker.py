@@ -1,0 +1,221 @@
+"""Oracle (FP64, numpy) of the fixed-rank Tucker algorithms of the paper.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Conventions (the paper is silent on them; the library uses the same ones):
+* Tensors are numpy arrays indexed (i_1, ..., i_d), 0-based.  The mode-k
+  unfolding X_(k) is n_k x prod_{m != k} n_m with the remaining indices
+  ordered lowest mode fastest (Kolda / Tensor Toolbox order, Section 2
+  gives only its size).
+* svd_econ returns left singular vectors sorted by descending singular
+  value, each column's sign fixed so that its entry of largest magnitude is
+  positive (lowest row index on ties).
+* l_k = min(r_k + s_k, n_k, columns of the current unfolding).
+* Shift rule of Algorithms 2/3: if Sigma(l,l) > alpha_{t-1} then
+  alpha_t = (Sigma(l,l) + alpha_{t-1}) / 2, else alpha_t = alpha_{t-1}; the
+  subtracted shift in the product is alpha_{t-1} (Algorithm 3 prints it
+  without index).
+"""
+import numpy as np
+
+from .omega import omega_rows
+
+SHIFT_PAPER = "paper"   # adaptive midpoint shift, Algorithms 2 and 3
+SHIFT_NONE = "none"     # alpha = 0 throughout: Algorithm A.1
+
+
+def unfold(X, k):
+    """Mode-k unfolding X_(k) (Section 2), Kolda column order."""
+    return np.reshape(np.moveaxis(X, k, 0), (X.shape[k], -1), order="F")
+
+
+def fold(M, k, shape):
+    """Inverse of ``unfold`` for a tensor of the given shape."""
+    rest = [shape[m] for m in range(len(shape)) if m != k]
+    return np.moveaxis(np.reshape(M, [shape[k]] + rest, order="F"), 0, k)
+
+
+def mode_product(X, B, k):
+    """X x_k B (Section 2): c_{..j..} = sum_{i_k} x_{..i_k..} b_{j i_k}."""
+    shape = list(X.shape)
+    shape[k] = B.shape[0]
+    return fold(B @ unfold(X, k), k, shape)
+
+
+def fix_signs(Q):
+    """Flip columns so the entry of largest |value| is positive."""
+    Q = np.array(Q, dtype=np.float64, copy=True)
+    if Q.size == 0:
+        return Q
+    idx = np.argmax(np.abs(Q), axis=0)     # first occurrence on ties
+    sgn = np.sign(Q[idx, np.arange(Q.shape[1])])
+    sgn[sgn == 0] = 1.0
+    return Q * sgn
+
+
+def svd_econ(Y):
+    """[Q, Sigma, ~] = svd(Y, 'econ') (LAPACK), with the sign convention."""
+    U, S, _ = np.linalg.svd(np.asarray(Y, dtype=np.float64), full_matrices=False)
+    return fix_signs(U), S
+
+
+def clamp_l(r_k, s_k, n_k, ncols):
+    return int(min(r_k + s_k, n_k, ncols))
+
+
+def omega(k, ncols, l, seed, tag):
+    """Omega_k (ncols x l) promoted to FP64."""
+    return omega_rows(k, 0, ncols, l, seed=seed, tag=tag).astype(np.float64)
+
+
+def sketch(X, k, l, seed=0, tag=0):
+    """Y = X_(k) Omega_k (Algorithm 2/3, first svd argument)."""
+    Xk = unfold(np.asarray(X, dtype=np.float64), k)
+    return Xk @ omega(k, Xk.shape[1], l, seed, tag)
+
+
+def shift_update(sigma_l, alpha_prev, rule=SHIFT_PAPER):
+    """alpha_t from Sigma(l,l) and alpha_{t-1} (Algorithms 2/3)."""
+    if rule == SHIFT_NONE:
+        return 0.0
+    if sigma_l > alpha_prev:
+        return 0.5 * (sigma_l + alpha_prev)
+    return alpha_prev
+
+
+def shifted_power(X, k, Q, alpha, q, rule=SHIFT_PAPER, X_for_step=None):
+    """q steps of the inner loop of Algorithm 2/3 on X_(k).
+
+    Step t: [Q, Sigma] = svd(X_(k) (X_(k)^T Q) - alpha_{t-1} Q), then the
+    shift update.  ``X_for_step(t)`` may supply a different tensor for step
+    t (the BF16 precision form); default X for all steps.
+    Returns (Q, Sigma, alpha, alpha_hist, sigma_l_hist).
+    """
+    S = None
+    a_hist, s_hist = [], []
+    for t in range(1, q + 1):
+        Xt = X if X_for_step is None else X_for_step(t)
+        Xk = unfold(np.asarray(Xt, dtype=np.float64), k)
+        a_used = 0.0 if rule == SHIFT_NONE else alpha
+        Y = Xk @ (Xk.T @ Q) - a_used * Q
+        Q, S = svd_econ(Y)
+        s_l = S[-1]
+        alpha = shift_update(s_l, alpha, rule)
+        a_hist.append(alpha)
+        s_hist.append(s_l)
+    return Q, S, alpha, a_hist, s_hist
+
+
+def _mode_factor(X, k, r_k, s_k, q, seed, tag, rule, X_for_step=None):
+    """Steps of Algorithms 2/3 for one mode: sketch, q shifted powers, U_k."""
+    Xk_cols = int(np.prod([X.shape[m] for m in range(X.ndim) if m != k]))
+    l = clamp_l(r_k, s_k, X.shape[k], Xk_cols)
+    Y = sketch(X, k, l, seed, tag)
+    Q, S = svd_econ(Y)
+    Q, S2, alpha, a_hist, s_hist = shifted_power(X, k, Q, 0.0, q, rule, X_for_step)
+    if S2 is not None:
+        S = S2
+    return Q[:, :r_k], dict(l=l, alpha=a_hist, sigma_l=s_hist, sigma=S)
+
+
+def rthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER):
+    """Algorithm 2: shifted randomized T-HOSVD.  Returns (G, [U_k], stats)."""
+    A = np.asarray(A, dtype=np.float64)
+    d = A.ndim
+    s = [s] * d if np.isscalar(s) else list(s)
+    Us, stats = [], []
+    G = A
+    for k in range(d):
+        U, st = _mode_factor(A, k, r[k], s[k], q, seed, tag, rule)
+        Us.append(U)
+        stats.append(st)
+        G = mode_product(G, U.T, k)
+    return G, Us, stats
+
+
+def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power=False):
+    """Algorithm 3: shifted randomized ST-HOSVD.  Returns (G, [U_k], stats).
+
+    ``order`` is a permutation of the modes (Section 2: any processing order).
+    ``bf16_power``: the precision form -- power steps 1..q-1 read the
+    current tensor rounded to bfloat16; the sketch and step q read it as
+    given; all arithmetic stays FP64.
+    """
+    G = np.asarray(A, dtype=np.float64)
+    d = G.ndim
+    s = [s] * d if np.isscalar(s) else list(s)
+    order = list(range(d)) if order is None else list(order)
+    Us = [None] * d
+    stats = [None] * d
+    for k in order:
+        X_for_step = None
+        if bf16_power:
+            Gb = round_bf16(G)
+            X_for_step = (lambda t, Gb=Gb, Gf=G: Gb if t < q else Gf)
+        U, st = _mode_factor(G, k, r[k], s[k], q, seed, tag, rule, X_for_step)
+        Us[k] = U
+        stats[k] = st
+        G = mode_product(G, U.T, k)
+    return G, Us, stats
+
+
+def hosvd(A, r, sequential):
+    """Algorithm 1: deterministic T-HOSVD (sequential=False) or ST-HOSVD."""
+    A = np.asarray(A, dtype=np.float64)
+    G = A
+    Us = []
+    for k in range(A.ndim):
+        X = G if sequential else A
+        Q, _ = svd_econ(unfold(X, k))
+        U = Q[:, :r[k]]
+        Us.append(U)
+        G = mode_product(G, U.T, k)
+    return G, Us
+
+
+def reconstruct(G, Us):
+    """A_hat = G x_1 U_1 x_2 U_2 ... x_d U_d."""
+    X = np.asarray(G, dtype=np.float64)
+    for k, U in enumerate(Us):
+        X = mode_product(X, U, k)
+    return X
+
+
+def rel_error(A, G, Us):
+    """RE = ||A - A_hat|| / ||A|| (Section 5, definition of RE)."""
+    A = np.asarray(A, dtype=np.float64)
+    return float(np.linalg.norm((A - reconstruct(G, Us)).ravel()) / np.linalg.norm(A.ravel()))
+
+
+def round_bf16(X):
+    """Round to bfloat16 (round to nearest, ties to even) and back to FP64.
+
+    Applied to the FP32 value of each entry (the library keeps FP32 data and
+    a bfloat16 shadow of it).
+    """
+    x = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    b = x.view(np.uint32).astype(np.uint64)
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    rounded = ((b + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (rounded & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    return out.astype(np.float64).reshape(np.shape(X))
+
+
+def principal_sines(U, V):
+    """Sines of the principal angles between range(U) and range(V)."""
+    Qu, _ = np.linalg.qr(np.asarray(U, dtype=np.float64))
+    Qv, _ = np.linalg.qr(np.asarray(V, dtype=np.float64))
+    # singular values of the residual (I - Qv Qv^T) Qu are the sines; this
+    # avoids the cancellation of sqrt(1 - cos^2) for small angles
+    s = np.linalg.svd(Qu - Qv @ (Qv.T @ Qu), compute_uv=False)
+    return np.sort(np.clip(s, 0.0, 1.0))
+
+
+def separated_block(sigma, r, gap=1e-5):
+    """Largest j <= r with (sigma_j^2 - sigma_{j+1}^2)/sigma_1^2 >= gap."""
+    sig = np.asarray(sigma, dtype=np.float64)
+    best = 0
+    for j in range(1, min(r, len(sig) - 1) + 1):
+        if (sig[j - 1] ** 2 - sig[j] ** 2) / sig[0] ** 2 >= gap:
+            best = j
+    return best

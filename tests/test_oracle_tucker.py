@@ -1,0 +1,234 @@
+"""Pins of the FP64 oracle of Algorithms 1, 2, 3 and A.1 (CPU only).
+
+Each test checks the oracle against something other than itself: a
+brute-force loop of a Section 2 definition, LAPACK through another driver,
+torch's bfloat16 rounding, closed forms, identities of the paper, the
+printed values of Table 5.3, or Algorithm 1 (dense SVDs) on tiny tensors.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tucker as T
+from paper_2506_04840_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _brute_unfold(X, k):
+    shape = X.shape
+    rest = [m for m in range(X.ndim) if m != k]
+    ncol = int(np.prod([shape[m] for m in rest]))
+    M = np.zeros((shape[k], ncol))
+    for idx in itertools.product(*[range(s) for s in shape]):
+        j, stride = 0, 1
+        for m in rest:                   # lowest remaining mode fastest
+            j += idx[m] * stride
+            stride *= shape[m]
+        M[idx[k], j] = X[idx]
+    return M
+
+
+def test_unfold_matches_definition():
+    X = np.random.default_rng(0).standard_normal((3, 4, 2, 5))
+    for k in range(4):
+        assert np.array_equal(T.unfold(X, k), _brute_unfold(X, k))
+        assert np.array_equal(T.fold(T.unfold(X, k), k, X.shape), X)
+
+
+def test_mode_product_matches_definition():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((3, 4, 5))
+    for k in range(3):
+        B = rng.standard_normal((2, X.shape[k]))
+        C = T.mode_product(X, B, k)
+        ref = np.zeros(C.shape)
+        for idx in itertools.product(*[range(s) for s in C.shape]):
+            for i in range(X.shape[k]):
+                src = list(idx)
+                src[k] = i
+                ref[idx] += X[tuple(src)] * B[idx[k], i]
+        assert np.allclose(C, ref, rtol=0, atol=1e-13)
+
+
+def test_svd_econ_properties_and_lapack_gesvd():
+    sla = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(2)
+    Y = rng.standard_normal((50, 7)) @ np.diag(10.0 ** -np.arange(7))
+    Q, S = T.svd_econ(Y)
+    assert np.all(np.diff(S) <= 0)
+    assert np.abs(Q.T @ Q - np.eye(7)).max() < 1e-14
+    # Y = Q S V^T reconstructs with V from the projection
+    V = (Q.T @ Y).T / S
+    assert np.abs(Q @ np.diag(S) @ V.T - Y).max() < 1e-13 * np.abs(Y).max()
+    # third opinion: LAPACK gesvd driver
+    U2, S2, _ = sla.svd(Y, full_matrices=False, lapack_driver="gesvd")
+    assert np.allclose(S, S2, rtol=1e-12, atol=0)
+    # same columns up to sign, and the sign convention holds
+    assert np.allclose(np.abs(Q), np.abs(U2), atol=1e-9)
+    for c in range(7):
+        i = np.argmax(np.abs(Q[:, c]))
+        assert Q[i, c] > 0
+
+
+def test_round_bf16_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(3).standard_normal(100000).astype(np.float32) * 37.0
+    x[:4] = [0.0, -0.0, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-8]      # ties to even
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(T.round_bf16(x), ref)
+
+
+def test_principal_sines_match_scipy():
+    sla = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(4)
+    U = rng.standard_normal((30, 4))
+    V = U + 1e-3 * rng.standard_normal((30, 4))
+    ref = np.sort(np.sin(sla.subspace_angles(U, V)))
+    assert np.allclose(np.sort(T.principal_sines(U, V)), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("alg", ["T", "ST"])
+def test_exact_recovery_of_exact_low_rank(alg):
+    A = I.tucker_plus_noise([24, 20, 18], [5, 4, 3], seed=5, noise=0.0, dtype=np.float64)
+    f = T.rthosvd if alg == "T" else T.rsthosvd
+    G, Us, _ = f(A, [5, 4, 3], 5, 1, seed=0)
+    assert T.rel_error(A, G, Us) < 1e-13
+    for U in Us:
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13
+    # factors span the exact column spaces of the unfoldings
+    for k, U in enumerate(Us):
+        Qk, _ = np.linalg.qr(T.unfold(A, k))
+        Uk_true = np.linalg.svd(T.unfold(A, k), full_matrices=False)[0][:, :U.shape[1]]
+        assert T.principal_sines(U, Uk_true).max() < 1e-10
+        del Qk
+
+
+def test_error_identity_and_st_telescoping():
+    A = I.tucker_plus_noise([16, 14, 12, 10], [4, 3, 3, 2], seed=6, noise=0.3, dtype=np.float64)
+    r = [4, 3, 3, 2]
+    for f in (T.rthosvd, T.rsthosvd):
+        G, Us, _ = f(A, r, 3, 2)
+        err2 = (T.rel_error(A, G, Us) * np.linalg.norm(A)) ** 2
+        assert abs(err2 - (np.sum(A**2) - np.sum(G**2))) < 1e-10 * np.sum(A**2)
+    # ST-HOSVD split (the sequential bound of Section 3 holds with equality)
+    G, Us, _ = T.rsthosvd(A, r, 3, 2)
+    X = A
+    tel = 0.0
+    for k in range(4):
+        Xn = T.mode_product(X, Us[k].T, k)
+        tel += np.sum(X**2) - np.sum(Xn**2)
+        X = Xn
+    err2 = (T.rel_error(A, G, Us) * np.linalg.norm(A)) ** 2
+    assert abs(err2 - tel) < 1e-10 * np.sum(A**2)
+
+
+def test_theorem_2_1_bound_for_algorithm_1():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((9, 8, 7)) + I.tucker_plus_noise([9, 8, 7], [3, 3, 3], 9, noise=0,
+                                                             dtype=np.float64) * 20
+    r = [3, 3, 2]
+    bound = sum(np.sum(np.linalg.svd(T.unfold(A, k), compute_uv=False)[r[k]:] ** 2)
+                for k in range(3))
+    for seq in (False, True):
+        G, Us = T.hosvd(A, r, sequential=seq)
+        err2 = (T.rel_error(A, G, Us) * np.linalg.norm(A)) ** 2
+        assert err2 <= bound * (1 + 1e-12)
+
+
+def test_q1_shift_is_never_applied_and_alpha0_is_algorithm_a1():
+    A = I.tucker_plus_noise([30, 25, 20], [6, 5, 4], seed=10, noise=1e-2, dtype=np.float64)
+    r = [6, 5, 4]
+    for f in (T.rthosvd, T.rsthosvd):
+        Gp, Up, sp = f(A, r, 4, 1, rule=T.SHIFT_PAPER)
+        Gn, Un, _ = f(A, r, 4, 1, rule=T.SHIFT_NONE)
+        assert np.array_equal(Gp, Gn)
+        for a, b in zip(Up, Un):
+            assert np.array_equal(a, b)
+        assert sp[0]["alpha"][0] > 0          # alpha_1 computed but unused
+    # q >= 2: the shift is applied and differs from Algorithm A.1
+    Gp, Up, _ = T.rsthosvd(A, r, 4, 3, rule=T.SHIFT_PAPER)
+    Gn, Un, _ = T.rsthosvd(A, r, 4, 3, rule=T.SHIFT_NONE)
+    assert not np.array_equal(Up[0], Un[0])
+
+
+def test_shift_invariants_against_dense_spectrum():
+    A = I.tucker_plus_noise([40, 30, 20], [8, 6, 5], seed=12, noise=0.05, dtype=np.float64)
+    r, s, q = [8, 6, 5], 4, 5
+    G, Us, st = T.rthosvd(A, r, s, q)
+    for k in range(3):
+        sig = np.linalg.svd(T.unfold(A, k), compute_uv=False)
+        l = st[k]["l"]
+        a = [0.0] + st[k]["alpha"]
+        assert all(a[t] <= a[t + 1] for t in range(len(a) - 1))
+        assert a[-1] <= sig[l - 1] ** 2 / 2 * (1 + 1e-12)
+
+
+def test_randomized_matches_dense_algorithm_1_with_many_powers():
+    A = I.tucker_plus_noise([12, 11, 10, 9], [3, 3, 2, 2], seed=13, noise=0.02, dtype=np.float64)
+    r = [3, 3, 2, 2]
+    for seq, f in ((False, T.rthosvd), (True, T.rsthosvd)):
+        Gd, Ud = T.hosvd(A, r, sequential=seq)
+        G, Us, _ = f(A, r, 2, 50)
+        for U, V in zip(Us, Ud):
+            assert T.principal_sines(U, V).max() < 1e-10
+        assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gd, Ud)) < 1e-10
+
+
+def _closed_form(v, r):
+    return float(np.sqrt(np.sum(v[r:] ** 2) / np.sum(v ** 2)))
+
+
+def test_table_5_3_printed_values_are_the_closed_form_optimum():
+    g = json.load(open(os.path.join(HERE, "golden", "table5_3_tensor_C.json")))
+    for row in g["rows"]:
+        v = I.superdiagonal_values(g["n"], row["decay"])
+        assert abs(row["re"] / _closed_form(v, row["r"]) - 1.0) < 0.01, row
+
+
+@pytest.mark.parametrize("decay,r", [("slow", 10), ("fast", 10), ("sshape", 32)])
+def test_oracle_reaches_the_tensor_C_optimum(decay, r):
+    n = 60
+    A = I.superdiagonal(n, decay, seed=14)
+    v = I.superdiagonal_values(n, decay)
+    opt = _closed_form(v, r)
+    # singular values of every unfolding are exactly v
+    assert np.allclose(np.linalg.svd(T.unfold(A, 1), compute_uv=False)[:n], v, rtol=1e-9,
+                       atol=1e-14)
+    G, Us, _ = T.rsthosvd(A, [r] * 3, 10, 3)
+    re = T.rel_error(A, G, Us)
+    assert opt * (1 - 1e-9) <= re <= opt * 1.01
+
+
+def test_hilbert_config_stays_near_theorem_2_1_bound():
+    # 60^3 Hilbert-type tensor, r = 10, s = 5, q = 1 (the shape of the FP64 workload, smaller)
+    A = I.hilbert([60, 60, 60])
+    G, Us, _ = T.rthosvd(A, [10, 10, 10], 5, 1)
+    Gd, Ud = T.hosvd(A, [10, 10, 10], sequential=False)
+    bound = np.sqrt(sum(np.sum(np.linalg.svd(T.unfold(A, k), compute_uv=False)[10:] ** 2)
+                        for k in range(3))) / np.linalg.norm(A)
+    re_d = T.rel_error(A, Gd, Ud)
+    assert re_d <= bound
+    assert T.rel_error(A, G, Us) <= 1.05 * re_d
+
+
+def test_bf16_form_is_within_one_percent_on_a_noisy_decaying_tensor():
+    A = I.tucker_plus_noise([64, 60, 56], [10, 10, 10], seed=15, noise=1e-4, decay=0.8,
+                            dtype=np.float32)
+    r = [8, 8, 8]
+    G, Us, _ = T.rsthosvd(A, r, 6, 3)
+    Gb, Ub, _ = T.rsthosvd(A, r, 6, 3, bf16_power=True)
+    re, reb = T.rel_error(A, G, Us), T.rel_error(A, Gb, Ub)
+    assert reb <= 1.01 * re
+
+
+def test_processing_order_is_respected():
+    A = I.tucker_plus_noise([20, 16, 12], [4, 4, 4], seed=16, noise=1e-2, dtype=np.float64)
+    G1, U1, s1 = T.rsthosvd(A, [4, 4, 4], 3, 2, order=[2, 1, 0])
+    # the first processed mode sees the full tensor: its l is not clamped by r
+    assert s1[2]["l"] == 7
+    assert G1.shape == (4, 4, 4)
+    assert T.rel_error(A, G1, U1) < 0.05
