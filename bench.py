@@ -1,0 +1,358 @@
+"""Benchmark of the shifted randomized ST-HOSVD hot path on GB300.
+
+A step is one pass of the whole path over one synthetic tensor: sketch,
+q adaptively shifted power steps, the small SVDs and shift updates, the TTM
+shrink of every mode (randomized ST-HOSVD with adaptive shifts) and the
+relative-error pass.  Default workload: a 400 x 400 x 400 FP32 tensor
+G x_1 U_1 x_2 U_2 x_3 U_3 + E (G 20^3 N(0,1) scaled by 0.8^(i+j+k), Haar U_k,
+E at 1e-4 ||G||/sqrt(N)), Tucker rank (20,20,20), oversampling 10, q = 2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...      # the FP64 CPU oracle, host cores
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica on its own tensor (the method has no cross-tensor
+exchange): weak scaling, max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "shifted-power HBM GB/s (% roofline), tensors/s at stated rel.err; serve p50/p99"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+SMS = 152
+MAX_SM_MHZ = 2070.0
+# FP32 FFMA issue rate: 128 lanes x 2 flop per SM per clock; FP64 nominal 1.25 TFLOP/s.
+FP32_ALU_TFLOPS = SMS * 128 * 2 * MAX_SM_MHZ * 1e6 / 1e12
+FP64_TFLOPS = 1.25
+
+WORKLOADS = {
+    "tucker400_fp32_st": dict(desc="400^3 FP32 Tucker(20^3, decay 0.8) + 1e-4 noise; "
+                                   "randomized ST-HOSVD, adaptive shifts, r=(20,20,20), p=10, q=2",
+                              shape=[400, 400, 400], r=[20, 20, 20], s=10, q=2, st=True,
+                              dtype="f32", prec=0),
+    "invradius1000_fp32_st": dict(desc="1000^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise; randomized "
+                                       "ST-HOSVD, r=(50,50,50), p=10, q=3, plain FP32",
+                                  shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3, st=True,
+                                  dtype="f32", prec=0),
+    "invradius1000_bf16power_st": dict(desc="as invradius1000_fp32_st with power steps 1..q-1 on "
+                                            "a bfloat16 copy (precision form)",
+                                       shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3,
+                                       st=True, dtype="f32", prec=1),
+    "hilbert100_fp64_t": dict(desc="100^3 FP64 Hilbert-type 1/(i+j+k-2); randomized T-HOSVD, "
+                                   "r=(10,10,10), p=5, q=1", shape=[100, 100, 100],
+                              r=[10, 10, 10], s=5, q=1, st=False, dtype="f64", prec=0),
+}
+DEFAULT_WORKLOAD = "tucker400_fp32_st"
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture (see
+# profiles/); None until measured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def make_input(name, rank=0):
+    from paper_2506_04840_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if name.startswith("tucker400"):
+        return I.tucker_plus_noise(w["shape"], w["r"], seed=2 + 1000 * rank, noise=1e-4,
+                                   decay=0.8, dtype=np.float32)
+    if name.startswith("invradius1000"):
+        return I.inverse_radius(1000, seed=3 + 1000 * rank, noise=1e-6)
+    if name.startswith("hilbert100"):
+        return I.hilbert(w["shape"])
+    raise KeyError(name)
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_step(A, w):
+    from oracle import tucker as T
+    f = T.rsthosvd if w["st"] else T.rthosvd
+    G, Us, _ = f(A, w["r"], w["s"], w["q"], bf16_power=bool(w["prec"])) if w["st"] else \
+        f(A, w["r"], w["s"], w["q"])
+    return T.rel_error(A, G, Us)
+
+
+def cpu_baseline(A, w, budget_s=12.0, max_samples=4):
+    """The oracle as it stands on the host cores: whole instances of the workload."""
+    n, t0 = 0, time.perf_counter()
+    re = None
+    while True:
+        re = oracle_step(A, w)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= max_samples:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n / el, "unit": "tensors/s", "cores": cores, "kind": "oracle",
+            "sample": "%d whole instance(s) of the workload (oracle FP64 numpy/LAPACK, %.1f s)"
+                      % (n, el), "rel_err": re}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    A = make_input(args.workload)
+    for _ in range(args.warmup):
+        oracle_step(A, w)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        re = oracle_step(A, w)
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    value = args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": w["desc"], "rel_err": re},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
+                             "unit": "tensors/s",
+                             "sample": "each step one whole instance of the workload"},
+            "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import torch
+    from paper_2506_04840_gb300 import api
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    api.load()
+
+    A = make_input(args.workload, rank)
+    dims = list(A.shape)
+    d = len(dims)
+    r = w["r"]
+    tdt = torch.float64 if w["dtype"] == "f64" else torch.float32
+    ndt = np.float64 if w["dtype"] == "f64" else np.float32
+    Ad = api.to_device(A, ndt)
+    core = torch.empty(int(np.prod(r)), dtype=tdt, device="cuda")
+    U = [torch.empty(dims[k] * r[k], dtype=tdt, device="cuda") for k in range(d)]
+    rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"])
+    nbytes = api.tucker_workspace_size(Ad, dims, r, opts, 1 if w["st"] else 0)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], workspace=ws)
+    fn = api.tucker_rsthosvd if w["st"] else api.tucker_rthosvd
+    stream = torch.cuda.current_stream()
+
+    def step(X):
+        fn(X, dims, r, opts, core, U, stats=False, stream=stream)
+        api.tucker_error(X, dims, core, r, U, rel, stream=stream)
+
+    for _ in range(args.warmup):
+        step(Ad)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region -----------------------------------
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    api.tucker_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(Ad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = api.tucker_profile_read()
+    api.tucker_profile_enable(False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rel_err = float(rel.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API, host buffers -----------------
+    pin = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=ndt).ravel(order="F"))).pin_memory()
+    core_h = torch.empty(core.numel(), dtype=tdt).pin_memory()
+    U_h = [torch.empty(u.numel(), dtype=tdt).pin_memory() for u in U]
+    rel_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = pin.numel() * pin.element_size()
+    d2h = core_h.numel() * core_h.element_size() + sum(u.numel() * u.element_size() for u in U_h) + 8
+    Ae = torch.empty_like(Ad)
+
+    def e2e_step():
+        Ae.copy_(pin, non_blocking=True)
+        step(Ae)
+        core_h.copy_(core, non_blocking=True)
+        for uh, ud in zip(U_h, U):
+            uh.copy_(ud, non_blocking=True)
+        rel_h.copy_(rel, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * args.steps / (ms_e2e / 1e3)
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    pk, pk_src = peaks()
+    kinds = prof["kinds"]
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    kd = kinds[dom]
+    avg_s = kd["ms"] / max(kd["launches"], 1) / 1e3
+    per_launch_bytes = kd["bytes"] / max(kd["launches"], 1)
+    per_launch_flops = kd["flops"] / max(kd["launches"], 1)
+    if dom == "power_fused":
+        bound, unit = "hbm", "GB/s"
+        achieved = per_launch_bytes / avg_s / 1e9
+        peak = float(pk["hbm_gbs"])
+        peak_note = "HBM copy bandwidth (%s)" % pk_src
+    elif w["dtype"] == "f64":
+        bound, unit = "alu", "TFLOP/s"
+        achieved = per_launch_flops / avg_s / 1e12
+        peak = FP64_TFLOPS
+        peak_note = "FP64 nominal 1.25 TFLOP/s (recipe table)"
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = per_launch_flops / avg_s / 1e12
+        peak = FP32_ALU_TFLOPS
+        peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, dom)),
+            "kernel": dom, "launches": kd["launches"], "avg_launch_ms": avg_s * 1e3,
+            "bytes_per_launch": per_launch_bytes, "flops_per_launch": per_launch_flops,
+            "peak_source": peak_note}
+    hbm_frac = {k: (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0)
+                for k, v in kinds.items()}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "gbs": round(hbm_frac[k], 1),
+                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0)}
+               for k, v in kinds.items() if v["launches"]}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": w["dtype"], "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "rel_err": rel_err,
+                       "l2": "input (%d MB) larger than L2 (129 MB)" % (Ad.numel() *
+                                                                       Ad.element_size() >> 20)
+                       if Ad.numel() * Ad.element_size() > 129e6 else "input fits L2"},
+            "roofline": roof, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk, "gpu_launches": prof["kernels"]}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, w)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

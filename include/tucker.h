@@ -1,0 +1,201 @@
+/*
+ * tucker.h -- C ABI of a GB300 (sm_103a) library for the fixed-rank Tucker
+ * approximation with adaptive shifts: shifted randomized T-HOSVD
+ * (Algorithm 2) and shifted randomized ST-HOSVD (Algorithm 3) of
+ * Che, Wei, Wu, Yan (arXiv 2506.04840).
+ *
+ * Problem (Problem 2.1, Section 2.2): given a tensor A of size
+ * n_1 x ... x n_d and a Tucker rank (r_1..r_d) with r_k < n_k, find
+ * orthonormal U_k (n_k x r_k) such that A ~ A x_1 U_1U_1^T ... x_d U_dU_d^T;
+ * the core is G = A x_1 U_1^T ... x_d U_d^T.
+ *
+ * Conventions shared by every entry point
+ *  - Tensors are dense and column-major: entry (i_1..i_d), 0-based, sits at
+ *    i_1 + n_1*(i_2 + n_2*(i_3 + ...)).  The mode-k unfolding A_(k)
+ *    (n_k x prod_{m!=k} n_m, Section 2) orders its columns lowest remaining
+ *    mode fastest; it is never materialised.
+ *  - Matrices (Y, Q, U_k) are column-major with leading dimension = rows.
+ *  - Every data pointer is a DEVICE pointer owned by the caller unless a
+ *    comment says "host".  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it unless they return host data
+ *    (tk_stats, tucker_server_poll), which synchronise the stream.
+ *  - Errors are returned as tk_status; nothing crosses the ABI as an
+ *    exception and no kernel traps.  Argument errors are detected before any
+ *    launch (TK_EINVAL).  Problems found on the device (non-finite values,
+ *    a bounded wait that ran out) are recorded in a device status word and
+ *    reported by the next call that synchronises.
+ *  - Omega_k (Algorithms 2/3, "draw a standard Gaussian matrix") is never
+ *    stored: entry (j, c) is regenerated from Philox4x32-10 with key =
+ *    (seed mod 2^32, seed >> 32) and counter (j mod 2^32, j >> 32, c >> 2,
+ *    (k & 0xff) | (tag << 8)), then Box-Muller with the library's own FP32
+ *    log/sin/cos (tucker_debug_omega returns the exact values).
+ *  - svd results are sorted by descending singular value and each column's
+ *    sign is fixed so that its entry of largest magnitude is positive.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TK_MAX_D 8     /* largest supported tensor order d */
+#define TK_MAX_Q 32    /* largest power-iteration count q */
+#define TK_MAX_L 128   /* largest sketch width l_k = r_k + s_k */
+
+typedef enum {
+  TK_OK = 0,
+  TK_EINVAL = 1,       /* invalid argument (checked before any launch) */
+  TK_ENOMEM = 2,       /* device allocation failed */
+  TK_ECUDA = 3,        /* a CUDA runtime call failed */
+  TK_EBREAKDOWN = 4,   /* non-finite value met on the device */
+  TK_ETIMEOUT = 5,     /* a bounded device wait ran out */
+  TK_ENOTIMPL = 6,     /* valid request outside the built kernels' limits */
+  TK_EWORKSPACE = 7    /* caller workspace smaller than tucker_workspace_size */
+} tk_status;
+
+typedef enum { TK_F64 = 0, TK_F32 = 1, TK_BF16 = 2 } tk_dtype;
+
+/* Shift rule of the power loop.
+ * TK_SHIFT_PAPER: alpha_0 = 0; after step t, if Sigma(l,l) > alpha_{t-1} then
+ *   alpha_t = (Sigma(l,l) + alpha_{t-1})/2 else alpha_t = alpha_{t-1}
+ *   (Algorithm 2, Algorithm 3).
+ * TK_SHIFT_NONE: alpha = 0 throughout (Algorithm A.1, the unshifted model). */
+typedef enum { TK_SHIFT_PAPER = 0, TK_SHIFT_NONE = 1 } tk_shift;
+
+/* Precision form.  TK_PREC_PLAIN: every pass reads the tensor in its own
+ * dtype.  TK_PREC_BF16_POWER (FP32 tensors only): power steps 1..q-1 read a
+ * bfloat16 copy of the current tensor (FP32 accumulation on tensor cores);
+ * the sketch, power step q, the TTM shrink and the core read FP32. */
+typedef enum { TK_PREC_PLAIN = 0, TK_PREC_BF16_POWER = 1 } tk_precision;
+
+/* A dense tensor.  data: device pointer, column-major, dtype F64 or F32
+ * (BF16 only where stated). */
+typedef struct {
+  int d;                   /* order, 1 <= d <= TK_MAX_D */
+  int64_t n[TK_MAX_D];     /* sizes n_1..n_d, each >= 1 */
+  tk_dtype dtype;
+  const void* data;
+} tk_tensor;
+
+/* Options of Algorithms 2/3 (inputs of the boxes: s, q; plus the draw). */
+typedef struct {
+  int q;                   /* power parameter q, 0 <= q <= TK_MAX_Q
+                              (q = 0: sketch only) */
+  int s[TK_MAX_D];         /* oversampling s_k; l_k = min(r_k+s_k, n_k, cols) */
+  uint64_t seed;           /* Omega key */
+  uint32_t tag;            /* Omega stream tag, < 2^24 */
+  tk_shift shift;
+  tk_precision prec;
+  int order[TK_MAX_D];     /* ST-HOSVD processing order (0-based modes, a
+                              permutation); order[0] < 0 means 0..d-1 */
+  void* workspace;         /* device workspace or NULL (then the call
+                              allocates and frees it on `stream`) */
+  size_t workspace_bytes;
+} tk_opts;
+
+/* Per-call statistics (HOST memory; filling it synchronises the stream). */
+typedef struct {
+  int d;
+  int q;
+  int l[TK_MAX_D];                      /* clamped sketch widths */
+  int order[TK_MAX_D];                  /* processing order used */
+  double alpha[TK_MAX_D][TK_MAX_Q];     /* alpha_t^(k), t = 1..q */
+  double sigma_l[TK_MAX_D][TK_MAX_Q];   /* Sigma_k(l,l) after step t */
+  double sigma[TK_MAX_D][TK_MAX_L];     /* final Sigma_k (first l entries) */
+} tk_stats;
+
+/* Human-readable name of a status code (static string). */
+const char* tucker_status_string(tk_status s);
+
+/* Bytes of device workspace tucker_rthosvd (st = 0) or tucker_rsthosvd
+ * (st = 1) needs for these arguments; 0 if the arguments are invalid. */
+size_t tucker_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o, int st);
+
+/* Rows [row0, row0+rows) of Omega_k for a sketch of width l (Algorithm 2/3,
+ * "draw a standard Gaussian matrix"), written as a rows x l column-major
+ * FP32 matrix `out` (device).  k: 0-based mode; tag < 2^24. */
+tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed,
+                             uint32_t tag, float* out, void* stream);
+
+/* Sketch Y = A_(k) Omega_k (Algorithm 2: svd argument before the power
+ * loop; Algorithm 3 with the current tensor G).  A: F64, F32 or BF16.
+ * Y: n_k x l FP64 (device), the exact sum of per-block FP32 (F32/BF16) or
+ * FP64 partial products reduced in FP64.  Omega_k is generated in
+ * registers, never stored. */
+tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_t tag,
+                        double* Y, void* stream);
+
+/* q steps of the shifted power loop on A_(k) (Algorithm 2 inner loop):
+ *   [Q, Sigma] = svd(A_(k)(A_(k)^T Q) - alpha_{t-1} Q, 'econ'), shift update.
+ * Q:     in: n_k x l orthonormal (FP64, device); out: left singular vectors.
+ * sigma: out: the l singular values of the last step (FP64, device).
+ * alpha: in: alpha_{t0}; out: alpha after q steps (one FP64, device).
+ * A: F64, F32 or BF16 (BF16: the reduced-precision pass, one fused read of
+ * A per step on tensor cores).  l <= TK_MAX_L. */
+tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift rule,
+                               double* Q, double* sigma, double* alpha, void* stream);
+
+/* Shifted randomized T-HOSVD, Algorithm 2.  r: host array of d ranks,
+ * 1 <= r_k < n_k (Problem 2.1).  core: r_1 x ... x r_d in A's dtype
+ * (device).  U: host array of d device pointers, U[k] n_k x r_k in A's
+ * dtype.  st: optional host stats (NULL = none).  A: F64 or F32. */
+tk_status tucker_rthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                         void* const* U, tk_stats* st, void* stream);
+
+/* Shifted randomized ST-HOSVD, Algorithm 3 (arguments as tucker_rthosvd;
+ * o->order gives the processing order, Section 2.2). */
+tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                          void* const* U, tk_stats* st, void* stream);
+
+/* Relative error RE = ||A - G x_1 U_1 ... x_d U_d|| / ||A|| (Section 5,
+ * definition of RE).  core, U as returned by tucker_r(s)thosvd (A's dtype);
+ * r: host ranks.  rel_err: one FP64 (device).  The reconstruction is never
+ * stored: the last mode product is fused with the squared-difference sum. */
+tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const void* const* U,
+                       double* rel_err, void* stream);
+
+/* ---- instrumentation (no counterpart in the paper; used by the benchmark)
+ * When enabled, every launch of the kernel classes below is bracketed by
+ * CUDA events recorded on the launch stream, together with the algorithmic
+ * bytes and flops of that launch (the data the method must move / the
+ * arithmetic it must do, not the kernel's actual traffic). */
+typedef enum {
+  TK_K_SKETCH = 0,      /* Y = X_(k) Omega_k */
+  TK_K_POWER_W = 1,     /* W = X_(k)^T Q (CUDA-core power step, first half) */
+  TK_K_POWER_Y = 2,     /* Y = X_(k) W (CUDA-core power step, second half) */
+  TK_K_POWER_FUSED = 3, /* Y = X_(k)(X_(k)^T Q) - alpha Q, one fused pass */
+  TK_K_SMALL_SVD = 4,   /* svd of the n_k x l iterate + shift update */
+  TK_K_TTM = 5,         /* G <- G x_k U_k^T */
+  TK_K_ERROR = 6,       /* reconstruction-error passes */
+  TK_K_CONVERT = 7,     /* bf16 shadow, copies, reductions, polish */
+  TK_K_KINDS = 8
+} tk_kernel_kind;
+
+typedef struct {
+  int64_t launches[TK_K_KINDS];   /* launches recorded */
+  double ms[TK_K_KINDS];          /* summed event-timed duration */
+  double bytes[TK_K_KINDS];       /* summed algorithmic bytes */
+  double flops[TK_K_KINDS];       /* summed algorithmic flops */
+  int64_t kernels;                /* all kernels launched since the last reset */
+} tk_profile;
+
+/* on != 0 starts recording (and clears what was recorded); 0 stops. */
+tk_status tucker_profile_enable(int on);
+/* Waits for the recorded events, fills *out (host) and clears the record. */
+tk_status tucker_profile_read(tk_profile* out);
+
+/* Round count FP32 values to bfloat16 (round to nearest, ties to even);
+ * out holds count uint16 bit patterns (device).  The precision form's
+ * shadow copy. */
+tk_status tucker_to_bf16(const float* x, int64_t count, uint16_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_H */

@@ -110,9 +110,20 @@ def _mode_factor(X, k, r_k, s_k, q, seed, tag, rule, X_for_step=None):
     """Steps of Algorithms 2/3 for one mode: sketch, q shifted powers, U_k."""
     Xk_cols = int(np.prod([X.shape[m] for m in range(X.ndim) if m != k]))
     l = clamp_l(r_k, s_k, X.shape[k], Xk_cols)
+    if l < r_k:
+        raise ValueError("mode %d: only %d columns for rank %d" % (k, l, r_k))
     Y = sketch(X, k, l, seed, tag)
     Q, S = svd_econ(Y)
-    Q, S2, alpha, a_hist, s_hist = shifted_power(X, k, Q, 0.0, q, rule, X_for_step)
+    if X_for_step is None or q < 2:
+        Q, S2, alpha, a_hist, s_hist = shifted_power(X, k, Q, 0.0, q, rule)
+    else:
+        # precision form: steps 1..q-1 on the bfloat16 copy; the shift sequence
+        # restarts at alpha = 0 for step q, which reads the FP32 tensor (the
+        # bfloat16 Sigma(l,l) sits on the rounding floor of the copy and would
+        # violate 0 < alpha < sigma_l(A A^T)/2, Section 3.1 item (a))
+        Q, _, _, a1, s1 = shifted_power(X_for_step(1), k, Q, 0.0, q - 1, rule)
+        Q, S2, alpha, a2, s2 = shifted_power(X_for_step(q), k, Q, 0.0, 1, rule)
+        a_hist, s_hist = a1 + a2, s1 + s2
     if S2 is not None:
         S = S2
     return Q[:, :r_k], dict(l=l, alpha=a_hist, sigma_l=s_hist, sigma=S)

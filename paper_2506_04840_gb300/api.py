@@ -1,0 +1,279 @@
+"""Thin Python binding of the C ABI in ``include/tucker.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device buffers are torch CUDA tensors used as plain memory; a
+tensor's data is the column-major (i_1 fastest) flattening of the
+n_1 x ... x n_d array and its sizes are passed explicitly.  Functions carry
+the C names; each raises ``TuckerError`` on a non-OK status.  There is no
+fallback: if ``libtucker.so`` cannot be loaded, ``load`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TK_MAX_D = 8
+TK_MAX_Q = 32
+TK_MAX_L = 128
+
+TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_EBREAKDOWN, TK_ETIMEOUT, TK_ENOTIMPL, TK_EWORKSPACE = range(8)
+TK_F64, TK_F32, TK_BF16 = 0, 1, 2
+TK_SHIFT_PAPER, TK_SHIFT_NONE = 0, 1
+TK_PREC_PLAIN, TK_PREC_BF16_POWER = 0, 1
+
+c_int, c_int64, c_uint64, c_uint32, c_double = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                                 ctypes.c_uint32, ctypes.c_double)
+c_void_p, c_size_t = ctypes.c_void_p, ctypes.c_size_t
+
+
+class tk_tensor(ctypes.Structure):
+    _fields_ = [("d", c_int), ("n", c_int64 * TK_MAX_D), ("dtype", c_int), ("data", c_void_p)]
+
+
+class tk_opts(ctypes.Structure):
+    _fields_ = [("q", c_int), ("s", c_int * TK_MAX_D), ("seed", c_uint64), ("tag", c_uint32),
+                ("shift", c_int), ("prec", c_int), ("order", c_int * TK_MAX_D),
+                ("workspace", c_void_p), ("workspace_bytes", c_size_t)]
+
+
+class tk_stats(ctypes.Structure):
+    _fields_ = [("d", c_int), ("q", c_int), ("l", c_int * TK_MAX_D), ("order", c_int * TK_MAX_D),
+                ("alpha", (c_double * TK_MAX_Q) * TK_MAX_D),
+                ("sigma_l", (c_double * TK_MAX_Q) * TK_MAX_D),
+                ("sigma", (c_double * TK_MAX_L) * TK_MAX_D)]
+
+
+TK_K_NAMES = ["sketch", "power_w", "power_y", "power_fused", "small_svd", "ttm", "error",
+              "convert"]
+
+
+class tk_profile(ctypes.Structure):
+    _fields_ = [("launches", c_int64 * 8), ("ms", c_double * 8), ("bytes", c_double * 8),
+                ("flops", c_double * 8), ("kernels", c_int64)]
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s" % (what, _LIB.tucker_status_string(status).decode()
+                                     if _LIB is not None else status))
+
+
+_LIB = None
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "tucker_status_string": (ctypes.c_char_p, [c_int]),
+    "tucker_workspace_size": (c_size_t, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                         ctypes.POINTER(tk_opts), c_int]),
+    "tucker_debug_omega": (c_int, [c_int, c_int64, c_int64, c_int, c_uint64, c_uint32, c_void_p,
+                                   c_void_p]),
+    "tucker_sketch": (c_int, [ctypes.POINTER(tk_tensor), c_int, c_int, c_uint64, c_uint32,
+                              c_void_p, c_void_p]),
+    "tucker_shifted_power": (c_int, [ctypes.POINTER(tk_tensor), c_int, c_int, c_int, c_int,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tucker_rthosvd": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                               ctypes.POINTER(tk_opts), c_void_p, ctypes.POINTER(c_void_p),
+                               ctypes.POINTER(tk_stats), c_void_p]),
+    "tucker_rsthosvd": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                ctypes.POINTER(tk_opts), c_void_p, ctypes.POINTER(c_void_p),
+                                ctypes.POINTER(tk_stats), c_void_p]),
+    "tucker_error": (c_int, [ctypes.POINTER(tk_tensor), c_void_p, ctypes.POINTER(c_int),
+                             ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
+    "tucker_to_bf16": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+    "tucker_profile_enable": (c_int, [c_int]),
+    "tucker_profile_read": (c_int, [ctypes.POINTER(tk_profile)]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libtucker.so (building it in-tree first if needed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libtucker.so is missing; run paper_2506_04840_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, what):
+    if status != TK_OK:
+        raise TuckerError(status, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return TK_F64
+    if t.dtype == torch.float32:
+        return TK_F32
+    if t.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+        return TK_BF16
+    raise TypeError("unsupported dtype %s" % t.dtype)
+
+
+def tensor_desc(data, dims, dtype=None):
+    """tk_tensor for a device buffer holding the column-major data."""
+    t = tk_tensor()
+    t.d = len(dims)
+    for k, n in enumerate(dims):
+        t.n[k] = int(n)
+    t.dtype = _dtype_code(data) if dtype is None else dtype
+    t.data = int(data.data_ptr())
+    return t
+
+
+def make_opts(d, q, s, seed=0, tag=0, shift=TK_SHIFT_PAPER, prec=TK_PREC_PLAIN, order=None,
+              workspace=None):
+    o = tk_opts()
+    o.q = int(q)
+    svals = [s] * d if np.isscalar(s) else list(s)
+    for k in range(d):
+        o.s[k] = int(svals[k])
+    o.seed = int(seed)
+    o.tag = int(tag)
+    o.shift = int(shift)
+    o.prec = int(prec)
+    if order is None:
+        o.order[0] = -1
+    else:
+        for k, m in enumerate(order):
+            o.order[k] = int(m)
+    if workspace is not None:
+        o.workspace = int(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def _ranks(r):
+    arr = (c_int * len(r))()
+    for k, x in enumerate(r):
+        arr[k] = int(x)
+    return arr
+
+
+def _ptr_array(ts):
+    arr = (c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = int(t.data_ptr())
+    return arr
+
+
+def tucker_status_string(status):
+    return load().tucker_status_string(int(status)).decode()
+
+
+def tucker_workspace_size(A, dims, r, opts, st):
+    desc = tensor_desc(A, dims)
+    return int(load().tucker_workspace_size(ctypes.byref(desc), _ranks(r), ctypes.byref(opts),
+                                            int(st)))
+
+
+def tucker_debug_omega(k, row0, rows, l, seed, tag, out, stream=None):
+    _check(load().tucker_debug_omega(k, row0, rows, l, seed, tag, _ptr(out), _stream(stream)),
+           "tucker_debug_omega")
+
+
+def tucker_sketch(A, dims, k, l, seed, tag, Y, stream=None):
+    desc = tensor_desc(A, dims)
+    _check(load().tucker_sketch(ctypes.byref(desc), k, l, seed, tag, _ptr(Y), _stream(stream)),
+           "tucker_sketch")
+
+
+def tucker_shifted_power(A, dims, k, l, q, rule, Q, sigma, alpha, stream=None):
+    desc = tensor_desc(A, dims)
+    _check(load().tucker_shifted_power(ctypes.byref(desc), k, l, q, rule, _ptr(Q), _ptr(sigma),
+                                       _ptr(alpha), _stream(stream)), "tucker_shifted_power")
+
+
+def _stats_dict(st):
+    d = st.d
+    return dict(l=[st.l[k] for k in range(d)], order=[st.order[k] for k in range(d)],
+                alpha=[[st.alpha[k][t] for t in range(st.q)] for k in range(d)],
+                sigma_l=[[st.sigma_l[k][t] for t in range(st.q)] for k in range(d)],
+                sigma=[[st.sigma[k][i] for i in range(st.l[k])] for k in range(d)])
+
+
+def _hosvd(fn, A, dims, r, opts, core, U, stats, stream):
+    desc = tensor_desc(A, dims)
+    st = tk_stats() if stats else None
+    _check(getattr(load(), fn)(ctypes.byref(desc), _ranks(r), ctypes.byref(opts), _ptr(core),
+                               _ptr_array(U), ctypes.byref(st) if st is not None else None,
+                               _stream(stream)), fn)
+    return _stats_dict(st) if st is not None else None
+
+
+def tucker_rthosvd(A, dims, r, opts, core, U, stats=False, stream=None):
+    return _hosvd("tucker_rthosvd", A, dims, r, opts, core, U, stats, stream)
+
+
+def tucker_rsthosvd(A, dims, r, opts, core, U, stats=False, stream=None):
+    return _hosvd("tucker_rsthosvd", A, dims, r, opts, core, U, stats, stream)
+
+
+def tucker_error(A, dims, core, r, U, rel_err, stream=None):
+    desc = tensor_desc(A, dims)
+    _check(load().tucker_error(ctypes.byref(desc), _ptr(core), _ranks(r), _ptr_array(U),
+                               _ptr(rel_err), _stream(stream)), "tucker_error")
+
+
+def tucker_to_bf16(x, out, stream=None):
+    _check(load().tucker_to_bf16(_ptr(x), int(x.numel()), _ptr(out), _stream(stream)),
+           "tucker_to_bf16")
+
+
+def tucker_profile_enable(on):
+    _check(load().tucker_profile_enable(1 if on else 0), "tucker_profile_enable")
+
+
+def tucker_profile_read():
+    p = tk_profile()
+    _check(load().tucker_profile_read(ctypes.byref(p)), "tucker_profile_read")
+    kinds = {}
+    for i, name in enumerate(TK_K_NAMES):
+        kinds[name] = dict(launches=int(p.launches[i]), ms=float(p.ms[i]),
+                           bytes=float(p.bytes[i]), flops=float(p.flops[i]))
+    return dict(kinds=kinds, kernels=int(p.kernels))
+
+
+# ---- host helpers (layout only) --------------------------------------------
+def to_device(arr, dtype=None, device="cuda"):
+    """Upload a numpy array as its column-major flattening."""
+    import torch
+    a = np.asarray(arr)
+    if dtype is not None:
+        a = a.astype(dtype)
+    flat = np.ascontiguousarray(a.ravel(order="F"))
+    return torch.from_numpy(flat).to(device)
+
+
+def from_device(t, dims):
+    """Download a column-major device buffer as a numpy array of shape dims."""
+    return t.detach().cpu().numpy().reshape(tuple(dims), order="F")

@@ -1,0 +1,416 @@
+// Strided mode-k contractions on CUDA cores (FFMA / DFMA), unfolding-free.
+//
+//  k_xb   : partial products of Y = X_(k) B, B = Omega_k (generated in
+//           registers from Philox, Algorithm 2/3 sketch) or B = W stored in
+//           the (P, l, S) layout (second half of the power step
+//           X_(k)(X_(k)^T Q)).
+//  k_xtb  : out = X x_k B^T, i.e. out[j, c] = sum_i X_(k)[i, j] B[i, c],
+//           written in the (P, m, S) layout.  This is the mode-k product of
+//           Section 2 with B^T, used for W = X_(k)^T Q, for the TTM shrink
+//           G <- G x_k U_k^T of Algorithms 2/3, and (with B = U^T) for the
+//           expansion G x_k U_k of the relative error.
+//  k_xtb_err : the last expansion fused with sum (A - A_hat)^2 and sum A^2
+//           (Section 5, RE), so A_hat is never stored.
+//
+// X(p, i, s) sits at p + P*(i + n*s); column j = p + P*s of X_(k).
+#include <algorithm>
+
+#include "tk_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+constexpr int XB_TJ = 32;   // column chunk of k_xb (FP32 accumulation; FP64 uses 16)
+template <typename TA> struct xb_tj { static constexpr int value = sizeof(TA) == 8 ? 16 : XB_TJ; };
+
+template <typename TX, int LC, int TM, bool OMEGA>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
+     const typename acc_of<TX>::type* __restrict__ W, int l, uint64_t seed, uint32_t tag,
+     int mode, int64_t cols_per_split, typename acc_of<TX>::type* __restrict__ part) {
+  typedef typename acc_of<TX>::type TA;
+  constexpr int TN = LC / 16;
+  constexpr int TI = 16 * TM;
+  constexpr int TJ = xb_tj<TA>::value;
+  __shared__ TA Xs[TJ][TI + 1];
+  __shared__ TA Bs[TJ][LC];
+  __shared__ int64_t offx[TJ];
+  __shared__ int64_t offw[TJ];
+
+  const int tid = threadIdx.x;
+  const int ti = tid & 15, tc = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  const int64_t ncols = P * S;
+  const int64_t jb = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t je = min(ncols, jb + cols_per_split);
+
+  TA acc[TM][TN];
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int q = 0; q < TN; ++q) acc[m][q] = (TA)0;
+
+  for (int64_t j0 = jb; j0 < je; j0 += TJ) {
+    if (tid < TJ) {
+      const int64_t j = j0 + tid;
+      if (j < je) {
+        const int64_t s = j / P, p = j - s * P;
+        offx[tid] = p + P * n * s;
+        offw[tid] = p + P * (int64_t)l * s;
+      } else {
+        offx[tid] = -1;
+        offw[tid] = -1;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < TI * TJ; e += TK_THREADS) {
+      int ii, jj;
+      if (P == 1) { ii = e % TI; jj = e / TI; } else { jj = e % TJ; ii = e / TJ; }
+      const int64_t i = i0 + ii;
+      const int64_t o = offx[jj];
+      TA v = (TA)0;
+      if (o >= 0 && i < n) v = load_as<TA>(X + o + P * i);
+      Xs[jj][ii] = v;
+    }
+    if (OMEGA) {
+      for (int e = tid; e < TJ * (LC / 4); e += TK_THREADS) {
+        const int jj = e % TJ, g = e / TJ;
+        float w4[4] = {0.f, 0.f, 0.f, 0.f};
+        const int64_t j = j0 + jj;
+        if (j < je && 4 * g < l) omega4((uint64_t)j, g, mode, tag, seed, w4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Bs[jj][4 * g + q] = (4 * g + q < l) ? (TA)w4[q] : (TA)0;
+      }
+    } else {
+      for (int e = tid; e < TJ * LC; e += TK_THREADS) {
+        int jj, c;
+        if (P == 1) { c = e % LC; jj = e / LC; } else { jj = e % TJ; c = e / TJ; }
+        const int64_t o = offw[jj];
+        TA v = (TA)0;
+        if (o >= 0 && c < l) v = W[o + P * c];
+        Bs[jj][c] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+      TA a[TM], b[TN];
+#pragma unroll
+      for (int m = 0; m < TM; ++m) a[m] = Xs[jj][ti + 16 * m];
+#pragma unroll
+      for (int q = 0; q < TN; ++q) b[q] = Bs[jj][tc + 16 * q];
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) acc[m][q] = fma(a[m], b[q], acc[m][q]);
+    }
+    __syncthreads();
+  }
+  TA* dst = part + (int64_t)blockIdx.y * n * LC;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int64_t i = i0 + ti + 16 * m;
+    if (i < n) {
+#pragma unroll
+      for (int q = 0; q < TN; ++q) dst[i * LC + tc + 16 * q] = acc[m][q];
+    }
+  }
+}
+
+template <typename TA>
+__global__ void k_reduce(const TA* __restrict__ part, int splits, int64_t n, int l, int lc,
+                         const double* __restrict__ Q, const double* __restrict__ alpha,
+                         double* __restrict__ Y) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * l) return;
+  const int64_t i = idx % n;
+  const int c = (int)(idx / n);
+  double s = 0.0;
+  for (int sp = 0; sp < splits; ++sp) s += (double)part[((int64_t)sp * n + i) * lc + c];
+  if (Q != nullptr) s -= alpha[0] * Q[idx];
+  Y[idx] = s;
+}
+
+// out[j, c] = sum_i X(p, i, s) B(i, c) for a tile of TJ columns and LC
+// outputs.  EPI = 0 stores out in the (P, m, S) layout; EPI = 1 (S == 1)
+// compares with A(p, c) and accumulates the two squared sums.
+template <typename TX, int LC, int EPI>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* __restrict__ B,
+      int64_t b_ri, int64_t b_cm, int m, typename acc_of<TX>::type* __restrict__ out,
+      const typename acc_of<TX>::type* __restrict__ A, double* __restrict__ err_part) {
+  typedef typename acc_of<TX>::type TA;
+  constexpr int TN = LC / 16;
+  constexpr int TMJ = 8;
+  constexpr int TJ = 16 * TMJ;
+  constexpr int TK = sizeof(TA) == 8 ? 8 : 16;
+  __shared__ TA Xs[TK][TJ + 1];
+  __shared__ TA Bs[TK][LC];
+  __shared__ int64_t offx[TJ];
+  __shared__ double red[2][TK_THREADS / 32];
+
+  const int tid = threadIdx.x;
+  // lanes run along the contiguous output dimension when writing
+  const bool cfast = (EPI == 0) && (P == 1);
+  const int tj = cfast ? (tid >> 4) : (tid & 15);
+  const int tc = cfast ? (tid & 15) : (tid >> 4);
+  const int64_t ncols = P * S;
+  const int64_t j0 = (int64_t)blockIdx.x * TJ;
+  const int c0 = blockIdx.y * LC;
+
+  if (tid < TJ) {
+    const int64_t j = j0 + tid;
+    if (j < ncols) {
+      const int64_t s = j / P, p = j - s * P;
+      offx[tid] = p + P * n * s;
+    } else {
+      offx[tid] = -1;
+    }
+  }
+  TA acc[TMJ][TN];
+#pragma unroll
+  for (int a = 0; a < TMJ; ++a)
+#pragma unroll
+    for (int q = 0; q < TN; ++q) acc[a][q] = (TA)0;
+  __syncthreads();
+
+  for (int64_t ib = 0; ib < n; ib += TK) {
+    for (int e = tid; e < TK * TJ; e += TK_THREADS) {
+      int ii, jj;
+      if (P == 1) { ii = e % TK; jj = e / TK; } else { jj = e % TJ; ii = e / TJ; }
+      const int64_t i = ib + ii;
+      const int64_t o = offx[jj];
+      TA v = (TA)0;
+      if (o >= 0 && i < n) v = load_as<TA>(X + o + P * i);
+      Xs[ii][jj] = v;
+    }
+    for (int e = tid; e < TK * LC; e += TK_THREADS) {
+      int ii, c;
+      if (b_cm == 1) { c = e % LC; ii = e / LC; } else { ii = e % TK; c = e / TK; }
+      const int64_t i = ib + ii;
+      TA v = (TA)0;
+      if (i < n && c0 + c < m) v = (TA)B[i * b_ri + (int64_t)(c0 + c) * b_cm];
+      Bs[ii][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < TK; ++ii) {
+      TA a[TMJ], b[TN];
+#pragma unroll
+      for (int q = 0; q < TMJ; ++q) a[q] = Xs[ii][tj + 16 * q];
+#pragma unroll
+      for (int q = 0; q < TN; ++q) b[q] = Bs[ii][tc + 16 * q];
+#pragma unroll
+      for (int x = 0; x < TMJ; ++x)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) acc[x][q] = fma(a[x], b[q], acc[x][q]);
+    }
+    __syncthreads();
+  }
+
+  if (EPI == 0) {
+#pragma unroll
+    for (int x = 0; x < TMJ; ++x) {
+      const int64_t j = j0 + tj + 16 * x;
+      if (j >= ncols) continue;
+      const int64_t s = j / P, p = j - s * P;
+#pragma unroll
+      for (int q = 0; q < TN; ++q) {
+        const int c = c0 + tc + 16 * q;
+        if (c < m) out[p + P * ((int64_t)c + (int64_t)m * s)] = acc[x][q];
+      }
+    }
+  } else {
+    double e2 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < TMJ; ++x) {
+      const int64_t j = j0 + tj + 16 * x;   // S == 1: j = p
+      if (j >= ncols) continue;
+#pragma unroll
+      for (int q = 0; q < TN; ++q) {
+        const int c = c0 + tc + 16 * q;
+        if (c < m) {
+          const TA av = A[j + P * (int64_t)c];
+          const double dv = (double)(av - acc[x][q]);
+          e2 += dv * dv;
+          a2 += (double)av * (double)av;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = e2;
+      red[1][tid >> 5] = a2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double se = 0.0, sa = 0.0;
+      for (int w = 0; w < TK_THREADS / 32; ++w) {
+        se += red[0][w];
+        sa += red[1][w];
+      }
+      const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+      err_part[2 * b] = se;
+      err_part[2 * b + 1] = sa;
+    }
+  }
+}
+
+__global__ void k_error_final(const double* __restrict__ part, int blocks,
+                              double* __restrict__ rel) {
+  __shared__ double se[TK_THREADS], sa[TK_THREADS];
+  double e = 0.0, a = 0.0;
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+    e += part[2 * b];
+    a += part[2 * b + 1];
+  }
+  se[threadIdx.x] = e;
+  sa[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      se[threadIdx.x] += se[threadIdx.x + o];
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rel[0] = sa[0] > 0.0 ? sqrt(se[0] / sa[0]) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+int xb_lc(int l) { return l <= 16 ? 16 : (l <= 32 ? 32 : (l <= 64 ? 64 : 128)); }
+
+static int xb_tm(int lc) { return lc <= 64 ? 8 : 4; }
+
+static int xb_ti(int lc) { return 16 * xb_tm(lc); }
+
+int xb_splits(View v, int l) {
+  const int lc = xb_lc(l);
+  const int64_t itiles = (v.n + xb_ti(lc) - 1) / xb_ti(lc);
+  const int64_t target = 4LL * num_sms();
+  int64_t splits = (target + itiles - 1) / itiles;
+  const int64_t maxs = std::max<int64_t>(1, (v.cols() + XB_TJ - 1) / XB_TJ);
+  splits = std::min(splits, maxs);
+  return (int)std::max<int64_t>(1, splits);
+}
+
+template <typename TX, int LC>
+static cudaError_t xb_dispatch(const void* X, View v, const void* W, int l, uint64_t seed,
+                               uint32_t tag, int mode, void* part, int splits, cudaStream_t st) {
+  typedef typename acc_of<TX>::type TA;
+  constexpr int TM = LC <= 64 ? 8 : 4;
+  const int64_t ti = 16 * TM;
+  const int64_t ncols = v.cols();
+  constexpr int TJ = xb_tj<TA>::value;
+  int64_t cps = (ncols + splits - 1) / splits;
+  cps = (cps + TJ - 1) / TJ * TJ;
+  dim3 grid((unsigned)((v.n + ti - 1) / ti), (unsigned)splits);
+  count_kernels(1);
+  if (W == nullptr)
+    k_xb<TX, LC, TM, true><<<grid, TK_THREADS, 0, st>>>((const TX*)X, v.P, v.n, v.S, nullptr, l,
+                                                       seed, tag, mode, cps, (TA*)part);
+  else
+    k_xb<TX, LC, TM, false><<<grid, TK_THREADS, 0, st>>>((const TX*)X, v.P, v.n, v.S,
+                                                        (const TA*)W, l, seed, tag, mode, cps,
+                                                        (TA*)part);
+  return cudaGetLastError();
+}
+
+template <typename TX>
+static cudaError_t xb_lc_dispatch(const void* X, View v, const void* W, int l, uint64_t seed,
+                                  uint32_t tag, int mode, void* part, int splits,
+                                  cudaStream_t st) {
+  switch (xb_lc(l)) {
+    case 16: return xb_dispatch<TX, 16>(X, v, W, l, seed, tag, mode, part, splits, st);
+    case 32: return xb_dispatch<TX, 32>(X, v, W, l, seed, tag, mode, part, splits, st);
+    case 64: return xb_dispatch<TX, 64>(X, v, W, l, seed, tag, mode, part, splits, st);
+    default: return xb_dispatch<TX, 128>(X, v, W, l, seed, tag, mode, part, splits, st);
+  }
+}
+
+cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
+                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st) {
+  if (v.n <= 0 || v.cols() <= 0 || l <= 0) return cudaSuccess;
+  switch (xt) {
+    case X_F64: return xb_lc_dispatch<double>(X, v, W, l, seed, tag, mode, part, splits, st);
+    case X_F32: return xb_lc_dispatch<float>(X, v, W, l, seed, tag, mode, part, splits, st);
+    default:
+      return xb_lc_dispatch<__nv_bfloat16>(X, v, W, l, seed, tag, mode, part, splits, st);
+  }
+}
+
+cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int l, int lc,
+                          const double* Q, const double* alpha, double* Y, cudaStream_t st) {
+  const int64_t tot = n * l;
+  if (tot <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((tot + 255) / 256);
+  count_kernels(1);
+  if (xt == X_F64)
+    k_reduce<double><<<blocks, 256, 0, st>>>((const double*)part, splits, n, l, lc, Q, alpha, Y);
+  else
+    k_reduce<float><<<blocks, 256, 0, st>>>((const float*)part, splits, n, l, lc, Q, alpha, Y);
+  return cudaGetLastError();
+}
+
+static int xtb_lc(int m) { return m <= 16 ? 16 : (m <= 32 ? 32 : 64); }
+
+template <typename TX, int LC, int EPI>
+static cudaError_t xtb_go(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                          int m, void* out, const void* A, double* err, cudaStream_t st) {
+  typedef typename acc_of<TX>::type TA;
+  dim3 grid((unsigned)((v.cols() + 127) / 128), (unsigned)((m + LC - 1) / LC));
+  count_kernels(1);
+  k_xtb<TX, LC, EPI><<<grid, TK_THREADS, 0, st>>>((const TX*)X, v.P, v.n, v.S, B, b_ri, b_cm, m,
+                                                  (TA*)out, (const TA*)A, err);
+  return cudaGetLastError();
+}
+
+template <typename TX, int EPI>
+static cudaError_t xtb_lc_go(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                             int m, void* out, const void* A, double* err, cudaStream_t st) {
+  switch (xtb_lc(m)) {
+    case 16: return xtb_go<TX, 16, EPI>(X, v, B, b_ri, b_cm, m, out, A, err, st);
+    case 32: return xtb_go<TX, 32, EPI>(X, v, B, b_ri, b_cm, m, out, A, err, st);
+    default: return xtb_go<TX, 64, EPI>(X, v, B, b_ri, b_cm, m, out, A, err, st);
+  }
+}
+
+cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
+                       int64_t b_cm, int m, void* out, cudaStream_t st) {
+  if (v.cols() <= 0 || m <= 0) return cudaSuccess;
+  switch (xt) {
+    case X_F64: return xtb_lc_go<double, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);
+    case X_F32: return xtb_lc_go<float, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);
+    default:
+      return xtb_lc_go<__nv_bfloat16, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);
+  }
+}
+
+int xtb_error_blocks(View v, int m) {
+  const int lc = xtb_lc(m);
+  return (int)(((v.cols() + 127) / 128) * ((m + lc - 1) / lc));
+}
+
+cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
+                             int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
+                             cudaStream_t st) {
+  *blocks = xtb_error_blocks(v, m);
+  if (v.cols() <= 0 || m <= 0) return cudaSuccess;
+  if (xt == X_F64) return xtb_lc_go<double, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
+  return xtb_lc_go<float, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
+}
+
+cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_err,
+                               cudaStream_t st) {
+  count_kernels(1);
+  k_error_final<<<1, TK_THREADS, 0, st>>>(err_part, blocks, rel_err);
+  return cudaGetLastError();
+}
+
+}  // namespace tk

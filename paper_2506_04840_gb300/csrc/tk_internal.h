@@ -1,0 +1,96 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "tucker.h"
+
+namespace tk {
+
+// Mode-k view of a column-major tensor: X(p, i, s) at p + P*(i + n*s), with
+// P = n_1..n_{k-1}, n = n_k, S = n_{k+1}..n_d.  Column j of the unfolding
+// X_(k) is j = p + P*s (Kolda order).
+struct View {
+  int64_t P, n, S;
+  int64_t cols() const { return P * S; }
+};
+
+enum XType { X_F64 = 0, X_F32 = 1, X_BF16 = 2 };
+
+inline size_t xsize(XType t) { return t == X_F64 ? 8 : (t == X_F32 ? 4 : 2); }
+inline size_t asize(XType t) { return t == X_F64 ? 8 : 4; }  // accumulation type
+
+int num_sms();
+
+// ---- instrumentation (tucker_api.cu) --------------------------------------
+// Counts kernel launches always; when profiling is on, brackets the scope
+// with CUDA events on `st` and records the algorithmic bytes and flops.
+void count_kernels(int n);
+struct ProfScope {
+  ProfScope(int kind, double bytes, double flops, cudaStream_t st);
+  ~ProfScope();
+  int idx;
+  cudaStream_t st;
+};
+
+// ---- contraction kernels (k_contract.cu) ---------------------------------
+// Partial products Y_part[split][i][c] of Y = X_(k) B with B = Omega_k
+// (generated) or B = W stored in the (P, l, S) layout.  Returns the number
+// of splits used; part must hold splits*n*lc accumulation-type values.
+int xb_splits(View v, int l);
+int xb_lc(int l);
+cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
+                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st);
+// Y = sum_split part - alpha*Q (Q, alpha may be NULL): n x l FP64.
+cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int l, int lc,
+                          const double* Q, const double* alpha, double* Y, cudaStream_t st);
+// out(P, m, S) = X x_k B^T with B(i, c) at B[i*b_ri + c*b_cm] (FP64):
+// out[j, c] = sum_i X(p, i, s) B(i, c).  Output in the accumulation type of
+// X (or `out_bf16` when non-null: BF16 output is not supported here).
+cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
+                       int64_t b_cm, int m, void* out, cudaStream_t st);
+// Fused last-mode expansion and error sums: for S == 1, a_hat(p, c) =
+// sum_i T(p, i) B(i, c); accumulates (A - a_hat)^2 and A^2 per block into
+// err_part[2*block].  Returns the number of blocks via *blocks.
+cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
+                             int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
+                             cudaStream_t st);
+int xtb_error_blocks(View v, int m);
+cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_err,
+                               cudaStream_t st);
+
+// ---- small dense solver (k_small.cu) -------------------------------------
+// [Q, Sigma] = svd(Y, 'econ') of an n x l FP64 matrix by a two-level
+// Householder TSQR, one-sided Jacobi on the l x l triangle, and the sign
+// convention; optional shift update.  `T` selects the working precision.
+struct SmallPlan {
+  int l, MB, Pb;
+  size_t scratch_bytes;
+};
+SmallPlan small_plan(int64_t n, int l, bool fp64);
+cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,
+                             double* Q, double* sigma, void* scratch, int shift_rule,
+                             bool update_shift, double* alpha, double* alpha_hist,
+                             double* sigl_hist, int* status, cudaStream_t st);
+
+// One FP64 CholeskyQR step on an n x r factor computed in FP32 arithmetic
+// (U <- U R^{-1}, R^T R = U^T U); scratch: polish_scratch(n, r) bytes.
+size_t polish_scratch(int64_t n, int r);
+cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* status,
+                          cudaStream_t st);
+
+// ---- misc (k_misc.cu) -----------------------------------------------------
+cudaError_t launch_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed, uint32_t tag,
+                         float* out, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* x, int64_t count, uint16_t* out, cudaStream_t st);
+// dst (rows x cols, ld_dst) = src (FP64, ld_src) converted to dtype.
+cudaError_t launch_copy_matrix(const double* src, int64_t ld_src, void* dst, int64_t ld_dst,
+                               int64_t rows, int64_t cols, XType dt, cudaStream_t st);
+cudaError_t launch_copy_tensor(const void* src, void* dst, int64_t count, XType dt,
+                               cudaStream_t st);
+cudaError_t launch_to_f64_from_f32(const float* x, int64_t count, double* y, cudaStream_t st);
+cudaError_t launch_check_finite(const double* x, int64_t count, int* status, cudaStream_t st);
+
+}  // namespace tk

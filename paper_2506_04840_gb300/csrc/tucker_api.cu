@@ -1,0 +1,657 @@
+// C ABI and host orchestration of Algorithms 2 (shifted randomized
+// T-HOSVD) and 3 (shifted randomized ST-HOSVD).  Control stays on the host
+// only for launches: the shift alpha, Q, Sigma and Y live on the device and
+// no device-to-host copy happens inside the mode loop.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "tk_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached = n > 0 ? n : 1;
+  }
+  return cached;
+}
+
+// ---------------------------------------------------------------------------
+// Instrumentation: launch counter and optional per-scope CUDA-event timing.
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+  int kind;
+  double bytes, flops;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<int64_t> g_kernels{0};
+
+cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void count_kernels(int n) { g_kernels.fetch_add(n, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int kind, double bytes, double flops, cudaStream_t s) : idx(-1), st(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  ProfRec r{kind, bytes, flops, pool_event(), pool_event()};
+  cudaEventRecord(r.a, st);
+  g_recs.push_back(r);
+  idx = (int)g_recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (idx < (int)g_recs.size()) cudaEventRecord(g_recs[idx].b, st);
+}
+
+static tk_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TK_OK;
+  if (e == cudaErrorMemoryAllocation) return TK_ENOMEM;
+  return TK_ECUDA;
+}
+
+#define TK_TRY(expr)                              \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return from_cuda(e_);  \
+  } while (0)
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator; with base == nullptr it only measures.
+struct Arena {
+  unsigned char* base = nullptr;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    const size_t o = offset(bytes);
+    return base ? base + o : nullptr;
+  }
+  size_t offset(size_t bytes) {
+    off = al(off);
+    const size_t o = off;
+    off += al(bytes);
+    return o;
+  }
+};
+
+static View view_of(const std::vector<int64_t>& dims, int k) {
+  View v;
+  v.P = 1;
+  for (int m = 0; m < k; ++m) v.P *= dims[m];
+  v.n = dims[k];
+  v.S = 1;
+  for (size_t m = k + 1; m < dims.size(); ++m) v.S *= dims[m];
+  return v;
+}
+
+static int64_t prod(const std::vector<int64_t>& d) {
+  int64_t p = 1;
+  for (auto x : d) p *= x;
+  return p;
+}
+
+static bool valid_tensor(const tk_tensor* A, bool allow_bf16) {
+  if (!A || A->d < 1 || A->d > TK_MAX_D || !A->data) return false;
+  if (!(A->dtype == TK_F64 || A->dtype == TK_F32 || (allow_bf16 && A->dtype == TK_BF16)))
+    return false;
+  int64_t tot = 1;
+  for (int k = 0; k < A->d; ++k) {
+    if (A->n[k] < 1) return false;
+    if (tot > INT64_MAX / A->n[k]) return false;
+    tot *= A->n[k];
+  }
+  return true;
+}
+
+static XType xtype(tk_dtype d) { return d == TK_F64 ? X_F64 : (d == TK_F32 ? X_F32 : X_BF16); }
+
+// ---------------------------------------------------------------------------
+// Plan of one tucker_rthosvd / tucker_rsthosvd call.
+// ---------------------------------------------------------------------------
+struct HosvdPlan {
+  int d = 0;
+  bool st = true;
+  XType xt = X_F32;
+  std::vector<int64_t> n;
+  std::vector<int> r, s, order, l;
+  int q = 0;
+  bool bf16 = false;
+  tk_shift rule = TK_SHIFT_PAPER;
+  // sizes (bytes)
+  size_t gbuf = 0, shadow = 0, wbuf = 0, part = 0, ymat = 0, small = 0, qd = 0;
+  std::vector<SmallPlan> sp;
+  std::vector<std::vector<int64_t>> dims_at;  // tensor dims seen by each step
+};
+
+static tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
+                           HosvdPlan& p) {
+  if (!valid_tensor(A, false) || !r || !o) return TK_EINVAL;
+  p.d = A->d;
+  p.st = st;
+  p.xt = xtype(A->dtype);
+  p.n.assign(A->n, A->n + A->d);
+  p.r.assign(r, r + A->d);
+  p.s.assign(o->s, o->s + A->d);
+  p.q = o->q;
+  p.rule = o->shift;
+  p.bf16 = o->prec == TK_PREC_BF16_POWER;
+  if (o->q < 0 || o->q > TK_MAX_Q) return TK_EINVAL;
+  if (o->tag >= (1u << 24)) return TK_EINVAL;
+  if (o->shift != TK_SHIFT_PAPER && o->shift != TK_SHIFT_NONE) return TK_EINVAL;
+  if (o->prec != TK_PREC_PLAIN && o->prec != TK_PREC_BF16_POWER) return TK_EINVAL;
+  if (p.bf16 && A->dtype != TK_F32) return TK_EINVAL;
+  for (int k = 0; k < p.d; ++k) {
+    if (p.r[k] < 1 || p.r[k] >= p.n[k]) return TK_EINVAL;   // Problem 2.1: r_k < n_k
+    if (p.s[k] < 0) return TK_EINVAL;
+  }
+  if (o->order[0] < 0) {
+    p.order.resize(p.d);
+    for (int k = 0; k < p.d; ++k) p.order[k] = k;
+  } else {
+    p.order.assign(o->order, o->order + p.d);
+    std::vector<int> seen(p.d, 0);
+    for (int k = 0; k < p.d; ++k) {
+      if (p.order[k] < 0 || p.order[k] >= p.d || seen[p.order[k]]) return TK_EINVAL;
+      seen[p.order[k]] = 1;
+    }
+    if (!st)
+      for (int k = 0; k < p.d; ++k) p.order[k] = k;   // T-HOSVD: order is immaterial
+  }
+  const size_t es = xsize(p.xt), ta = asize(p.xt);
+  p.l.assign(p.d, 0);
+  p.sp.assign(p.d, SmallPlan{});
+  p.dims_at.assign(p.d, {});
+  std::vector<int64_t> cur = p.n;
+  for (int step = 0; step < p.d; ++step) {
+    const int k = p.order[step];
+    p.dims_at[k] = cur;
+    const View v = view_of(cur, k);
+    const int64_t cols = v.cols();
+    const int64_t lk = std::min<int64_t>({(int64_t)p.r[k] + p.s[k], v.n, cols});
+    if (lk < p.r[k]) return TK_EINVAL;        // U_k = Q(:, 1:r_k) needs l_k >= r_k
+    if (lk > TK_MAX_L) return TK_ENOTIMPL;
+    p.l[k] = (int)lk;
+    p.sp[k] = small_plan(v.n, (int)lk, p.xt == X_F64);
+    if (p.sp[k].Pb <= 0) return TK_ENOTIMPL;
+    p.small = std::max(p.small, p.sp[k].scratch_bytes);
+    if (p.xt != X_F64) p.small = std::max(p.small, polish_scratch(v.n, p.r[k]));
+    const int lc = xb_lc((int)lk);
+    const int splits = xb_splits(v, (int)lk);
+    p.part = std::max(p.part, (size_t)splits * v.n * lc * ta);
+    if (p.q > 0) p.wbuf = std::max(p.wbuf, (size_t)cols * lk * ta);
+    p.ymat = std::max(p.ymat, (size_t)v.n * lk * sizeof(double));
+    if (p.bf16 && p.q >= 2) p.shadow = std::max(p.shadow, (size_t)prod(cur) * 2);
+    if (st) {
+      cur[k] = p.r[k];
+      if (step < p.d - 1) p.gbuf = std::max(p.gbuf, (size_t)prod(cur) * es);
+    }
+  }
+  if (!st) {
+    std::vector<int64_t> c2 = p.n;
+    for (int k = 0; k < p.d - 1; ++k) {
+      c2[k] = p.r[k];
+      p.gbuf = std::max(p.gbuf, (size_t)prod(c2) * es);
+    }
+    for (int k = 0; k < p.d; ++k) p.qd += al((size_t)p.n[k] * p.r[k] * sizeof(double));
+  }
+  return TK_OK;
+}
+
+struct HosvdWs {
+  void* g[2];
+  void* shadow;
+  void* w;
+  void* part;
+  double* Y;
+  double* Q;
+  void* small;
+  double* qd;
+  double* alpha;
+  double* ahist;
+  double* shist;
+  double* sig;
+  int* status;
+};
+
+static size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
+  Arena a;
+  a.base = base;
+  HosvdWs w{};
+  w.g[0] = a.take(p.gbuf);
+  w.g[1] = a.take(p.gbuf);
+  w.shadow = a.take(p.shadow);
+  w.w = a.take(p.wbuf);
+  w.part = a.take(p.part);
+  w.Y = (double*)a.take(p.ymat);
+  w.Q = (double*)a.take(p.ymat);
+  w.small = a.take(p.small);
+  w.qd = (double*)a.take(p.qd);
+  w.alpha = (double*)a.take(sizeof(double));
+  w.ahist = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_Q);
+  w.shist = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_Q);
+  w.sig = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_L);
+  w.status = (int*)a.take(sizeof(int));
+  if (ws) *ws = w;
+  return al(a.off) + 256;
+}
+
+// Sketch, q shifted power steps and the final svd for mode k of X
+// (Algorithm 2/3 steps for one k).  Leaves Q (n x l) and Sigma in ws.
+static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt, View v,
+                             uint64_t seed, uint32_t tag, const HosvdWs& w, cudaStream_t st) {
+  const int l = p.l[k];
+  const int lc = xb_lc(l);
+  const int splits = xb_splits(v, l);
+  const bool fp64 = xt == X_F64;
+  double* sig = w.sig + (size_t)k * TK_MAX_L;
+  const double N = (double)v.P * (double)v.n * (double)v.S;
+  const double nl = (double)v.n * l;
+  const double red_bytes = (double)splits * v.n * lc * asize(xt) + nl * 8.0;
+  const double svd_flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
+  {
+    ProfScope ps(TK_K_SKETCH, N * xsize(xt), 2.0 * N * l, st);
+    TK_TRY(launch_xb(xt, X, v, nullptr, l, seed, tag, k, w.part, splits, st));
+  }
+  {
+    ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
+    TK_TRY(launch_reduce(xt, w.part, splits, v.n, l, lc, nullptr, nullptr, w.Y, st));
+  }
+  TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
+  {
+    ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
+    TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false,
+                            w.alpha, nullptr, nullptr, w.status, st));
+  }
+  if (p.bf16 && p.q >= 2) {
+    ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
+    TK_TRY(launch_to_bf16((const float*)X, v.P * v.n * v.S, (uint16_t*)w.shadow, st));
+  }
+  for (int t = 1; t <= p.q; ++t) {
+    const bool low = p.bf16 && t < p.q;
+    const void* Xp = low ? w.shadow : X;
+    const XType xp = low ? X_BF16 : xt;
+    // precision form: the shift sequence restarts when the step switches
+    // from the bfloat16 copy to the FP32 tensor (the bfloat16 Sigma(l,l)
+    // sits on the copy's rounding floor, far above sigma_l(X X^T)/2)
+    if (p.bf16 && p.q >= 2 && t == p.q) TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
+    {
+      ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
+      TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st));
+    }
+    {
+      ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
+      TK_TRY(launch_xb(xp, Xp, v, w.w, l, seed, tag, k, w.part, splits, st));
+    }
+    {
+      ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
+      TK_TRY(launch_reduce(xp, w.part, splits, v.n, l, lc, w.Q, w.alpha, w.Y, st));
+    }
+    {
+      ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
+      TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, true,
+                              w.alpha, w.ahist + (size_t)k * TK_MAX_Q + (t - 1),
+                              w.shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, st));
+    }
+  }
+  return TK_OK;
+}
+
+// TTM shrink G <- G x_k U_k^T with U_k = Q(:, 1:r_k) (Algorithm 2/3, last
+// step of each k), instrumented.
+static cudaError_t ttm(XType xt, const void* X, View v, const double* U, int r, void* out,
+                       cudaStream_t st) {
+  const double N = (double)v.P * (double)v.n * (double)v.S;
+  ProfScope ps(TK_K_TTM, (N + N / v.n * r) * xsize(xt), 2.0 * N * r, st);
+  return launch_xtb(xt, X, v, U, 1, v.n, r, out, st);
+}
+
+static cudaError_t polish(double* Q, int64_t n, int r, void* scratch, int* status,
+                          cudaStream_t st) {
+  ProfScope ps(TK_K_CONVERT, 2.0 * n * r * 8.0, 2.0 * n * r * r, st);
+  return launch_polish(Q, n, r, scratch, status, st);
+}
+
+static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                           void* const* U, tk_stats* stats, cudaStream_t st, bool sequential) {
+  HosvdPlan p;
+  tk_status s = make_plan(A, r, o, sequential, p);
+  if (s != TK_OK) return s;
+  if (!core || !U) return TK_EINVAL;
+  for (int k = 0; k < p.d; ++k)
+    if (!U[k]) return TK_EINVAL;
+  const size_t need = carve(p, nullptr, nullptr);
+  unsigned char* base = (unsigned char*)o->workspace;
+  bool owned = false;
+  if (base == nullptr) {
+    TK_TRY(cudaMallocAsync((void**)&base, need, st));
+    owned = true;
+  } else if (o->workspace_bytes < need) {
+    return TK_EWORKSPACE;
+  }
+  HosvdWs w;
+  carve(p, (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255), &w);
+  tk_status rs = TK_OK;
+  auto run = [&]() -> tk_status {
+    TK_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    TK_TRY(cudaMemsetAsync(w.ahist, 0, sizeof(double) * TK_MAX_D * TK_MAX_Q, st));
+    TK_TRY(cudaMemsetAsync(w.shist, 0, sizeof(double) * TK_MAX_D * TK_MAX_Q, st));
+    TK_TRY(cudaMemsetAsync(w.sig, 0, sizeof(double) * TK_MAX_D * TK_MAX_L, st));
+    const size_t es = xsize(p.xt);
+    if (p.st) {
+      const void* X = A->data;
+      std::vector<int64_t> cur = p.n;
+      int pp = 0;
+      for (int step = 0; step < p.d; ++step) {
+        const int k = p.order[step];
+        const View v = view_of(cur, k);
+        tk_status e = factor_mode(p, k, X, p.xt, v, o->seed, o->tag, w, st);
+        if (e != TK_OK) return e;
+        if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
+        TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
+        void* out = (step == p.d - 1) ? core : w.g[pp];
+        TK_TRY(ttm(p.xt, X, v, w.Q, p.r[k], out, st));
+        X = out;
+        pp ^= 1;
+        cur[k] = p.r[k];
+      }
+    } else {
+      size_t off = 0;
+      std::vector<double*> qd(p.d);
+      for (int k = 0; k < p.d; ++k) {
+        qd[k] = (double*)((unsigned char*)w.qd + off);
+        off += al((size_t)p.n[k] * p.r[k] * sizeof(double));
+        const View v = view_of(p.n, k);
+        tk_status e = factor_mode(p, k, A->data, p.xt, v, o->seed, o->tag, w, st);
+        if (e != TK_OK) return e;
+        if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
+        TK_TRY(launch_copy_matrix(w.Q, v.n, qd[k], v.n, v.n, p.r[k], X_F64, st));
+        TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
+      }
+      // core G = A x_1 U_1^T ... x_d U_d^T (Algorithm 2, last step of each k)
+      const void* X = A->data;
+      std::vector<int64_t> cur = p.n;
+      for (int k = 0; k < p.d; ++k) {
+        const View v = view_of(cur, k);
+        void* out = (k == p.d - 1) ? core : w.g[k & 1];
+        TK_TRY(ttm(p.xt, X, v, qd[k], p.r[k], out, st));
+        X = out;
+        cur[k] = p.r[k];
+      }
+    }
+    (void)es;
+    if (stats) {
+      std::vector<double> ah(TK_MAX_D * TK_MAX_Q), sh(TK_MAX_D * TK_MAX_Q), sg(TK_MAX_D * TK_MAX_L);
+      int status = 0;
+      TK_TRY(cudaMemcpyAsync(ah.data(), w.ahist, ah.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(sh.data(), w.shist, sh.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(sg.data(), w.sig, sg.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaStreamSynchronize(st));
+      std::memset(stats, 0, sizeof(*stats));
+      stats->d = p.d;
+      stats->q = p.q;
+      for (int k = 0; k < p.d; ++k) {
+        stats->l[k] = p.l[k];
+        stats->order[k] = p.order[k];
+        for (int t = 0; t < TK_MAX_Q; ++t) {
+          stats->alpha[k][t] = ah[k * TK_MAX_Q + t];
+          stats->sigma_l[k][t] = sh[k * TK_MAX_Q + t];
+        }
+        for (int i = 0; i < TK_MAX_L; ++i) stats->sigma[k][i] = sg[k * TK_MAX_L + i];
+      }
+      if (status != 0) return (tk_status)status;
+    }
+    return TK_OK;
+  };
+  rs = run();
+  if (owned) {
+    cudaError_t e = cudaFreeAsync(base, st);
+    if (rs == TK_OK && e != cudaSuccess) rs = from_cuda(e);
+  }
+  return rs;
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+const char* tucker_status_string(tk_status s) {
+  switch (s) {
+    case TK_OK: return "TK_OK";
+    case TK_EINVAL: return "TK_EINVAL: invalid argument";
+    case TK_ENOMEM: return "TK_ENOMEM: device allocation failed";
+    case TK_ECUDA: return "TK_ECUDA: CUDA runtime error";
+    case TK_EBREAKDOWN: return "TK_EBREAKDOWN: non-finite value on the device";
+    case TK_ETIMEOUT: return "TK_ETIMEOUT: bounded device wait ran out";
+    case TK_ENOTIMPL: return "TK_ENOTIMPL: outside the built kernels' limits";
+    case TK_EWORKSPACE: return "TK_EWORKSPACE: workspace too small";
+  }
+  return "unknown tk_status";
+}
+
+size_t tucker_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o, int st) {
+  HosvdPlan p;
+  if (make_plan(A, r, o, st != 0, p) != TK_OK) return 0;
+  return carve(p, nullptr, nullptr);
+}
+
+tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed,
+                             uint32_t tag, float* out, void* stream) {
+  if (k < 0 || k > 255 || row0 < 0 || rows < 0 || l < 0 || tag >= (1u << 24)) return TK_EINVAL;
+  if (rows > 0 && l > 0 && out == nullptr) return TK_EINVAL;
+  TK_TRY(launch_omega(k, row0, rows, l, seed, tag, out, (cudaStream_t)stream));
+  return TK_OK;
+}
+
+tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_t tag, double* Y,
+                        void* stream) {
+  if (!valid_tensor(A, true) || k < 0 || k >= A->d || l < 1 || l > TK_MAX_L || !Y ||
+      tag >= (1u << 24))
+    return TK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> dims(A->n, A->n + A->d);
+  const View v = view_of(dims, k);
+  const XType xt = xtype(A->dtype);
+  const int splits = xb_splits(v, l);
+  const int lc = xb_lc(l);
+  void* part = nullptr;
+  TK_TRY(cudaMallocAsync(&part, (size_t)splits * v.n * lc * asize(xt), st));
+  cudaError_t e = launch_xb(xt, A->data, v, nullptr, l, seed, tag, k, part, splits, st);
+  if (e == cudaSuccess) e = launch_reduce(xt, part, splits, v.n, l, lc, nullptr, nullptr, Y, st);
+  cudaError_t e2 = cudaFreeAsync(part, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(e2);
+}
+
+tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift rule,
+                               double* Q, double* sigma, double* alpha, void* stream) {
+  if (!valid_tensor(A, true) || k < 0 || k >= A->d || l < 1 || l > TK_MAX_L || q < 0 ||
+      q > TK_MAX_Q || !Q || !sigma || !alpha)
+    return TK_EINVAL;
+  if (rule != TK_SHIFT_PAPER && rule != TK_SHIFT_NONE) return TK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> dims(A->n, A->n + A->d);
+  const View v = view_of(dims, k);
+  if (l > v.n || l > v.cols()) return TK_EINVAL;
+  const XType xt = xtype(A->dtype);
+  const bool fp64 = xt == X_F64;
+  const SmallPlan sp = small_plan(v.n, l, fp64);
+  if (sp.Pb <= 0) return TK_ENOTIMPL;
+  const int splits = xb_splits(v, l);
+  const int lc = xb_lc(l);
+  Arena b;
+  const size_t o_w = b.offset((size_t)v.cols() * l * asize(xt));
+  const size_t o_part = b.offset((size_t)splits * v.n * lc * asize(xt));
+  const size_t o_y = b.offset((size_t)v.n * l * sizeof(double));
+  const size_t o_sm = b.offset(sp.scratch_bytes);
+  const size_t o_st = b.offset(sizeof(int));
+  unsigned char* base = nullptr;
+  TK_TRY(cudaMallocAsync((void**)&base, b.off + 256, st));
+  void* wv = base + o_w;
+  void* part = base + o_part;
+  void* Y = base + o_y;
+  void* sm = base + o_sm;
+  void* stt = base + o_st;
+  auto body = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(stt, 0, sizeof(int), st);
+    for (int t = 1; t <= q && e == cudaSuccess; ++t) {
+      e = launch_xtb(xt, A->data, v, Q, 1, v.n, l, wv, st);
+      if (e == cudaSuccess) e = launch_xb(xt, A->data, v, wv, l, 0, 0, k, part, splits, st);
+      if (e == cudaSuccess)
+        e = launch_reduce(xt, part, splits, v.n, l, lc, Q, alpha, (double*)Y, st);
+      if (e == cudaSuccess)
+        e = launch_small_svd(fp64, sp, (const double*)Y, v.n, Q, sigma, sm, (int)rule, true,
+                             alpha, nullptr, nullptr, (int*)stt, st);
+    }
+    return e;
+  };
+  cudaError_t e = body();
+  cudaError_t e2 = cudaFreeAsync(base, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(e2);
+}
+
+tk_status tucker_rthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                         void* const* U, tk_stats* st, void* stream) {
+  return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, false);
+}
+
+tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                          void* const* U, tk_stats* st, void* stream) {
+  return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, true);
+}
+
+tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const void* const* U,
+                       double* rel_err, void* stream) {
+  if (!valid_tensor(A, false) || !core || !r || !U || !rel_err) return TK_EINVAL;
+  const int d = A->d;
+  for (int k = 0; k < d; ++k)
+    if (r[k] < 1 || r[k] > A->n[k] || !U[k]) return TK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const XType xt = xtype(A->dtype);
+  const size_t es = xsize(xt);
+  // expansion chain sizes: after step k the dims are (n_1..n_k, r_{k+1}..r_d)
+  std::vector<int64_t> cur(r, r + d);
+  size_t tbuf = 0;
+  for (int k = 0; k < d - 1; ++k) {
+    cur[k] = A->n[k];
+    tbuf = std::max(tbuf, (size_t)prod(cur) * es);
+  }
+  std::vector<int64_t> last(r, r + d);
+  for (int k = 0; k < d - 1; ++k) last[k] = A->n[k];
+  const View vl = view_of(last, d - 1);
+  const int blocks = xtb_error_blocks(vl, (int)A->n[d - 1]);
+  Arena a;
+  const size_t t0 = a.offset(tbuf);
+  const size_t t1 = a.offset(tbuf);
+  std::vector<size_t> uoff(d);
+  for (int k = 0; k < d; ++k) uoff[k] = a.offset((size_t)A->n[k] * r[k] * sizeof(double));
+  const size_t ep = a.offset((size_t)blocks * 2 * sizeof(double));
+  unsigned char* base = nullptr;
+  TK_TRY(cudaMallocAsync((void**)&base, a.off + 256, st));
+  auto body = [&]() -> cudaError_t {
+    std::vector<double*> Ud(d);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < d && e == cudaSuccess; ++k) {
+      Ud[k] = (double*)(base + uoff[k]);
+      if (xt == X_F64)
+        e = cudaMemcpyAsync(Ud[k], U[k], (size_t)A->n[k] * r[k] * 8, cudaMemcpyDeviceToDevice, st);
+      else
+        e = launch_to_f64_from_f32((const float*)U[k], (int64_t)A->n[k] * r[k], Ud[k], st);
+    }
+    const void* X = core;
+    std::vector<int64_t> dims(r, r + d);
+    void* tb[2] = {base + t0, base + t1};
+    for (int k = 0; k < d - 1 && e == cudaSuccess; ++k) {
+      const View v = view_of(dims, k);
+      // B(i = core index, c = output index) = U_k(c, i)
+      const double cin = (double)v.P * v.n * v.S;
+      ProfScope ps(TK_K_ERROR, (cin + cin / v.n * A->n[k]) * es, 2.0 * cin / v.n * A->n[k] * v.n,
+                   st);
+      e = launch_xtb(xt, X, v, Ud[k], A->n[k], 1, (int)A->n[k], tb[k & 1], st);
+      X = tb[k & 1];
+      dims[k] = A->n[k];
+    }
+    int nb = 0;
+    const double Nf = (double)vl.P * (double)A->n[d - 1];
+    ProfScope ps(TK_K_ERROR, Nf * es + (double)vl.P * vl.n * es, 2.0 * Nf * vl.n, st);
+    if (e == cudaSuccess)
+      e = launch_xtb_error(xt, X, vl, Ud[d - 1], A->n[d - 1], 1, (int)A->n[d - 1], A->data,
+                           (double*)(base + ep), &nb, st);
+    if (e == cudaSuccess) e = launch_error_final((double*)(base + ep), nb, rel_err, st);
+    return e;
+  };
+  cudaError_t e = body();
+  cudaError_t e2 = cudaFreeAsync(base, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(e2);
+}
+
+tk_status tucker_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_recs) {
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  g_prof_on = on != 0;
+  g_kernels.store(0);
+  return TK_OK;
+}
+
+tk_status tucker_profile_read(tk_profile* out) {
+  if (!out) return TK_EINVAL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::memset(out, 0, sizeof(*out));
+  tk_status st = TK_OK;
+  for (auto& r : g_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      st = TK_ECUDA;
+    if (r.kind >= 0 && r.kind < TK_K_KINDS) {
+      out->launches[r.kind] += 1;
+      out->ms[r.kind] += ms;
+      out->bytes[r.kind] += r.bytes;
+      out->flops[r.kind] += r.flops;
+    }
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  out->kernels = g_kernels.exchange(0);
+  return st;
+}
+
+tk_status tucker_to_bf16(const float* x, int64_t count, uint16_t* out, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !out))) return TK_EINVAL;
+  TK_TRY(launch_to_bf16(x, count, out, (cudaStream_t)stream));
+  return TK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated once, used throughout):
+* Omega: bit-exact.
+* FP64 tensors: contraction error <= 1e-12 on the same scale, core <= 1e-12,
+  |RE_gpu - RE_oracle| <= 1e-12, principal-angle sines <= 1e-9.
+* FP32 tensors: error of a single contraction <= 1e-6 relative to
+  || |X_(k)| |B| ||_F (the forward-error scale of a floating-point product),
+  |RE_gpu - RE_oracle| <= 1e-6, sines <= 1e-5 on the well-separated leading
+  block of each factor (gap (s_j^2 - s_{j+1}^2)/s_1^2 >= 1e-5 in the
+  oracle's final Sigma), orthonormality ||U^T U - I||_max <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+from oracle import omega as om
+from oracle import tucker as T
+from paper_2506_04840_gb300 import api
+from paper_2506_04840_gb300 import inputs as I
+
+from gpu_helpers import gpu_error, run_hosvd
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def _sketch_err(got, X, k, l, seed, tag):
+    """||Y_gpu - Y_oracle|| / || |X_(k)| |Omega| ||: the forward-error scale of
+    a floating-point product (stable under cancellation in Y itself)."""
+    Xk = T.unfold(np.asarray(X, dtype=np.float64), k)
+    Om = om.omega_rows(k, 0, Xk.shape[1], l, seed=seed, tag=tag).astype(np.float64)
+    want = Xk @ Om
+    scale = np.linalg.norm(np.abs(Xk) @ np.abs(Om))
+    return np.linalg.norm(got - want) / max(scale, 1e-300)
+
+
+@pytest.mark.parametrize("k,row0,rows,l,seed,tag", [
+    (0, 0, 1000, 60, 0, 0),
+    (1, 12345, 777, 7, 0, 3),
+    (2, (1 << 32) - 300, 600, 13, (1 << 40) + 3, 5),     # row index crosses 2^32
+    (7, 5, 33, 1, 0xFFFFFFFFFFFFFFFF, (1 << 24) - 1),
+    (3, 0, 257, 128, 99, 0),
+])
+def test_omega_is_bit_exact(lib, k, row0, rows, l, seed, tag):
+    out = torch.empty(rows * l, dtype=torch.float32, device="cuda")
+    api.tucker_debug_omega(k, row0, rows, l, seed, tag, out)
+    got = out.cpu().numpy().reshape((rows, l), order="F")
+    want = om.omega_rows(k, row0, rows, l, seed=seed, tag=tag)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+SHAPES = [(37, 29, 23), (9, 11, 7, 13), (130, 3, 70), (1, 40, 33)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sketch_all_modes(lib, shape, dtype):
+    rng = np.random.default_rng(1)
+    A = np.asfortranarray(rng.standard_normal(shape).astype(dtype))
+    Ad = api.to_device(A, dtype)
+    for k in range(len(shape)):
+        cols = int(np.prod(shape)) // shape[k]
+        for l in sorted({1, min(5, cols), min(17, cols)}):
+            Y = torch.empty(shape[k] * l, dtype=torch.float64, device="cuda")
+            api.tucker_sketch(Ad, list(shape), k, l, 0, 2, Y)
+            got = Y.cpu().numpy().reshape((shape[k], l), order="F")
+            tol = 1e-12 if dtype == np.float64 else 1e-6
+            assert _sketch_err(got, A, k, l, 0, 2) <= tol, (k, l)
+
+
+def test_sketch_reads_bfloat16(lib):
+    rng = np.random.default_rng(2)
+    shape = (50, 41, 30)
+    A = np.asfortranarray(rng.standard_normal(shape).astype(np.float32))
+    Ad = api.to_device(A, np.float32)
+    Ab = torch.empty(Ad.numel(), dtype=torch.int16, device="cuda")
+    api.tucker_to_bf16(Ad, Ab)
+    # the shadow is the oracle's round-to-nearest-even bfloat16
+    bits = Ab.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    assert np.array_equal(bits.view(np.float32).astype(np.float64),
+                          T.round_bf16(A).ravel(order="F"))
+    for k in range(3):
+        Y = torch.empty(shape[k] * 9, dtype=torch.float64, device="cuda")
+        api.tucker_sketch(Ab, list(shape), k, 9, 0, 0, Y)
+        got = Y.cpu().numpy().reshape((shape[k], 9), order="F")
+        assert _sketch_err(got, T.round_bf16(A), k, 9, 0, 0) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("rule", [api.TK_SHIFT_PAPER, api.TK_SHIFT_NONE])
+def test_shifted_power_steps(lib, dtype, rule):
+    A = I.tucker_plus_noise([90, 70, 50], [8, 8, 8], seed=3, noise=1e-2, decay=0.9, dtype=dtype)
+    k, l, q = 1, 14, 3
+    orule = T.SHIFT_PAPER if rule == api.TK_SHIFT_PAPER else T.SHIFT_NONE
+    Q0, _ = T.svd_econ(T.sketch(A, k, l))
+    Qw, Sw, aw, _, _ = T.shifted_power(A, k, Q0, 0.0, q, orule)
+    Ad = api.to_device(A, dtype)
+    Qd = api.to_device(Q0, np.float64)
+    sig = torch.zeros(l, dtype=torch.float64, device="cuda")
+    alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+    api.tucker_shifted_power(Ad, list(A.shape), k, l, q, rule, Qd, sig, alpha)
+    Qg = Qd.cpu().numpy().reshape((A.shape[k], l), order="F")
+    Sg = sig.cpu().numpy()
+    tol = 1e-12 if dtype == np.float64 else 1e-6
+    j = T.separated_block(Sw, l)
+    assert j >= 8
+    assert np.max(np.abs(Sg[:j] - Sw[:j]) / Sw[:j]) <= (1e-10 if dtype == np.float64 else 1e-5)
+    assert T.principal_sines(Qg[:, :j], Qw[:, :j]).max() <= (1e-9 if dtype == np.float64 else 1e-5)
+    assert np.abs(Qg.T @ Qg - np.eye(l)).max() <= max(tol, 1e-13)
+    if rule == api.TK_SHIFT_NONE:
+        assert alpha.item() == 0.0
+    else:
+        assert abs(alpha.item() - aw) <= 1e-3 * max(abs(aw), 1e-30) + 1e-6 * Sw[0]
+
+
+def _check_factors(Us_g, Us_w, stats_w, dtype):
+    for k, (Ug, Uw) in enumerate(zip(Us_g, Us_w)):
+        r = Uw.shape[1]
+        orth = np.abs(Ug.T @ Ug - np.eye(r)).max()
+        assert orth <= (1e-13 if dtype == np.float64 else 1e-6), (k, orth)
+        j = T.separated_block(stats_w[k]["sigma"], r)
+        if j > 0:
+            s = T.principal_sines(Ug[:, :j], Uw[:, :j]).max()
+            assert s <= (1e-9 if dtype == np.float64 else 1e-5), (k, j, s)
+
+
+CASES = [
+    # shape, ranks, s, q, seed of the input
+    ((40, 36, 30), (6, 5, 4), 5, 2, 11),
+    ((21, 18, 15, 12), (4, 3, 3, 2), 3, 1, 12),
+    ((64, 20, 131), (10, 7, 12), 10, 3, 13),
+    ((33, 33, 33), (32, 8, 8), 4, 2, 14),      # r = n - 1, l clamped at n
+    ((40, 36, 30), (6, 5, 4), 5, 0, 15),       # q = 0: sketch only
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("st", [True, False])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_hosvd_matches_oracle(lib, case, st, dtype):
+    shape, r, s, q, seed = case
+    A = I.tucker_plus_noise(shape, [min(x + 2, n - 1) for x, n in zip(r, shape)], seed,
+                            noise=1e-3, decay=0.85, dtype=dtype)
+    f = T.rsthosvd if st else T.rthosvd
+    Gw, Uw, sw = f(A, list(r), s, q)
+    G, Us, info = run_hosvd(A, list(r), s, q, st=st)
+    re_w = T.rel_error(A, Gw, Uw)
+    re_g = T.rel_error(A, G, Us)
+    assert abs(re_g - re_w) <= (1e-12 if dtype == np.float64 else 1e-6), (re_g, re_w)
+    assert info["l"] == [x["l"] for x in sw]
+    _check_factors(Us, Uw, sw, dtype)
+    # core is A x_k U_k^T of the returned factors
+    Gchk = A.astype(np.float64)
+    for k in range(A.ndim) if not st else [0, 1, 2, 3][:A.ndim]:
+        Gchk = T.mode_product(Gchk, Us[k].T.astype(np.float64), k)
+    assert _rel(G, Gchk) <= (1e-12 if dtype == np.float64 else 1e-5)
+    # shift history on the well-resolved modes matches the oracle
+    if dtype == np.float64:
+        for k in range(A.ndim):
+            for t in range(q):
+                aw = sw[k]["alpha"][t]
+                assert abs(info["alpha"][k][t] - aw) <= 1e-8 * max(aw, 1e-300) + 1e-14
+
+
+@pytest.mark.parametrize("rule", [api.TK_SHIFT_PAPER, api.TK_SHIFT_NONE])
+def test_shift_rules_and_order(lib, rule):
+    A = I.tucker_plus_noise([48, 40, 32], [6, 6, 6], 21, noise=1e-2, dtype=np.float64)
+    orule = T.SHIFT_PAPER if rule == api.TK_SHIFT_PAPER else T.SHIFT_NONE
+    order = [2, 0, 1]
+    Gw, Uw, sw = T.rsthosvd(A, [5, 5, 5], 4, 3, rule=orule, order=order)
+    G, Us, info = run_hosvd(A, [5, 5, 5], 4, 3, shift=rule, order=order)
+    assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gw, Uw)) <= 1e-12
+    assert info["order"] == order
+    _check_factors(Us, Uw, sw, np.float64)
+
+
+def test_config_hilbert_100_fp64_thosvd(lib):
+    A = I.hilbert([100, 100, 100])
+    Gw, Uw, sw = T.rthosvd(A, [10, 10, 10], 5, 1)
+    G, Us, info = run_hosvd(A, [10, 10, 10], 5, 1, st=False)
+    re_w, re_g = T.rel_error(A, Gw, Uw), T.rel_error(A, G, Us)
+    assert abs(re_g - re_w) <= 1e-12
+    _check_factors(Us, Uw, sw, np.float64)
+    assert abs(gpu_error(A, G, Us) - re_g) <= 1e-12
+
+
+@pytest.mark.slow
+def test_config_tucker_400_fp32_sthosvd(lib):
+    A = I.tucker_plus_noise([400, 400, 400], [20, 20, 20], seed=2, noise=1e-4, decay=0.8,
+                            dtype=np.float32)
+    Gw, Uw, sw = T.rsthosvd(A, [20, 20, 20], 10, 2)
+    G, Us, info = run_hosvd(A, [20, 20, 20], 10, 2)
+    re_w, re_g = T.rel_error(A, Gw, Uw), T.rel_error(A, G, Us)
+    assert abs(re_g - re_w) <= 1e-6
+    _check_factors(Us, Uw, sw, np.float32)
+    assert abs(gpu_error(A, G, Us) - re_g) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_error_kernel(lib, dtype):
+    rng = np.random.default_rng(5)
+    A = np.asfortranarray(rng.standard_normal((23, 31, 19, 5)).astype(dtype))
+    r = [4, 6, 3, 2]
+    G = np.asfortranarray(rng.standard_normal(r).astype(dtype))
+    Us = [np.linalg.qr(rng.standard_normal((n, k)))[0].astype(dtype) for n, k in zip(A.shape, r)]
+    want = T.rel_error(A, G, Us)
+    got = gpu_error(A, G, Us)
+    assert abs(got - want) <= (1e-13 if dtype == np.float64 else 1e-6)
+    # exact reconstruction gives zero
+    Ax = np.asfortranarray(T.reconstruct(G, Us).astype(dtype))
+    assert gpu_error(Ax, G, Us) <= (1e-14 if dtype == np.float64 else 1e-6)
+
+
+def test_workspace_and_determinism(lib):
+    A = I.tucker_plus_noise([70, 50, 40], [6, 6, 6], 31, noise=1e-3, dtype=np.float32)
+    G1, U1, _ = run_hosvd(A, [5, 5, 5], 5, 2)
+    G2, U2, _ = run_hosvd(A, [5, 5, 5], 5, 2, workspace=True)
+    G3, U3, _ = run_hosvd(A, [5, 5, 5], 5, 2, stats=False)
+    assert np.array_equal(G1, G2) and np.array_equal(G1, G3)
+    for a, b, c in zip(U1, U2, U3):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_rank_exceeding_columns_is_rejected(lib):
+    # mode 1 has 2*2 = 4 columns: l_1 = min(5 + 1, 6, 4) = 4 < r_1 = 5
+    A = np.asfortranarray(np.ones((6, 2, 2), dtype=np.float32))
+    with pytest.raises(api.TuckerError) as e:
+        run_hosvd(A, [5, 1, 1], 1, 1)
+    assert e.value.status == api.TK_EINVAL
+
+
+def test_bf16_form_accuracy(lib):
+    A = I.tucker_plus_noise([120, 110, 100], [12, 12, 12], 41, noise=1e-4, decay=0.85,
+                            dtype=np.float32)
+    r = [10, 10, 10]
+    G, Us, _ = run_hosvd(A, r, 6, 3)
+    Gb, Ub, _ = run_hosvd(A, r, 6, 3, prec=api.TK_PREC_BF16_POWER)
+    re, reb = T.rel_error(A, G, Us), T.rel_error(A, Gb, Ub)
+    assert reb <= 1.01 * re
+    Gw, Uw, _ = T.rsthosvd(A, r, 6, 3, bf16_power=True)
+    assert abs(reb - T.rel_error(A, Gw, Uw)) <= 1e-6

@@ -225,6 +225,25 @@ def test_bf16_form_is_within_one_percent_on_a_noisy_decaying_tensor():
     assert reb <= 1.01 * re
 
 
+def test_bf16_form_needs_the_shift_restart():
+    # inverse-radius tensor with 1e-6 noise (the shape of the 1000^3 workload,
+    # smaller): the bfloat16 rounding floor lies far above the noise floor
+    A = I.inverse_radius(100, seed=3, noise=1e-6)
+    r, s, q = [30, 30, 30], 10, 3
+    G, Us, _ = T.rsthosvd(A, r, s, q)
+    Gb, Ub, stb = T.rsthosvd(A, r, s, q, bf16_power=True)
+    re, reb = T.rel_error(A, G, Us), T.rel_error(A, Gb, Ub)
+    assert reb <= 1.01 * re
+    # the restarted shift of step q stays below sigma_l(A_(1) A_(1)^T)/2
+    sig = np.linalg.svd(T.unfold(np.asarray(A, np.float64), 0), compute_uv=False)
+    assert stb[0]["alpha"][-1] <= sig[stb[0]["l"] - 1] ** 2 / 2 * (1 + 1e-9)
+    # carrying the bfloat16 shift into the FP32 step loses the accuracy
+    Ab = T.round_bf16(A)
+    Q, _ = T.svd_econ(T.sketch(A, 0, 40))
+    Q, _, a, _, _ = T.shifted_power(Ab, 0, Q, 0.0, 2)
+    assert a > sig[39] ** 2 / 2
+
+
 def test_processing_order_is_respected():
     A = I.tucker_plus_noise([20, 16, 12], [4, 4, 4], seed=16, noise=1e-2, dtype=np.float64)
     G1, U1, s1 = T.rsthosvd(A, [4, 4, 4], 3, 2, order=[2, 1, 0])
