@@ -123,10 +123,18 @@ def _check_factors(Us_g, Us_w, stats_w, dtype):
         r = Uw.shape[1]
         orth = np.abs(Ug.T @ Ug - np.eye(r)).max()
         assert orth <= (1e-13 if dtype == np.float64 else 1e-6), (k, orth)
-        j = T.separated_block(stats_w[k]["sigma"], r)
+        sig = np.asarray(stats_w[k]["sigma"])
+        if not stats_w[k]["alpha"]:
+            # q = 0: Sigma is sigma(A Omega), linear in A; square it so the gap
+            # test sees the same scale as the power steps' sigma(A A^T Q)
+            sig = sig ** 2
+        j = T.separated_block(sig, r)
         if j > 0:
             s = T.principal_sines(Ug[:, :j], Uw[:, :j]).max()
-            assert s <= (1e-9 if dtype == np.float64 else 1e-5), (k, j, s)
+            # sketch-only factors (q = 0) are not contracted by any power
+            # step, so upstream FP32 differences reach them at first order
+            tol = 1e-9 if dtype == np.float64 else (1e-5 if stats_w[k]["alpha"] else 1e-4)
+            assert s <= tol, (k, j, s)
 
 
 CASES = [
