@@ -130,6 +130,26 @@ tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t 
 tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_t tag,
                         double* Y, void* stream);
 
+/* The sketch of tucker_sketch, computed without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory on their behalf (servers that
+ * reserve all device memory up front, plugins whose host application owns
+ * the allocator, loops that must not risk an allocation failing or stalling
+ * mid-request).  It calls no cudaMalloc, cudaFree or allocating routine.
+ * Its partial products live in one static device array of
+ * TK_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit.  Arguments, layout and result are those of tucker_sketch.
+ * Limits: n_k * (l rounded up to 16, 32, 64 or 128) * 4 bytes (8 for F64
+ * tensors) must not exceed TK_NOALLOC_SCRATCH_BYTES, else TK_EWORKSPACE is
+ * returned and nothing runs.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (different streams, concurrent
+ * threads) race on it and must be serialised by the caller. */
+#define TK_NOALLOC_SCRATCH_BYTES (8u << 20)
+tk_status tucker_sketch_noalloc(const tk_tensor* A, int k, int l, uint64_t seed, uint32_t tag,
+                                double* Y, void* stream);
+
 /* q steps of the shifted power loop on A_(k) (Algorithm 2 inner loop):
  *   [Q, Sigma] = svd(A_(k)(A_(k)^T Q) - alpha_{t-1} Q, 'econ'), shift update.
  * Q:     in: n_k x l orthonormal (FP64, device); out: left singular vectors.
