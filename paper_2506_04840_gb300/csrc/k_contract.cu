@@ -121,14 +121,16 @@ template <typename TA>
 __global__ void k_reduce(const TA* __restrict__ part, int splits, int64_t n, int l, int lc,
                          const double* __restrict__ Q, const double* __restrict__ alpha,
                          double* __restrict__ Y) {
+  // consecutive threads take consecutive columns c of one row: coalesced
+  // reads of the [split][i][c] partials
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * l) return;
-  const int64_t i = idx % n;
-  const int c = (int)(idx / n);
+  const int c = (int)(idx % l);
+  const int64_t i = idx / l;
   double s = 0.0;
   for (int sp = 0; sp < splits; ++sp) s += (double)part[((int64_t)sp * n + i) * lc + c];
-  if (Q != nullptr) s -= alpha[0] * Q[idx];
-  Y[idx] = s;
+  if (Q != nullptr) s -= alpha[0] * Q[i + n * c];
+  Y[i + n * c] = s;
 }
 
 // out[j, c] = sum_i X(p, i, s) B(i, c) for a tile of TJ columns and LC
@@ -221,7 +223,10 @@ k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* _
       }
     }
   } else {
-    double e2 = 0.0, a2 = 0.0;
+    // per-thread sums of TMJ*TN terms in the accumulation type (FP64 FMAs
+    // run at a small fraction of the FP32 rate on this GPU), then FP64
+    // across threads and blocks
+    TA e2t = (TA)0, a2t = (TA)0;
 #pragma unroll
     for (int x = 0; x < TMJ; ++x) {
       const int64_t j = j0 + tj + 16 * x;   // S == 1: j = p
@@ -231,12 +236,13 @@ k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* _
         const int c = c0 + tc + 16 * q;
         if (c < m) {
           const TA av = A[j + P * (int64_t)c];
-          const double dv = (double)(av - acc[x][q]);
-          e2 += dv * dv;
-          a2 += (double)av * (double)av;
+          const TA dv = av - acc[x][q];
+          e2t = fma(dv, dv, e2t);
+          a2t = fma(av, av, a2t);
         }
       }
     }
+    double e2 = (double)e2t, a2 = (double)a2t;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       e2 += __shfl_xor_sync(0xffffffffu, e2, o);

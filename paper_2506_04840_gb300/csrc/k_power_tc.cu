@@ -1,0 +1,508 @@
+// Fused shifted power step on tcgen05 tensor cores, bfloat16 tensor:
+//   Y_part = X_(k) (X_(k)^T Q)      (Algorithm 2/3 inner loop; the shift
+//                                    -alpha Q is applied by the reduction)
+// for a mode-major view (P == 1): X_(k) is n x cols, column j contiguous.
+//
+// One HBM read of X per step.  A CTA owns a 32-wide part of the l columns
+// of Q (c-part) and streams column slabs of 64 columns:
+//   GEMM1  D1[j, c] = sum_i X[i, j] Q[i, c]      (M = 64 slab columns,
+//          N = 32, K = n; A = the TMA tile read K-major, B = Q^T resident)
+//   epilogue: D1 (TMEM) -> bfloat16 W^T tile in shared memory
+//   GEMM2  Y[i, c] += sum_j X[i, j] W[j, c]      (M = 128 rows per tile,
+//          N = 32, K = 64; A = the same TMA tile read MN-major)
+// Y stays in TMEM (ceil(n/128) tiles x 32 columns) for the whole launch and
+// is written once as a per-CTA FP32 partial.  CTAs of different c-parts
+// process the same slabs in the same order, so the second read of a slab is
+// served by L2.
+//
+// Roles: warp 0 issues TMA, warp 1 issues MMAs (one thread) and owns TMEM,
+// warps 2-5 run the epilogue.  Every wait is bounded by a time limit; on
+// expiry the CTA records TK_ETIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tk_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+namespace tc {
+
+constexpr int NC = 32;          // Q columns per CTA (c-part width)
+constexpr int BJ = 64;          // slab width (columns of X_(k))
+constexpr int CHUNK_I = 64;     // rows of one TMA box (128 bytes of bf16)
+constexpr int SUP_BYTES = 2 * CHUNK_I * BJ * 2;   // 128 rows x 64 cols bf16 = 16 KB
+constexpr int QT_CHUNK_BYTES = NC * 128;           // 32 rows x 64 i bf16 = 4 KB
+constexpr int W_BYTES = NC * 128;                  // 32 rows (c) x 64 j bf16 = 4 KB
+constexpr int THREADS = 192;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// 64-bit shared-memory matrix descriptor, 128-byte swizzle.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B, FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the limit ran out (and sets *abort).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (true) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort) return false;
+    if (now_ns() - t0 > WAIT_NS) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3}], [%4];"
+               :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+               "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                 "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                 "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                 "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Params {
+  int n;           // rows of X_(k)
+  int nt;          // 128-row tiles (superchunks) per slab
+  long long cols;  // columns of X_(k)
+  int nslabs;      // ceil(cols / BJ)
+  int cparts;      // c-parts (l_pad / NC)
+  int ring;        // superchunk slots
+  int l_pad;       // row stride of the partial output
+  uint32_t tmem_cols;
+};
+
+struct __align__(8) Bars {
+  uint64_t full[16];
+  uint64_t empty[16];
+  uint64_t qfull;
+  uint64_t d1_full[2];
+  uint64_t d1_empty[2];
+  uint64_t w_full[2];
+  uint64_t w_empty[2];
+  uint64_t y_done;
+  uint64_t drain;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+           Params pr, float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  __shared__ Bars bars;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int nq = pr.nt * 2;                       // Q^T chunks of 64 rows
+  unsigned char* sQ = sm;                         // nq x 4 KB
+  unsigned char* sRing = sQ + nq * QT_CHUNK_BYTES;   // ring x 16 KB
+  unsigned char* sW = sRing + pr.ring * SUP_BYTES;   // 2 x 4 KB
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpart = blockIdx.x % pr.cparts;
+  const int group = blockIdx.x / pr.cparts;
+  const int ngroups = gridDim.x / pr.cparts;
+  // slabs of this CTA: group, group + ngroups, ...
+  const int my_slabs = group < pr.nslabs ? (pr.nslabs - 1 - group) / ngroups + 1 : 0;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < pr.ring; ++s) {
+      mbar_init(smem_u32(&bars.full[s]), 1);
+      mbar_init(smem_u32(&bars.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bars.qfull), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars.d1_full[b]), 1);
+      mbar_init(smem_u32(&bars.d1_empty[b]), 4);
+      mbar_init(smem_u32(&bars.w_full[b]), 4);
+      mbar_init(smem_u32(&bars.w_empty[b]), 1);
+    }
+    mbar_init(smem_u32(&bars.y_done), 1);
+    mbar_init(smem_u32(&bars.drain), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(pr.tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t d1col0 = (uint32_t)(pr.nt * NC);
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && my_slabs > 0) {
+      asm volatile("prefetch.tensormap [%0];" :: "l"((uint64_t)&tmX) : "memory");
+      const uint32_t qb = smem_u32(&bars.qfull);
+      mbar_expect_tx(qb, (uint32_t)(nq * QT_CHUNK_BYTES));
+      for (int ch = 0; ch < nq; ++ch)
+        tma_load_2d(smem_u32(sQ + ch * QT_CHUNK_BYTES), &tmQ, ch * CHUNK_I, cpart * NC, qb);
+      long long issued = 0;
+      for (int k = 0; k < my_slabs && !abort_flag; ++k) {
+        const int slab = group + k * ngroups;
+        for (int t = 0; t < pr.nt; ++t, ++issued) {
+          const int slot = (int)(issued % pr.ring);
+          const uint32_t use = (uint32_t)(issued / pr.ring);
+          if (!mbar_wait(smem_u32(&bars.empty[slot]), (use & 1) ^ 1, &abort_flag)) break;
+          const uint32_t fb = smem_u32(&bars.full[slot]);
+          mbar_expect_tx(fb, SUP_BYTES);
+          const uint32_t dst = smem_u32(sRing + slot * SUP_BYTES);
+          tma_load_2d(dst, &tmX, t * 128, slab * BJ, fb);
+          tma_load_2d(dst + SUP_BYTES / 2, &tmX, t * 128 + CHUNK_I, slab * BJ, fb);
+        }
+        if (abort_flag) break;
+      }
+      // drain: every issued copy must have landed before the CTA exits
+      const long long first = issued > pr.ring ? issued - pr.ring : 0;
+      for (long long u = first; u < issued; ++u) {
+        const int slot = (int)(u % pr.ring);
+        const uint32_t use = (uint32_t)(u / pr.ring);
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(smem_u32(&bars.full[slot]), use & 1) && now_ns() - t0 < WAIT_NS) {
+        }
+      }
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(qb, 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0 && my_slabs > 0) {
+      const uint32_t ID1 = idesc_bf16(64, NC, 0, 0);
+      const uint32_t ID2 = idesc_bf16(128, NC, 1, 0);
+      bool ok = mbar_wait(smem_u32(&bars.qfull), 0, &abort_flag);
+      fence_after();
+      long long consumed = 0;
+      const uint32_t qbase = smem_u32(sQ);
+      int slots[16];
+      for (int k = 0; k < my_slabs && ok; ++k) {
+        const int b = k & 1;
+        const uint32_t v = (uint32_t)(k >> 1);
+        const uint32_t d1 = tmem + d1col0 + (uint32_t)(b * NC);
+        if (!mbar_wait(smem_u32(&bars.d1_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
+        fence_after();
+        // GEMM1: D1 = X_slab^T Q_part  (K over the n rows)
+        for (int t = 0; t < pr.nt; ++t, ++consumed) {
+          const int slot = (int)(consumed % pr.ring);
+          const uint32_t use = (uint32_t)(consumed / pr.ring);
+          slots[t] = slot;
+          if (!mbar_wait(smem_u32(&bars.full[slot]), use & 1, &abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t da = desc_sw128(sbase + h * (SUP_BYTES / 2) + kk * 32, 16, 1024);
+              const uint64_t db = desc_sw128(qbase + (2 * t + h) * QT_CHUNK_BYTES + kk * 32, 16,
+                                             1024);
+              mma_bf16(d1, da, db, ID1, (t | h | kk) != 0);
+            }
+          }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars.d1_full[b]));
+        // GEMM2: Y_tile(t) += X_tile(t) W   (K over the 64 slab columns)
+        if (!mbar_wait(smem_u32(&bars.w_full[b]), v & 1, &abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint32_t wbase = smem_u32(sW + b * W_BYTES);
+        for (int t = 0; t < pr.nt; ++t) {
+          const uint32_t sbase = smem_u32(sRing + slots[t] * SUP_BYTES);
+          const uint32_t yt = tmem + (uint32_t)(t * NC);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
+            const uint64_t db = desc_sw128(wbase + kk * 32, 16, 1024);
+            mma_bf16(yt, da, db, ID2, (k | kk) != 0);
+          }
+          mma_commit(smem_u32(&bars.empty[slots[t]]));
+        }
+        mma_commit(smem_u32(&bars.w_empty[b]));
+      }
+      mma_commit(smem_u32(&bars.y_done));
+      // drain: all MMAs issued by this thread complete before TMEM is freed
+      mma_commit(smem_u32(&bars.drain));
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(smem_u32(&bars.drain), 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2..5 ----------------
+    const int q = warp & 3;                     // TMEM lane quarter of this warp
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    bool ok = true;
+    for (int k = 0; k < my_slabs && ok; ++k) {
+      const int b = k & 1;
+      const uint32_t v = (uint32_t)(k >> 1);
+      if (!mbar_wait(smem_u32(&bars.d1_full[b]), v & 1, &abort_flag)) { ok = false; break; }
+      fence_after();
+      uint32_t r[32];
+      tmem_ld32(tmem + lane_off + d1col0 + (uint32_t)(b * NC), r);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.d1_empty[b]));
+      if (!mbar_wait(smem_u32(&bars.w_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
+      // M = 64 accumulator: lanes 0..15 of quarter q hold slab columns j = 16 q + lane
+      if (lane < 16) {
+        const int j = 16 * q + lane;
+        unsigned char* wb = sW + b * W_BYTES;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int off = c * 128 + ((((2 * j) >> 4) ^ (c & 7)) << 4) + ((2 * j) & 15);
+          *reinterpret_cast<__nv_bfloat16*>(wb + off) = __float2bfloat16_rn(__uint_as_float(r[c]));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.w_full[b]));
+    }
+    // write this CTA's Y partial: rows 128 t + 32 q + lane, columns of this c-part
+    const bool have = my_slabs > 0 && ok && mbar_wait(smem_u32(&bars.y_done), 0, &abort_flag);
+    if (have) fence_after();
+    for (int t = 0; t < pr.nt; ++t) {
+      uint32_t r[32];
+      if (have) tmem_ld32(tmem + lane_off + (uint32_t)(t * NC), r);
+      const int i = t * 128 + q * 32 + lane;
+      if (i < pr.n) {
+        float* dst = part + ((long long)group * pr.n + i) * pr.l_pad + cpart * NC;
+#pragma unroll
+        for (int c = 0; c < NC; c += 4) {
+          float4 v4;
+          v4.x = have ? __uint_as_float(r[c]) : 0.f;
+          v4.y = have ? __uint_as_float(r[c + 1]) : 0.f;
+          v4.z = have ? __uint_as_float(r[c + 2]) : 0.f;
+          v4.w = have ? __uint_as_float(r[c + 3]) : 0.f;
+          *reinterpret_cast<float4*>(dst + c) = v4;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) atomicExch(err, (int)TK_ETIMEOUT);
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(pr.tmem_cols) : "memory");
+  }
+}
+
+// Q (n x l, FP64, column-major) -> Q^T (l_pad x n_pad) bfloat16, zero padded.
+__global__ void k_qt_bf16(const double* __restrict__ Q, int n, int l, int n_pad, int l_pad,
+                          __nv_bfloat16* __restrict__ qt) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n_pad * l_pad) return;
+  const int i = (int)(idx % n_pad), c = (int)(idx / n_pad);
+  const float v = (i < n && c < l) ? (float)Q[i + (long long)n * c] : 0.f;
+  qt[idx] = __float2bfloat16_rn(v);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+                 uint32_t box_inner, uint32_t box_outer) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct TcShape {
+  int nt, nq, l_pad, cparts, ring;
+  uint32_t tmem_cols;
+  size_t smem;
+};
+
+bool tc_shape(int64_t n, int l, TcShape* s) {
+  if (n < 8 || (n % 8) != 0 || l < 1 || l > TK_MAX_L) return false;
+  s->nt = (int)((n + 127) / 128);
+  if (s->nt > 16) return false;                 // MMA thread keeps 16 slot ids
+  s->nq = 2 * s->nt;
+  s->l_pad = (l + tc::NC - 1) / tc::NC * tc::NC;
+  s->cparts = s->l_pad / tc::NC;
+  const uint32_t need = (uint32_t)(s->nt * tc::NC + 2 * tc::NC);
+  uint32_t cols = 32;
+  while (cols < need) cols <<= 1;
+  if (cols > 512) return false;
+  s->tmem_cols = cols;
+  const size_t fixed = (size_t)s->nq * tc::QT_CHUNK_BYTES + 2 * tc::W_BYTES + 1024;
+  const size_t budget = 227 * 1024 - 2048;   // static smem (barriers) kept aside
+  if (fixed + (size_t)(s->nt + 1) * tc::SUP_BYTES > budget) return false;
+  int ring = (int)((budget - fixed) / tc::SUP_BYTES);
+  ring = std::min(ring, 16);
+  ring = std::min(ring, 2 * s->nt + 2);
+  s->ring = ring;
+  s->smem = fixed + (size_t)ring * tc::SUP_BYTES;
+  return true;
+}
+
+}  // namespace
+
+bool power_tc_supported(View v, int l, const void* X) {
+  TcShape s;
+  return v.P == 1 && tc_shape(v.n, l, &s) && (((uintptr_t)X) & 15) == 0 &&
+         v.cols() < (1LL << 31) && get_encode() != nullptr;
+}
+
+int power_tc_groups(View v, int l) {
+  TcShape s;
+  if (!tc_shape(v.n, l, &s)) return 0;
+  const int per_sm = (int)(512 / s.tmem_cols);
+  const long long nslabs = (v.cols() + tc::BJ - 1) / tc::BJ;
+  long long groups = (long long)num_sms() * per_sm / s.cparts;
+  groups = std::max(1LL, std::min(groups, nslabs));
+  return (int)groups;
+}
+
+size_t power_tc_scratch(View v, int l) {
+  TcShape s;
+  if (!tc_shape(v.n, l, &s)) return 0;
+  return (size_t)s.nt * 128 * s.l_pad * sizeof(__nv_bfloat16) + 256;
+}
+
+cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void* scratch,
+                            float* part, int groups, int* err, cudaStream_t st) {
+  TcShape s;
+  if (!tc_shape(v.n, l, &s)) return cudaErrorInvalidValue;
+  const int n_pad = s.nt * 128;
+  __nv_bfloat16* qt = (__nv_bfloat16*)scratch;
+  {
+    const long long tot = (long long)n_pad * s.l_pad;
+    count_kernels(1);
+    tc::k_qt_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Q, (int)v.n, l, n_pad, s.l_pad,
+                                                                  qt);
+  }
+  CUtensorMap mx, mq;
+  if (!make_map_2d(&mx, X, (uint64_t)v.n, (uint64_t)v.cols(), 64, tc::BJ)) return cudaErrorUnknown;
+  if (!make_map_2d(&mq, qt, (uint64_t)n_pad, (uint64_t)s.l_pad, 64, tc::NC))
+    return cudaErrorUnknown;
+  tc::Params pr;
+  pr.n = (int)v.n;
+  pr.nt = s.nt;
+  pr.cols = v.cols();
+  pr.nslabs = (int)((v.cols() + tc::BJ - 1) / tc::BJ);
+  pr.cparts = s.cparts;
+  pr.ring = s.ring;
+  pr.l_pad = s.l_pad;
+  pr.tmem_cols = s.tmem_cols;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_power_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024 - 2048);
+    attr = true;
+  }
+  // occupancy: at most 512 / tmem_cols CTAs per SM (TMEM), enforced through
+  // the shared-memory request
+  const int per_sm = (int)(512 / s.tmem_cols);
+  size_t smem = s.smem;
+  if (per_sm == 1) smem = std::max(smem, (size_t)120 * 1024);
+  else if (per_sm == 2) smem = std::max(smem, (size_t)80 * 1024);
+  else smem = std::max(smem, (size_t)(230 * 1024 / (per_sm + 1)));
+  count_kernels(1);
+  tc::k_power_tc<<<groups * s.cparts, tc::THREADS, smem, st>>>(mx, mq, pr, part, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tk

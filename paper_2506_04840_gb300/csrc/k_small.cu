@@ -2,16 +2,17 @@
 // and 3 call it after the sketch and after every shifted power step), plus
 // the adaptive shift update of Algorithms 2/3.
 //
-//  k_leaf_qr : Householder QR of row blocks of MB rows (one CTA each).
-//  k_root    : Householder QR of the stacked l x l triangles, one-sided
-//              (Hestenes) Jacobi on R^T, whose accumulated rotations are the
-//              left singular vectors of R; descending sort; multiplication
-//              of the root Q into them; the shift update.
-//  k_leaf_q  : Q rows of each block = block reflectors applied to the
-//              block's share of the root result; per-column largest |entry|.
-//  k_sign    : sign convention (entry of largest |value| positive, lowest
-//              row on ties).
-//
+// Method (all on the device, no host round trip):
+//   Householder QR Y = Q_h R;  one-sided (Hestenes) Jacobi on the columns of
+//   R^T, whose accumulated rotations U_R are R's left singular vectors
+//   (orthogonal even when Y is rank deficient) and whose column norms are
+//   Sigma;  descending sort;  Q = Q_h U_R;  sign convention (entry of
+//   largest |value| positive, lowest row on ties);  shift update.
+// Paths:
+//   * one CTA (k_svd_one) when Y fits in shared memory;
+//   * otherwise a two-level TSQR: k_leaf_qr (row blocks) -> k_root (QR of the
+//     stacked triangles, Jacobi, root Q times U_R) -> k_leaf_q (block Q times
+//     the root result) -> k_sign.
 // The working precision T is FP64 for FP64 tensors and FP32 for FP32/BF16
 // tensors, matching the precision in which Y itself was formed.
 #include <algorithm>
@@ -33,6 +34,72 @@ template <typename T> __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// Householder reflector for column j of A (ld m) given ssq = sum of squares of
+// its entries below the diagonal; run by one warp.  LAPACK-style generation
+// (beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta)).
+template <typename T>
+__device__ __forceinline__ void make_reflector(T* A, int m, int j, T ssq, T* tau) {
+  const int lane = threadIdx.x & 31;
+  T* x = A + (int64_t)m * j;
+  const T alpha = x[j];
+  const T xnorm = sqrt(ssq);
+  T beta = alpha, tj = (T)0;
+  if (xnorm > (T)0) {
+    const T mx = max((T)fabs(alpha), xnorm);
+    const T a1 = alpha / mx, x1 = xnorm / mx;
+    beta = -copysign(mx * sqrt(a1 * a1 + x1 * x1), alpha);
+    tj = (beta - alpha) / beta;
+    const T scal = (T)1 / (alpha - beta);
+    for (int i = j + 1 + lane; i < m; i += 32) x[i] *= scal;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    x[j] = beta;
+    tau[j] = tj;
+  }
+}
+
+// Householder QR with look-ahead, in place, of an m x l column-major matrix
+// A (ld = m) in shared memory whose entries are O(1) (the caller scales);
+// reflector j is (1, A[j+1:, j]) with factor tau[j]; R is the upper
+// triangle.  Column c belongs to warp c % nw; the owner of column j+1 updates
+// it first and builds reflector j+1 before the step's only barrier.
+template <typename T>
+__device__ void householder_qr_la(T* A, int m, int l, T* tau) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp == 0) {
+    T s = 0;
+    for (int i = 1 + lane; i < m; i += 32) s += A[i] * A[i];
+    s = warp_sum(s);
+    make_reflector(A, m, 0, s, tau);
+  }
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    const T tj = tau[j];
+    const T* v = A + (int64_t)m * j;
+    const int own_next = (j + 1) % nw;
+    // the owner of column j+1 handles it first, then the rest of its columns
+    for (int c = j + 1 + ((warp - (j + 1)) % nw + nw) % nw; c < l; c += nw) {
+      T* y = A + (int64_t)m * c;
+      if (tj != (T)0) {
+        T w = lane == 0 ? y[j] : (T)0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * y[i];
+        w = warp_sum(w) * tj;
+        if (lane == 0) y[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) y[i] -= w * v[i];
+        __syncwarp();
+      }
+      if (c == j + 1 && warp == own_next) {
+        T s = 0;
+        for (int i = c + 1 + lane; i < m; i += 32) s += y[i] * y[i];
+        s = warp_sum(s);
+        make_reflector(A, m, c, s, tau);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Householder QR, in place, of an m x l column-major matrix A (ld = m) in
 // shared memory; reflector j is (1, A[j+1:, j]) with factor tau[j]; R is the
 // upper triangle.  LAPACK-style generation (beta = -sign(alpha) ||x||,
@@ -47,11 +114,13 @@ __device__ void householder_qr(T* A, int m, int l, T* tau) {
       for (int i = j + 1 + lane; i < m; i += 32) amax = max(amax, (T)fabs(x[i]));
       amax = warp_max(amax);
       T ssq = (T)0;
-      if (amax > (T)0)
+      if (amax > (T)0) {
+        const T inv = (T)1 / amax;
         for (int i = j + 1 + lane; i < m; i += 32) {
-          const T t = x[i] / amax;
+          const T t = x[i] * inv;
           ssq += t * t;
         }
+      }
       ssq = warp_sum(ssq);
       const T xnorm = amax * sqrt(ssq);
       const T alpha = x[j];
@@ -87,17 +156,17 @@ __device__ void householder_qr(T* A, int m, int l, T* tau) {
   }
 }
 
-// B (m x l, ld m, shared) <- H_0 H_1 ... H_{l-1} B for reflectors stored in
-// V (ld m, global or shared) with factors tau.
+// Overwrite the reflectors in A (m x l, from householder_qr) with the first
+// l columns of Q_h = H_0 H_1 ... H_{l-1} [I; 0] (backward accumulation).
 template <typename T>
-__device__ void apply_q(const T* V, const T* tau, T* B, int m, int l) {
+__device__ void form_q_inplace(T* A, int m, int l, const T* tau) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = l - 1; j >= 0; --j) {
     const T tj = tau[j];
+    const T* v = A + (int64_t)m * j;
     if (tj != (T)0) {
-      const T* v = V + (int64_t)m * j;
-      for (int c = warp; c < l; c += nw) {
-        T* y = B + (int64_t)m * c;
+      for (int c = j + 1 + warp; c < l; c += nw) {
+        T* y = A + (int64_t)m * c;
         T w = lane == 0 ? y[j] : (T)0;
         for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * y[i];
         w = warp_sum(w) * tj;
@@ -106,9 +175,260 @@ __device__ void apply_q(const T* V, const T* tau, T* B, int m, int l) {
       }
     }
     __syncthreads();
+    T* x = A + (int64_t)m * j;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (i < j) x[i] = (T)0;
+      else if (i == j) x[i] = (T)1 - tj;
+      else x[i] = -tj * x[i];
+    }
+    __syncthreads();
   }
 }
 
+template <typename T> __device__ __forceinline__ T jacobi_tol(int l);
+template <> __device__ __forceinline__ float jacobi_tol<float>(int l) {
+  return fmaxf(4e-6f, 4.0f * (float)l * 5.9604645e-8f);
+}
+template <> __device__ __forceinline__ double jacobi_tol<double>(int l) {
+  return 4.0 * (double)l * 1.1102230246251565e-16;
+}
+
+// One-sided Jacobi on the l columns of J (l x l), accumulating the rotations
+// in Vp (starts as I) when Vp is non-null.  Round-robin pairing; each pair is
+// handled by a group of g lanes (g = 4 for l <= 32, 8 above) and the rounds
+// are spread over up to 8 warps synchronised by the named barrier 1 (only
+// those warps wait).  All threads of the block must call it; threads outside
+// the Jacobi warps return at once and the caller synchronises afterwards.
+// The rotation parameters use fast reciprocal square roots: c = rsqrt(1+t^2),
+// s = c t is an exact plane rotation up to rounding either way.
+template <typename T>
+__device__ void jacobi_warp(T* J, T* Vp, int l) {
+  const int m2 = l + (l & 1);
+  const int npairs = m2 / 2;
+  const int g = l > 32 ? 8 : 4;
+  const int nwj = min((npairs * g + 31) / 32, min(8, (int)(blockDim.x >> 5)));
+  const int nthr = nwj * 32;
+  if ((int)threadIdx.x >= nthr) return;
+  const int lane = threadIdx.x & 31;
+  const int groups = nthr / g;
+  const int gi = (int)threadIdx.x / g, sub = (int)threadIdx.x % g;
+  __shared__ int jflag[2];
+  if (threadIdx.x == 0) jflag[0] = jflag[1] = 0;
+  if (nwj > 1) asm volatile("bar.sync 1, %0;" :: "r"(nthr) : "memory");
+  else __syncwarp();
+  const T tol = jacobi_tol<T>(l);
+  const T tol2 = tol * tol;
+  const int max_sweeps = sizeof(T) == 8 ? 40 : 24;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    const int fb = sweep & 1;
+    int rotated = 0;
+    for (int rd = 0; rd < m2 - 1; ++rd) {
+      for (int pr0 = 0; pr0 < npairs; pr0 += groups) {
+        const int pr = pr0 + gi;
+        int p = 0, q = 0;
+        bool act = pr < npairs;
+        if (act) {
+          if (pr == 0) { p = rd; q = m2 - 1; }
+          else { p = (rd + pr) % (m2 - 1); q = (rd - pr + (m2 - 1)) % (m2 - 1); }
+          act = p < l && q < l;
+        }
+        T a = 0, bb = 0, gm = 0;
+        T* xp = J + (int64_t)l * p;
+        T* xq = J + (int64_t)l * q;
+        if (act)
+          for (int i = sub; i < l; i += g) {
+            const T u = xp[i], w = xq[i];
+            a += u * u;
+            bb += w * w;
+            gm += u * w;
+          }
+        for (int o = 1; o < g; o <<= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          gm += __shfl_xor_sync(0xffffffffu, gm, o);
+        }
+        if (act && gm != (T)0 && gm * gm > tol2 * a * bb) {
+          const T zeta = (bb - a) / (gm + gm);
+          T t;
+          if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
+          else t = copysign((T)1 / (fabs(zeta) + sqrt((T)1 + zeta * zeta)), zeta);
+          const T cs = rsqrt((T)1 + t * t);
+          const T sn = cs * t;
+          for (int i = sub; i < l; i += g) {
+            const T u = xp[i], w = xq[i];
+            xp[i] = cs * u - sn * w;
+            xq[i] = sn * u + cs * w;
+          }
+          if (Vp != nullptr) {
+            T* vp = Vp + (int64_t)l * p;
+            T* vq = Vp + (int64_t)l * q;
+            for (int i = sub; i < l; i += g) {
+              const T u = vp[i], w = vq[i];
+              vp[i] = cs * u - sn * w;
+              vq[i] = sn * u + cs * w;
+            }
+          }
+          rotated = 1;
+        }
+        if (nwj > 1) asm volatile("bar.sync 1, %0;" :: "r"(nthr) : "memory");
+        else __syncwarp();
+      }
+      // the other sweep's flag is free once every Jacobi thread has passed
+      // this sweep's first round (all have read it by then)
+      if (rd == 0 && threadIdx.x == 0) jflag[fb ^ 1] = 0;
+    }
+    if (__any_sync(0xffffffffu, rotated) && lane == 0) jflag[fb] = 1;
+    if (nwj > 1) asm volatile("bar.sync 1, %0;" :: "r"(nthr) : "memory");
+    else __syncwarp();
+    if (!jflag[fb]) break;
+  }
+}
+
+// sg[c] = ||J(:, c)||; perm = indices sorted by descending sg (lower index
+// first on ties).
+// The accumulated rotations Vp drift from unit column norms by a few
+// roundings per rotation; their columns are renormalised here.
+template <typename T>
+__device__ void sigma_perm(const T* J, int l, T* sg, int* perm, T* Vp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < l; c += nw) {
+    const T* x = J + (int64_t)l * c;
+    T s = 0;
+    for (int i = lane; i < l; i += 32) s += x[i] * x[i];
+    s = warp_sum(s);
+    if (lane == 0) sg[c] = sqrt(s);
+    T* v = Vp + (int64_t)l * c;
+    T t = 0;
+    for (int i = lane; i < l; i += 32) t += v[i] * v[i];
+    t = warp_sum(t);
+    const T inv = t > (T)0 ? (T)1 / sqrt(t) : (T)1;
+    __syncwarp();
+    for (int i = lane; i < l; i += 32) v[i] *= inv;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const T si = sg[i];
+    int rank = 0;
+    for (int j = 0; j < l; ++j) {
+      const T sj = sg[j];
+      if (sj > si || (sj == si && j < i)) ++rank;
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void shift_update(double sl, int rule, double* alpha,
+                                             double* alpha_hist, double* sigl_hist) {
+  const double a0 = alpha[0];
+  double an;
+  if (rule == (int)TK_SHIFT_NONE) an = 0.0;
+  else an = (sl > a0) ? 0.5 * (sl + a0) : a0;
+  alpha[0] = an;
+  if (alpha_hist) alpha_hist[0] = an;
+  if (sigl_hist) sigl_hist[0] = sl;
+}
+
+// Sign convention on columns of Q (n x l, global), one warp per column.
+__device__ void sign_fix_block(double* Q, int64_t n, int l) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < l; c += nw) {
+    double* q = Q + n * c;
+    double best = -1.0;
+    int64_t bi = 0;
+    for (int64_t i = lane; i < n; i += 32) {
+      const double v = fabs(q[i]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    const bool neg = q[bi] < 0.0;
+    if (neg)
+      for (int64_t i = lane; i < n; i += 32) q[i] = -q[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-CTA path: Y (n x l) fits in shared memory.
+// smem: A (n*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_svd_one(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
+                          double* __restrict__ sigma, int shift_rule, int update_shift,
+                          int basis_only, double* __restrict__ alpha,
+                          double* __restrict__ alpha_hist, double* __restrict__ sigl_hist,
+                          int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* J = A + (int64_t)n * l;
+  T* Vp = J + l * l;
+  T* sg = Vp + l * l;
+  T* ts = sg + l;
+  __shared__ int perm[TK_MAX_L];
+  __shared__ double wmax[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // scale Y to max |entry| = 1 so plain sums of squares cannot under/overflow
+  // (one pass over global memory, the scaling in shared memory)
+  T mx = 0;
+#pragma unroll 4
+  for (int64_t e = tid; e < (int64_t)n * l; e += blockDim.x) {
+    const T v = (T)Y[e];
+    A[e] = v;
+    mx = max(mx, (T)fabs(v));
+  }
+  mx = warp_max(mx);
+  if (lane == 0) wmax[warp] = (double)mx;
+  __syncthreads();
+  double gmax = 0.0;
+  for (int w = 0; w < nw; ++w) gmax = fmax(gmax, wmax[w]);
+  const double scale = (gmax > 0.0 && isfinite(gmax)) ? 1.0 / gmax : 1.0;
+  const T sc = (T)scale;
+  for (int64_t e = tid; e < (int64_t)n * l; e += blockDim.x) A[e] *= sc;
+  __syncthreads();
+  householder_qr_la(A, n, l, ts);
+  if (basis_only) {
+    // only span(Y) is needed: Q = Q_h
+    form_q_inplace(A, n, l, ts);
+    for (int64_t e = tid; e < (int64_t)n * l; e += blockDim.x) Q[e] = (double)A[e];
+    return;
+  }
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    J[e] = (c <= i) ? A[c + (int64_t)n * i] : (T)0;   // J = R^T
+    Vp[e] = (i == c) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  jacobi_warp(J, Vp, l);
+  __syncthreads();
+  sigma_perm(J, l, sg, perm, Vp);
+  form_q_inplace(A, n, l, ts);
+  // Q = Q_h U_R (U_R = Vp with columns in perm order), row by row
+  for (int i = tid; i < n; i += blockDim.x) {
+    for (int c = 0; c < l; ++c) {
+      const T* u = Vp + (int64_t)l * perm[c];
+      T s = 0;
+      for (int k = 0; k < l; ++k) s += A[i + (int64_t)n * k] * u[k];
+      Q[i + (int64_t)n * c] = (double)s;
+    }
+  }
+  __syncthreads();
+  sign_fix_block(Q, n, l);
+  if (tid < l) {
+    const double sv = (double)sg[perm[tid]] / scale;
+    sigma[tid] = sv;
+    if (!isfinite(sv)) atomicExch(status, (int)TK_EBREAKDOWN);
+  }
+  if (tid == 0 && update_shift)
+    shift_update((double)sg[perm[l - 1]] / scale, shift_rule, alpha, alpha_hist, sigl_hist);
+}
+
+// ---------------------------------------------------------------------------
+// Two-level TSQR path.
+// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_leaf_qr(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
                           T* __restrict__ V, T* __restrict__ tau, T* __restrict__ Rst) {
@@ -134,139 +454,52 @@ __global__ void k_leaf_qr(const double* __restrict__ Y, int64_t n, int l, int MB
   for (int j = threadIdx.x; j < l; j += blockDim.x) tau[(int64_t)b * l + j] = ts[j];
 }
 
-template <typename T> __device__ __forceinline__ T jacobi_tol(int l);
-template <> __device__ __forceinline__ float jacobi_tol<float>(int l) {
-  return fmaxf(1e-6f, 8.0f * (float)l * 5.9604645e-8f);
-}
-template <> __device__ __forceinline__ double jacobi_tol<double>(int l) {
-  return 8.0 * (double)l * 1.1102230246251565e-16;
-}
-
+// smem: S (m*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l), m = Pb*l
 template <typename T>
-__global__ void k_root(const T* __restrict__ Rst, int Pb, int l, T* __restrict__ Vr,
-                       T* __restrict__ taur, T* __restrict__ Mout, double* __restrict__ sigma,
-                       int shift_rule, int update_shift, double* __restrict__ alpha,
-                       double* __restrict__ alpha_hist, double* __restrict__ sigl_hist,
-                       int* __restrict__ status) {
+__global__ void k_root(const T* __restrict__ Rst, int Pb, int l, T* __restrict__ Mout,
+                       double* __restrict__ sigma, int shift_rule, int update_shift,
+                       double* __restrict__ alpha, double* __restrict__ alpha_hist,
+                       double* __restrict__ sigl_hist, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = Pb * l;
-  T* S = reinterpret_cast<T*>(smem_raw);          // m x l
-  T* J = S + (int64_t)m * l;                      // l x l, columns of R^T
-  T* Vp = J + (int64_t)l * l;                     // l x l rotations
-  T* sg = Vp + (int64_t)l * l;                    // l
-  T* ts = sg + l;                                 // l
+  T* S = reinterpret_cast<T*>(smem_raw);
+  T* J = S + (int64_t)m * l;
+  T* Vp = J + (int64_t)l * l;
+  T* sg = Vp + (int64_t)l * l;
+  T* ts = sg + l;
   __shared__ int perm[TK_MAX_L];
-  __shared__ int flag;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-
+  const int tid = threadIdx.x;
   for (int64_t e = tid; e < (int64_t)m * l; e += blockDim.x) S[e] = Rst[e];
   __syncthreads();
   householder_qr(S, m, l, ts);
-  for (int64_t e = tid; e < (int64_t)m * l; e += blockDim.x) Vr[e] = S[e];
-  for (int j = tid; j < l; j += blockDim.x) taur[j] = ts[j];
-  // J = R^T: J(i, c) = R(c, i); Vp = I
   for (int e = tid; e < l * l; e += blockDim.x) {
     const int i = e % l, c = e / l;
     J[e] = (c <= i) ? S[c + (int64_t)m * i] : (T)0;
     Vp[e] = (i == c) ? (T)1 : (T)0;
   }
   __syncthreads();
-
-  // One-sided Jacobi on the columns of J, round-robin pairing.
-  const int m2 = l + (l & 1);
-  const T tol = jacobi_tol<T>(l);
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) flag = 0;
-    __syncthreads();
-    for (int rd = 0; rd < m2 - 1; ++rd) {
-      for (int pr = warp; pr < m2 / 2; pr += nw) {
-        int p, q;
-        if (pr == 0) { p = rd; q = m2 - 1; }
-        else { p = (rd + pr) % (m2 - 1); q = (rd - pr + (m2 - 1)) % (m2 - 1); }
-        if (p >= l || q >= l) continue;
-        T* xp = J + (int64_t)l * p;
-        T* xq = J + (int64_t)l * q;
-        T a = 0, bb = 0, g = 0;
-        for (int i = lane; i < l; i += 32) {
-          a += xp[i] * xp[i];
-          bb += xq[i] * xq[i];
-          g += xp[i] * xq[i];
-        }
-        a = warp_sum(a);
-        bb = warp_sum(bb);
-        g = warp_sum(g);
-        if (g != (T)0 && fabs(g) > tol * sqrt(a) * sqrt(bb)) {
-          const T zeta = (bb - a) / (g + g);
-          T t;
-          if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
-          else t = copysign((T)1 / (fabs(zeta) + sqrt((T)1 + zeta * zeta)), zeta);
-          const T cs = (T)1 / sqrt((T)1 + t * t);
-          const T sn = cs * t;
-          for (int i = lane; i < l; i += 32) {
-            const T u = xp[i], w = xq[i];
-            xp[i] = cs * u - sn * w;
-            xq[i] = sn * u + cs * w;
-          }
-          T* vp = Vp + (int64_t)l * p;
-          T* vq = Vp + (int64_t)l * q;
-          for (int i = lane; i < l; i += 32) {
-            const T u = vp[i], w = vq[i];
-            vp[i] = cs * u - sn * w;
-            vq[i] = sn * u + cs * w;
-          }
-          if (lane == 0) flag = 1;
-        }
-      }
-      __syncthreads();
-    }
-    const int f = flag;
-    __syncthreads();
-    if (!f) break;
-  }
-  // singular values = column norms of J
-  for (int c = warp; c < l; c += nw) {
-    const T* x = J + (int64_t)l * c;
-    T s = 0;
-    for (int i = lane; i < l; i += 32) s += x[i] * x[i];
-    s = warp_sum(s);
-    if (lane == 0) sg[c] = sqrt(s);
-  }
+  jacobi_warp(J, Vp, l);
   __syncthreads();
-  for (int i = tid; i < l; i += blockDim.x) {
-    const T si = sg[i];
-    int rank = 0;
-    for (int j = 0; j < l; ++j) {
-      const T sj = sg[j];
-      if (sj > si || (sj == si && j < i)) ++rank;
+  sigma_perm(J, l, sg, perm, Vp);
+  form_q_inplace(S, m, l, ts);
+  for (int i = tid; i < m; i += blockDim.x) {
+    for (int c = 0; c < l; ++c) {
+      const T* u = Vp + (int64_t)l * perm[c];
+      T s = 0;
+      for (int k = 0; k < l; ++k) s += S[i + (int64_t)m * k] * u[k];
+      Mout[i + (int64_t)m * c] = s;
     }
-    perm[rank] = i;
-  }
-  __syncthreads();
-  // B = [U_R ; 0] with U_R columns sorted by descending sigma
-  for (int64_t e = tid; e < (int64_t)m * l; e += blockDim.x) {
-    const int i = (int)(e % m), c = (int)(e / m);
-    S[e] = i < l ? Vp[i + (int64_t)l * perm[c]] : (T)0;
   }
   if (tid < l) {
     const double sv = (double)sg[perm[tid]];
     sigma[tid] = sv;
     if (!isfinite(sv)) atomicExch(status, (int)TK_EBREAKDOWN);
   }
-  __syncthreads();
-  apply_q(Vr, ts, S, m, l);
-  for (int64_t e = tid; e < (int64_t)m * l; e += blockDim.x) Mout[e] = S[e];
-  if (tid == 0 && update_shift) {
-    const double sl = (double)sg[perm[l - 1]];
-    const double a0 = alpha[0];
-    double an;
-    if (shift_rule == (int)TK_SHIFT_NONE) an = 0.0;
-    else an = (sl > a0) ? 0.5 * (sl + a0) : a0;
-    alpha[0] = an;
-    if (alpha_hist) alpha_hist[0] = an;
-    if (sigl_hist) sigl_hist[0] = sl;
-  }
+  if (tid == 0 && update_shift)
+    shift_update((double)sg[perm[l - 1]], shift_rule, alpha, alpha_hist, sigl_hist);
 }
 
+// smem: B (MB*l) block reflectors -> block Q | M (l*l) | tau (l)
 template <typename T>
 __global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
                          const T* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
@@ -274,26 +507,36 @@ __global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
                          int* __restrict__ colidx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* B = reinterpret_cast<T*>(smem_raw);
+  T* M = B + (int64_t)MB * l;
+  T* ts = M + (int64_t)l * l;
   const int b = blockIdx.x;
   const int m = Pb * l;
   const int64_t r0 = (int64_t)b * MB;
   const int64_t rows = min((int64_t)MB, n - r0);
-  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) {
-    const int i = (int)(e % MB), c = (int)(e / MB);
-    B[e] = i < l ? Mout[((int64_t)b * l + i) + (int64_t)m * c] : (T)0;
+  const T* Vb = V + (int64_t)b * MB * l;
+  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) B[e] = Vb[e];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    M[e] = Mout[((int64_t)b * l + i) + (int64_t)m * c];
+  }
+  for (int j = threadIdx.x; j < l; j += blockDim.x) ts[j] = tau[(int64_t)b * l + j];
+  __syncthreads();
+  form_q_inplace(B, MB, l, ts);
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+    for (int c = 0; c < l; ++c) {
+      const T* u = M + (int64_t)l * c;
+      T s = 0;
+      for (int k = 0; k < l; ++k) s += B[i + (int64_t)MB * k] * u[k];
+      Q[(r0 + i) + n * c] = (double)s;
+    }
   }
   __syncthreads();
-  apply_q(V + (int64_t)b * MB * l, tau + (int64_t)b * l, B, MB, l);
-  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) {
-    const int64_t i = e % MB, c = e / MB;
-    if (i < rows) Q[(r0 + i) + n * c] = (double)B[e];
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < l; c += nw) {
     double best = -1.0;
     int bi = 0;                      // a valid row even if every entry is NaN
     for (int i = lane; i < rows; i += 32) {
-      const double v = fabs((double)B[i + (int64_t)MB * c]);
+      const double v = fabs(Q[(r0 + i) + n * c]);
       if (v > best) { best = v; bi = i; }
     }
 #pragma unroll
@@ -301,7 +544,6 @@ __global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
       const double ov = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      // (lanes that saw only NaN keep best = -1 and lose every comparison)
     }
     if (lane == 0) {
       colmax[(int64_t)b * l + c] = best;
@@ -357,17 +599,25 @@ __global__ void k_gram_part(const double* __restrict__ U, int64_t n, int r,
   }
 }
 
+// smem: R (r*r) | block rows (kPolishRows*r)
 __global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
                          const double* __restrict__ part, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* R = reinterpret_cast<double*>(smem_raw);      // r x r
+  double* R = reinterpret_cast<double*>(smem_raw);
+  double* Ub = R + (int64_t)r * r;
   __shared__ int bad;
   const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * kPolishRows;
+  const int rows = (int)min((int64_t)kPolishRows, n - r0);
   if (tid == 0) bad = 0;
   for (int e = tid; e < r * r; e += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * r * r + e];
     R[e] = s;
+  }
+  for (int e = tid; e < kPolishRows * r; e += blockDim.x) {
+    const int i = e % kPolishRows, c = e / kPolishRows;
+    Ub[e] = i < rows ? U[(r0 + i) + n * c] : 0.0;
   }
   __syncthreads();
   // Cholesky, upper factor in place: R(i, j) for i <= j, R^T R = G.
@@ -391,16 +641,18 @@ __global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
     if (tid == 0 && blockIdx.x == 0) atomicExch(status, (int)TK_EBREAKDOWN);
     return;
   }
-  // rows of this block: u <- u R^{-1} (forward substitution on R^T)
-  const int64_t r0 = (int64_t)blockIdx.x * kPolishRows;
-  const int rows = (int)min((int64_t)kPolishRows, n - r0);
+  // rows of this block: u <- u R^{-1} (forward substitution on R^T), in smem
   for (int i = tid; i < rows; i += blockDim.x) {
-    double* u = U + r0 + i;
     for (int c = 0; c < r; ++c) {
-      double s = u[n * c];
-      for (int k = 0; k < c; ++k) s -= u[n * k] * R[k + r * c];
-      u[n * c] = s / R[c + r * c];
+      double s = Ub[i + kPolishRows * c];
+      for (int k = 0; k < c; ++k) s -= Ub[i + kPolishRows * k] * R[k + r * c];
+      Ub[i + kPolishRows * c] = s / R[c + r * c];
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < kPolishRows * r; e += blockDim.x) {
+    const int i = e % kPolishRows, c = e / kPolishRows;
+    if (i < rows) U[(r0 + i) + n * c] = Ub[e];
   }
 }
 
@@ -421,8 +673,8 @@ cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* statu
   count_kernels(2);
   k_gram_part<<<nblk, 256, (size_t)kPolishRows * r * sizeof(double), st>>>(U, n, r,
                                                                            (double*)scratch);
-  k_polish<<<nblk, 128, (size_t)r * r * sizeof(double), st>>>(U, n, r, nblk,
-                                                               (const double*)scratch, status);
+  k_polish<<<nblk, 64, ((size_t)r * r + (size_t)kPolishRows * r) * sizeof(double), st>>>(
+      U, n, r, nblk, (const double*)scratch, status);
   return cudaGetLastError();
 }
 
@@ -431,67 +683,84 @@ static const size_t kSmemBudget = 200 * 1024;
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static size_t one_smem(int64_t n, int l, size_t es) {
+  return ((size_t)n * l + 2 * (size_t)l * l + 2 * (size_t)l) * es;
+}
 static size_t root_smem(int Pb, int l, size_t es) {
   return ((size_t)Pb * l * l + 2 * (size_t)l * l + 2 * (size_t)l) * es;
 }
+static size_t leafq_smem(int MB, int l, size_t es) {
+  return ((size_t)MB * l + (size_t)l * l + (size_t)l) * es;
+}
 
+// Pb == 1 selects the single-CTA path (MB = n).
 SmallPlan small_plan(int64_t n, int l, bool fp64) {
   SmallPlan p{l, 0, 0, 0};
   const size_t es = fp64 ? 8 : 4;
   if (l <= 0 || l > TK_MAX_L || n < l) return p;
-  int MB = (int)std::max<int64_t>(l, std::min<int64_t>(n, 128));
-  MB = (MB + 31) / 32 * 32;
-  for (;;) {
-    const int Pb = (int)((n + MB - 1) / MB);
-    const size_t leaf = ((size_t)MB * l + l) * es;
-    if (leaf > kSmemBudget) return p;
-    if (root_smem(Pb, l, es) <= kSmemBudget) {
+  if (one_smem(n, l, es) <= kSmemBudget) {
+    p.MB = (int)n;
+    p.Pb = 1;
+    p.scratch_bytes = 256;
+    return p;
+  }
+  for (int Pb = 2; Pb <= 64; ++Pb) {
+    int MB = (int)((n + Pb - 1) / Pb);
+    MB = std::max(MB, l);
+    MB = (MB + 31) / 32 * 32;
+    const int Pbe = (int)((n + MB - 1) / MB);
+    if (leafq_smem(MB, l, es) <= kSmemBudget && root_smem(Pbe, l, es) <= kSmemBudget) {
       p.MB = MB;
-      p.Pb = Pb;
+      p.Pb = Pbe;
       break;
     }
-    if (Pb == 1) return p;
-    MB *= 2;
   }
+  if (p.Pb <= 0) return p;
   const size_t Pb = p.Pb, MBs = p.MB, L = l;
   p.scratch_bytes = align256(Pb * MBs * L * es) + align256(Pb * L * es) +
-                    3 * align256(Pb * L * L * es) + align256(L * es) + align256(Pb * L * 8) +
-                    align256(Pb * L * 4);
+                    2 * align256(Pb * L * L * es) + align256(Pb * L * 8) + align256(Pb * L * 4);
   return p;
 }
 
 template <typename T>
 static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, double* Q,
                             double* sigma, void* scratch, int shift_rule, bool update_shift,
-                            double* alpha, double* alpha_hist, double* sigl_hist, int* status,
-                            cudaStream_t st) {
+                            bool basis_only, double* alpha, double* alpha_hist,
+                            double* sigl_hist, int* status, cudaStream_t st) {
   const int l = pl.l, MB = pl.MB, Pb = pl.Pb;
   const size_t es = sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int mx = (int)kSmemBudget + 4096;
+    cudaFuncSetAttribute(k_svd_one<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    attr_set = true;
+  }
+  if (Pb == 1) {
+    const int threads = (int64_t)n * l >= 4096 ? 1024 : 256;
+    count_kernels(1);
+    k_svd_one<T><<<1, threads, one_smem(n, l, es), st>>>(Y, (int)n, l, Q, sigma, shift_rule,
+                                                          update_shift ? 1 : 0,
+                                                          basis_only ? 1 : 0, alpha,
+                                                          alpha_hist, sigl_hist, status);
+    return cudaGetLastError();
+  }
   unsigned char* w = (unsigned char*)scratch;
   T* V = (T*)w;            w += align256((size_t)Pb * MB * l * es);
   T* tau = (T*)w;          w += align256((size_t)Pb * l * es);
   T* Rst = (T*)w;          w += align256((size_t)Pb * l * l * es);
-  T* Vr = (T*)w;           w += align256((size_t)Pb * l * l * es);
   T* Mout = (T*)w;         w += align256((size_t)Pb * l * l * es);
-  T* taur = (T*)w;         w += align256((size_t)l * es);
   double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
   int* colidx = (int*)w;
-
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_leaf_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget + 4096);
-    cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget + 4096);
-    cudaFuncSetAttribute(k_leaf_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget + 4096);
-    attr_set = true;
-  }
-  const size_t leaf_smem = ((size_t)MB * l + l) * es;
   count_kernels(4);
-  k_leaf_qr<T><<<Pb, 256, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
-  k_root<T><<<1, 512, root_smem(Pb, l, es), st>>>(Rst, Pb, l, Vr, taur, Mout, sigma, shift_rule,
-                                                  update_shift ? 1 : 0, alpha, alpha_hist,
-                                                  sigl_hist, status);
-  k_leaf_q<T><<<Pb, 256, (size_t)MB * l * es, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
-                                                    colidx);
+  k_leaf_qr<T><<<Pb, 512, ((size_t)MB * l + l) * es, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
+  k_root<T><<<1, 1024, root_smem(Pb, l, es), st>>>(Rst, Pb, l, Mout, sigma, shift_rule,
+                                                   update_shift ? 1 : 0, alpha, alpha_hist,
+                                                   sigl_hist, status);
+  k_leaf_q<T><<<Pb, 512, leafq_smem(MB, l, es), st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
+                                                      colidx);
   k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
   return cudaGetLastError();
 }
@@ -499,13 +768,14 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
 cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,
                              double* Q, double* sigma, void* scratch, int shift_rule,
                              bool update_shift, double* alpha, double* alpha_hist,
-                             double* sigl_hist, int* status, cudaStream_t st) {
+                             double* sigl_hist, int* status, cudaStream_t st,
+                             bool basis_only) {
   if (pl.Pb <= 0) return cudaErrorInvalidValue;
   if (fp64)
-    return small_go<double>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, alpha,
-                            alpha_hist, sigl_hist, status, st);
-  return small_go<float>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, alpha,
-                         alpha_hist, sigl_hist, status, st);
+    return small_go<double>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, basis_only,
+                            alpha, alpha_hist, sigl_hist, status, st);
+  return small_go<float>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, basis_only,
+                         alpha, alpha_hist, sigl_hist, status, st);
 }
 
 }  // namespace tk

@@ -61,10 +61,24 @@ int xtb_error_blocks(View v, int m);
 cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_err,
                                cudaStream_t st);
 
+// ---- fused bfloat16 power step on tcgen05 (k_power_tc.cu) ------------------
+// Y_part = X_(k)(X_(k)^T Q) for a mode-major (P == 1) bfloat16 view.  The
+// partials are [groups][n][l_pad] FP32 (l_pad = l rounded up to 32); sum them
+// with launch_reduce(X_BF16, part, groups, n, l, l_pad, ...).  scratch holds
+// the bfloat16 Q^T operand (power_tc_scratch bytes).
+bool power_tc_supported(View v, int l, const void* X);
+int power_tc_groups(View v, int l);
+size_t power_tc_scratch(View v, int l);
+inline int power_tc_lpad(int l) { return (l + 31) / 32 * 32; }
+cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void* scratch,
+                            float* part, int groups, int* err, cudaStream_t st);
+
 // ---- small dense solver (k_small.cu) -------------------------------------
 // [Q, Sigma] = svd(Y, 'econ') of an n x l FP64 matrix by a two-level
 // Householder TSQR, one-sided Jacobi on the l x l triangle, and the sign
 // convention; optional shift update.  `T` selects the working precision.
+// basis_only: Q = any orthonormal basis of span(Y) (Householder Q), no Sigma
+// (used where only the span matters: the sketch before a power step).
 struct SmallPlan {
   int l, MB, Pb;
   size_t scratch_bytes;
@@ -73,7 +87,8 @@ SmallPlan small_plan(int64_t n, int l, bool fp64);
 cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,
                              double* Q, double* sigma, void* scratch, int shift_rule,
                              bool update_shift, double* alpha, double* alpha_hist,
-                             double* sigl_hist, int* status, cudaStream_t st);
+                             double* sigl_hist, int* status, cudaStream_t st,
+                             bool basis_only = false);
 
 // One FP64 CholeskyQR step on an n x r factor computed in FP32 arithmetic
 // (U <- U R^{-1}, R^T R = U^T U); scratch: polish_scratch(n, r) bytes.

@@ -204,7 +204,14 @@ static tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, b
     p.part = std::max(p.part, (size_t)splits * v.n * lc * ta);
     if (p.q > 0) p.wbuf = std::max(p.wbuf, (size_t)cols * lk * ta);
     p.ymat = std::max(p.ymat, (size_t)v.n * lk * sizeof(double));
-    if (p.bf16 && p.q >= 2) p.shadow = std::max(p.shadow, (size_t)prod(cur) * 2);
+    if (p.bf16 && p.q >= 2) {
+      p.shadow = std::max(p.shadow, (size_t)prod(cur) * 2);
+      if (v.P == 1) {   // the fused tensor-core pass may run on this mode
+        p.part = std::max(p.part, (size_t)power_tc_groups(v, (int)lk) * v.n *
+                                      power_tc_lpad((int)lk) * sizeof(float));
+        p.small = std::max(p.small, power_tc_scratch(v, (int)lk));
+      }
+    }
     if (st) {
       cur[k] = p.r[k];
       if (step < p.d - 1) p.gbuf = std::max(p.gbuf, (size_t)prod(cur) * es);
@@ -283,8 +290,10 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
   TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
   {
     ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
+    // before a power step only span(Y) matters (alpha_0 = 0 needs no Sigma),
+    // so the sketch's svd reduces to an orthonormal basis
     TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false,
-                            w.alpha, nullptr, nullptr, w.status, st));
+                            w.alpha, nullptr, nullptr, w.status, st, p.q >= 1));
   }
   if (p.bf16 && p.q >= 2) {
     ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
@@ -298,17 +307,32 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     // from the bfloat16 copy to the FP32 tensor (the bfloat16 Sigma(l,l)
     // sits on the copy's rounding floor, far above sigma_l(X X^T)/2)
     if (p.bf16 && p.q >= 2 && t == p.q) TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
-    {
-      ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
-      TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st));
-    }
-    {
-      ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
-      TK_TRY(launch_xb(xp, Xp, v, w.w, l, seed, tag, k, w.part, splits, st));
-    }
-    {
-      ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
-      TK_TRY(launch_reduce(xp, w.part, splits, v.n, l, lc, w.Q, w.alpha, w.Y, st));
+    if (low && power_tc_supported(v, l, Xp)) {
+      // one fused tensor-core pass over the bfloat16 copy
+      const int groups = power_tc_groups(v, l);
+      const int lp = power_tc_lpad(l);
+      {
+        ProfScope ps(TK_K_POWER_FUSED, N * 2.0, 4.0 * N * l, st);
+        TK_TRY(launch_power_tc(Xp, v, w.Q, l, w.small, (float*)w.part, groups, w.status, st));
+      }
+      {
+        ProfScope ps(TK_K_CONVERT, (double)groups * v.n * lp * 4.0 + nl * 8.0,
+                     (double)groups * nl, st);
+        TK_TRY(launch_reduce(X_BF16, w.part, groups, v.n, l, lp, w.Q, w.alpha, w.Y, st));
+      }
+    } else {
+      {
+        ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
+        TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st));
+      }
+      {
+        ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
+        TK_TRY(launch_xb(xp, Xp, v, w.w, l, seed, tag, k, w.part, splits, st));
+      }
+      {
+        ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
+        TK_TRY(launch_reduce(xp, w.part, splits, v.n, l, lc, w.Q, w.alpha, w.Y, st));
+      }
     }
     {
       ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
@@ -505,11 +529,16 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
   if (sp.Pb <= 0) return TK_ENOTIMPL;
   const int splits = xb_splits(v, l);
   const int lc = xb_lc(l);
+  // bfloat16 mode-major tensors take the fused tensor-core pass
+  const bool tc = xt == X_BF16 && power_tc_supported(v, l, A->data);
+  const int groups = tc ? power_tc_groups(v, l) : 0;
+  const int lp = power_tc_lpad(l);
   Arena b;
-  const size_t o_w = b.offset((size_t)v.cols() * l * asize(xt));
-  const size_t o_part = b.offset((size_t)splits * v.n * lc * asize(xt));
+  const size_t o_w = b.offset(tc ? 0 : (size_t)v.cols() * l * asize(xt));
+  const size_t o_part = b.offset(tc ? (size_t)groups * v.n * lp * sizeof(float)
+                                    : (size_t)splits * v.n * lc * asize(xt));
   const size_t o_y = b.offset((size_t)v.n * l * sizeof(double));
-  const size_t o_sm = b.offset(sp.scratch_bytes);
+  const size_t o_sm = b.offset(std::max(sp.scratch_bytes, tc ? power_tc_scratch(v, l) : 0));
   const size_t o_st = b.offset(sizeof(int));
   unsigned char* base = nullptr;
   TK_TRY(cudaMallocAsync((void**)&base, b.off + 256, st));
@@ -517,24 +546,44 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
   void* part = base + o_part;
   void* Y = base + o_y;
   void* sm = base + o_sm;
-  void* stt = base + o_st;
+  int* stt = (int*)(base + o_st);
+  const double N = (double)v.P * (double)v.n * (double)v.S;
   auto body = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(stt, 0, sizeof(int), st);
     for (int t = 1; t <= q && e == cudaSuccess; ++t) {
-      e = launch_xtb(xt, A->data, v, Q, 1, v.n, l, wv, st);
-      if (e == cudaSuccess) e = launch_xb(xt, A->data, v, wv, l, 0, 0, k, part, splits, st);
-      if (e == cudaSuccess)
-        e = launch_reduce(xt, part, splits, v.n, l, lc, Q, alpha, (double*)Y, st);
+      if (tc) {
+        {
+          ProfScope ps(TK_K_POWER_FUSED, N * 2.0, 4.0 * N * l, st);
+          e = launch_power_tc(A->data, v, Q, l, sm, (float*)part, groups, stt, st);
+        }
+        if (e == cudaSuccess)
+          e = launch_reduce(X_BF16, part, groups, v.n, l, lp, Q, alpha, (double*)Y, st);
+      } else {
+        {
+          ProfScope ps(TK_K_POWER_W, N * xsize(xt), 2.0 * N * l, st);
+          e = launch_xtb(xt, A->data, v, Q, 1, v.n, l, wv, st);
+        }
+        if (e == cudaSuccess) {
+          ProfScope ps(TK_K_POWER_Y, N * xsize(xt), 2.0 * N * l, st);
+          e = launch_xb(xt, A->data, v, wv, l, 0, 0, k, part, splits, st);
+        }
+        if (e == cudaSuccess)
+          e = launch_reduce(xt, part, splits, v.n, l, lc, Q, alpha, (double*)Y, st);
+      }
       if (e == cudaSuccess)
         e = launch_small_svd(fp64, sp, (const double*)Y, v.n, Q, sigma, sm, (int)rule, true,
-                             alpha, nullptr, nullptr, (int*)stt, st);
+                             alpha, nullptr, nullptr, stt, st);
     }
     return e;
   };
   cudaError_t e = body();
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, stt, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaFreeAsync(base, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return from_cuda(e);
-  return from_cuda(e2);
+  if (e2 != cudaSuccess) return from_cuda(e2);
+  return (tk_status)status;
 }
 
 tk_status tucker_rthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,

@@ -121,6 +121,7 @@ def test_shifted_power_steps(lib, dtype, rule):
 def _check_factors(Us_g, Us_w, stats_w, dtype):
     for k, (Ug, Uw) in enumerate(zip(Us_g, Us_w)):
         r = Uw.shape[1]
+        Ug = np.asarray(Ug, dtype=np.float64)      # check in FP64, not in the data's FP32
         orth = np.abs(Ug.T @ Ug - np.eye(r)).max()
         assert orth <= (1e-13 if dtype == np.float64 else 1e-6), (k, orth)
         sig = np.asarray(stats_w[k]["sigma"])
