@@ -374,6 +374,366 @@ __global__ void k_qt_bf16(const double* __restrict__ Q, int n, int l, int n_pad,
   qt[idx] = __float2bfloat16_rn(v);
 }
 
+// ===========================================================================
+// Cluster variant: a pair of CTAs (one cluster) shares each slab.  CTA rank r
+// owns rows [r*half, (r+1)*half) of X_(k) and of Q (all 64 columns of Q), so
+// every byte of X is read from HBM exactly once and each CTA holds a
+// double-buffered half slab:
+//   GEMM1  D1_r[j, c] = sum_{i in half r} X[i, j] Q[i, c]   (M = 64, N = 64)
+//   the two partials are exchanged through distributed shared memory and
+//   summed (own + peer, the same order in both CTAs: identical W);
+//   GEMM2  Y[i, c] += sum_j X[i, j] W[j, c] for the CTA's rows (M = 128).
+// GEMM1 and GEMM2 are issued from two different warps, so waiting for the
+// next slab's data never delays the current slab's GEMM2.
+// Roles: warp 0 TMA, warp 1 GEMM1 issuer + TMEM owner, warp 2 GEMM2 issuer,
+// warps 3..6 epilogue (exchange, W, Y write-back).
+// ===========================================================================
+constexpr int NC2 = 64;
+constexpr int THREADS2 = 224;
+constexpr int XBUF_BYTES = BJ * NC2 * 4;        // 64 x 64 FP32 partial = 16 KB
+constexpr int W2_BYTES = BJ * 128;              // 64 rows (j) x 64 c bf16 = 8 KB
+constexpr int QT2_CHUNK_BYTES = NC2 * 128;      // 64 rows (c) x 64 i bf16 = 8 KB
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];"
+               :: "r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+               "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t a, uint32_t parity,
+                                                  volatile int* abort) {
+  if (mbar_try_acq_cluster(a, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (true) {
+    if (mbar_try_acq_cluster(a, parity)) return true;
+    if (*abort) return false;
+    if (now_ns() - t0 > WAIT_NS) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+// Asynchronous store into a peer CTA's shared memory; completion counts 16
+// bytes on the peer's mbarrier (no fence needed on either side).
+__device__ __forceinline__ void st_async_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                            uint32_t d, uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+               :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d), "r"(remote_mbar) : "memory");
+}
+
+struct Params2 {
+  int n;           // rows of X_(k)
+  int half;        // rows per CTA (multiple of 128)
+  int nth;         // 128-row tiles per CTA
+  long long cols;
+  int nslabs;
+  int l_pad;       // row stride of the partial output (64)
+  uint32_t tmem_cols;
+};
+
+struct __align__(8) Bars2 {
+  uint64_t full[12];
+  uint64_t empty[12];
+  uint64_t qfull;
+  uint64_t d1_full[2];
+  uint64_t d1_empty[2];
+  uint64_t w_full;
+  uint64_t w_empty;
+  uint64_t xfull;       // peer's partial has landed in my exchange buffer
+  uint64_t peer_free;   // the peer has consumed its exchange buffer
+  uint64_t y_done;
+  uint64_t drain1, drain2;
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
+k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+            Params2 pr, float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  __shared__ Bars2 bars;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int nq = pr.nth * 2;                           // Q^T chunks of 64 rows
+  const int ring = 2 * pr.nth;                         // two half-slab buffers
+  unsigned char* sQ = sm;                              // nq x 8 KB
+  unsigned char* sRing = sQ + nq * QT2_CHUNK_BYTES;    // ring x 16 KB
+  unsigned char* sW = sRing + ring * SUP_BYTES;        // 8 KB
+  float* sX = reinterpret_cast<float*>(sW + W2_BYTES);  // 16 KB exchange buffer
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;
+  const int cid = blockIdx.x >> 1;
+  const int nclusters = gridDim.x >> 1;
+  const int my_slabs = cid < pr.nslabs ? (pr.nslabs - 1 - cid) / nclusters + 1 : 0;
+  const int row0 = (int)rank * pr.half;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < ring; ++s) {
+      mbar_init(smem_u32(&bars.full[s]), 1);
+      mbar_init(smem_u32(&bars.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bars.qfull), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars.d1_full[b]), 1);
+      mbar_init(smem_u32(&bars.d1_empty[b]), 4);
+    }
+    mbar_init(smem_u32(&bars.w_full), 4);
+    mbar_init(smem_u32(&bars.w_empty), 1);
+    // xfull: one local arrival per phase carrying the expected 16 KB that the
+    // peer's asynchronous stores complete
+    mbar_init(smem_u32(&bars.xfull), 1);
+    mbar_init(smem_u32(&bars.peer_free), 4);
+    if (my_slabs > 0) mbar_expect_tx(smem_u32(&bars.xfull), (uint32_t)XBUF_BYTES);
+    mbar_init(smem_u32(&bars.y_done), 1);
+    mbar_init(smem_u32(&bars.drain1), 1);
+    mbar_init(smem_u32(&bars.drain2), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(pr.tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  cluster_sync();              // barriers of both CTAs initialised before any remote arrive
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t d1col0 = (uint32_t)(pr.nth * NC2);
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && my_slabs > 0) {
+      const uint32_t qb = smem_u32(&bars.qfull);
+      mbar_expect_tx(qb, (uint32_t)(nq * QT2_CHUNK_BYTES));
+      for (int ch = 0; ch < nq; ++ch)
+        tma_load_2d(smem_u32(sQ + ch * QT2_CHUNK_BYTES), &tmQ, row0 + ch * CHUNK_I, 0, qb);
+      long long issued = 0;
+      for (int k = 0; k < my_slabs && !abort_flag; ++k) {
+        const int slab = cid + k * nclusters;
+        for (int t = 0; t < pr.nth; ++t, ++issued) {
+          const int slot = (int)(issued % ring);
+          const uint32_t use = (uint32_t)(issued / ring);
+          if (!mbar_wait(smem_u32(&bars.empty[slot]), (use & 1) ^ 1, &abort_flag)) break;
+          const uint32_t fb = smem_u32(&bars.full[slot]);
+          mbar_expect_tx(fb, SUP_BYTES);
+          const uint32_t dst = smem_u32(sRing + slot * SUP_BYTES);
+          tma_load_2d(dst, &tmX, row0 + t * 128, slab * BJ, fb);
+          tma_load_2d(dst + SUP_BYTES / 2, &tmX, row0 + t * 128 + CHUNK_I, slab * BJ, fb);
+        }
+        if (abort_flag) break;
+      }
+      const long long first = issued > ring ? issued - ring : 0;
+      for (long long u = first; u < issued; ++u) {
+        const int slot = (int)(u % ring);
+        const uint32_t use = (uint32_t)(u / ring);
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(smem_u32(&bars.full[slot]), use & 1) && now_ns() - t0 < WAIT_NS) {
+        }
+      }
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(qb, 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- GEMM1 issuer: D1 = X_half^T Q_half ----------------
+    if (lane == 0 && my_slabs > 0) {
+      const uint32_t ID1 = idesc_bf16(64, NC2, 0, 0);
+      bool ok = mbar_wait(smem_u32(&bars.qfull), 0, &abort_flag);
+      fence_after();
+      const uint32_t qbase = smem_u32(sQ);
+      for (int k = 0; k < my_slabs && ok; ++k) {
+        const int b = k & 1;
+        const uint32_t v = (uint32_t)(k >> 1);
+        const uint32_t d1 = tmem + d1col0 + (uint32_t)(b * NC2);
+        if (!mbar_wait(smem_u32(&bars.d1_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
+        fence_after();
+        for (int t = 0; t < pr.nth; ++t) {
+          const long long u = (long long)k * pr.nth + t;
+          const int slot = (int)(u % ring);
+          const uint32_t use = (uint32_t)(u / ring);
+          if (!mbar_wait(smem_u32(&bars.full[slot]), use & 1, &abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t da = desc_sw128(sbase + h * (SUP_BYTES / 2) + kk * 32, 16, 1024);
+              const uint64_t db = desc_sw128(qbase + (2 * t + h) * QT2_CHUNK_BYTES + kk * 32, 16,
+                                             1024);
+              mma_bf16(d1, da, db, ID1, (t | h | kk) != 0);
+            }
+          }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars.d1_full[b]));
+      }
+      mma_commit(smem_u32(&bars.drain1));
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(smem_u32(&bars.drain1), 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else if (warp == 2) {
+    // ---------------- GEMM2 issuer: Y_tile += X_tile W ----------------
+    if (lane == 0 && my_slabs > 0) {
+      const uint32_t ID2 = idesc_bf16(128, NC2, 1, 1);
+      const uint32_t wbase = smem_u32(sW);
+      bool ok = true;
+      for (int k = 0; k < my_slabs && ok; ++k) {
+        if (!mbar_wait(smem_u32(&bars.w_full), k & 1, &abort_flag)) { ok = false; break; }
+        fence_after();
+        for (int t = 0; t < pr.nth; ++t) {
+          const long long u = (long long)k * pr.nth + t;
+          const int slot = (int)(u % ring);
+          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+          const uint32_t yt = tmem + (uint32_t)(t * NC2);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
+            const uint64_t db = desc_sw128(wbase + kk * 2048, 1024, 1024);
+            mma_bf16(yt, da, db, ID2, (k | kk) != 0);
+          }
+          mma_commit(smem_u32(&bars.empty[slot]));
+        }
+        mma_commit(smem_u32(&bars.w_empty));
+      }
+      mma_commit(smem_u32(&bars.y_done));
+      mma_commit(smem_u32(&bars.drain2));
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(smem_u32(&bars.drain2), 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 3..6 ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int j = 16 * q + (lane & 15);                 // D1 row of this lane (lane < 16)
+    const uint32_t xrow_peer = mapa(smem_u32(sX + j * NC2), peer);
+    const uint32_t peer_xfull = mapa(smem_u32(&bars.xfull), peer);
+    const uint32_t peer_free = mapa(smem_u32(&bars.peer_free), peer);
+    bool ok = true;
+    for (int k = 0; k < my_slabs && ok; ++k) {
+      const int b = k & 1;
+      const uint32_t v = (uint32_t)(k >> 1);
+      if (!mbar_wait(smem_u32(&bars.d1_full[b]), v & 1, &abort_flag)) { ok = false; break; }
+      fence_after();
+      uint32_t r0[32], r1[32];
+      tmem_ld32(tmem + lane_off + d1col0 + (uint32_t)(b * NC2), r0);
+      tmem_ld32(tmem + lane_off + d1col0 + (uint32_t)(b * NC2) + 32, r1);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.d1_empty[b]));
+      // send my partial row j to the peer once its exchange buffer is free
+      if (!mbar_wait_cluster(smem_u32(&bars.peer_free), (k & 1) ^ 1, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 4)
+          st_async_v4(xrow_peer + c * 4, r0[c], r0[c + 1], r0[c + 2], r0[c + 3], peer_xfull);
+#pragma unroll
+        for (int c = 0; c < 32; c += 4)
+          st_async_v4(xrow_peer + (32 + c) * 4, r1[c], r1[c + 1], r1[c + 2], r1[c + 3],
+                      peer_xfull);
+      }
+      // the peer's partial for my rows (its 16 KB completes my xfull phase)
+      if (!mbar_wait_cluster(smem_u32(&bars.xfull), k & 1, &abort_flag)) { ok = false; break; }
+      if (!mbar_wait(smem_u32(&bars.w_empty), (k & 1) ^ 1, &abort_flag)) { ok = false; break; }
+      if (lane < 16) {
+        const float* px = sX + j * NC2;
+        unsigned char* wrow = sW + j * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t* rr = ch < 4 ? r0 : r1;
+          const int c0 = (ch & 3) * 8;
+          const float4 pa = *reinterpret_cast<const float4*>(px + ch * 8);
+          const float4 pb = *reinterpret_cast<const float4*>(px + ch * 8 + 4);
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(__uint_as_float(rr[c0]) + pa.x,
+                                                    __uint_as_float(rr[c0 + 1]) + pa.y);
+          __nv_bfloat162 h1 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 2]) + pa.z,
+                                                    __uint_as_float(rr[c0 + 3]) + pa.w);
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 4]) + pb.x,
+                                                    __uint_as_float(rr[c0 + 5]) + pb.y);
+          __nv_bfloat162 h3 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 6]) + pb.z,
+                                                    __uint_as_float(rr[c0 + 7]) + pb.w);
+          uint4 o;
+          o.x = *reinterpret_cast<uint32_t*>(&h0);
+          o.y = *reinterpret_cast<uint32_t*>(&h1);
+          o.z = *reinterpret_cast<uint32_t*>(&h2);
+          o.w = *reinterpret_cast<uint32_t*>(&h3);
+          *reinterpret_cast<uint4*>(wrow + ((ch ^ (j & 7)) << 4)) = o;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bars.w_full));
+        // re-arm xfull for the next slab before the peer may send it
+        if (q == 0 && k + 1 < my_slabs) mbar_expect_tx(smem_u32(&bars.xfull), (uint32_t)XBUF_BYTES);
+        mbar_arrive_remote(peer_free);      // my exchange buffer may be refilled
+      }
+    }
+    // write this CTA's rows of the Y partial
+    const bool have = my_slabs > 0 && ok && mbar_wait(smem_u32(&bars.y_done), 0, &abort_flag);
+    if (have) fence_after();
+    for (int t = 0; t < pr.nth; ++t) {
+      uint32_t y0[32], y1[32];
+      if (have) {
+        tmem_ld32(tmem + lane_off + (uint32_t)(t * NC2), y0);
+        tmem_ld32(tmem + lane_off + (uint32_t)(t * NC2) + 32, y1);
+      }
+      const int i = row0 + t * 128 + q * 32 + lane;
+      if (i < pr.n) {
+        float* dst = part + ((long long)cid * pr.n + i) * pr.l_pad;
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          float4 a4, b4;
+          a4.x = have ? __uint_as_float(y0[c]) : 0.f;
+          a4.y = have ? __uint_as_float(y0[c + 1]) : 0.f;
+          a4.z = have ? __uint_as_float(y0[c + 2]) : 0.f;
+          a4.w = have ? __uint_as_float(y0[c + 3]) : 0.f;
+          b4.x = have ? __uint_as_float(y1[c]) : 0.f;
+          b4.y = have ? __uint_as_float(y1[c + 1]) : 0.f;
+          b4.z = have ? __uint_as_float(y1[c + 2]) : 0.f;
+          b4.w = have ? __uint_as_float(y1[c + 3]) : 0.f;
+          *reinterpret_cast<float4*>(dst + c) = a4;
+          *reinterpret_cast<float4*>(dst + 32 + c) = b4;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync();              // no CTA leaves while its peer may still touch its memory
+  if (abort_flag && threadIdx.x == 0) atomicExch(err, (int)TK_ETIMEOUT);
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(pr.tmem_cols) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -438,6 +798,36 @@ bool tc_shape(int64_t n, int l, TcShape* s) {
   return true;
 }
 
+
+// Cluster variant shape (n in [512, 1024], l <= 64).
+struct Tc2Shape {
+  int nth, half, nq, ring, nt;
+  uint32_t tmem_cols;
+  size_t smem;
+};
+
+bool tc2_shape(int64_t n, int l, Tc2Shape* s) {
+  if (n < 512 || n > 1024 || (n % 8) != 0 || l < 1 || l > tc::NC2) return false;
+  s->nt = (int)((n + 127) / 128);
+  s->nth = (s->nt + 1) / 2;
+  s->half = s->nth * 128;
+  s->nq = 2 * s->nth;
+  s->ring = 2 * s->nth;
+  const uint32_t need = (uint32_t)(s->nth * tc::NC2 + 2 * tc::NC2);
+  uint32_t cols = 32;
+  while (cols < need) cols <<= 1;
+  if (cols > 512 || s->ring > 12) return false;
+  s->tmem_cols = cols;
+  s->smem = (size_t)s->nq * tc::QT2_CHUNK_BYTES + (size_t)s->ring * tc::SUP_BYTES +
+            tc::W2_BYTES + tc::XBUF_BYTES + 1024;
+  return s->smem <= 227 * 1024 - 2048;
+}
+
+bool use_cluster(View v, int l) {
+  Tc2Shape s2;
+  return tc2_shape(v.n, l, &s2);
+}
+
 }  // namespace
 
 bool power_tc_supported(View v, int l, const void* X) {
@@ -446,11 +836,19 @@ bool power_tc_supported(View v, int l, const void* X) {
          v.cols() < (1LL << 31) && get_encode() != nullptr;
 }
 
+int power_tc_lpad(View v, int l) {
+  return use_cluster(v, l) ? tc::NC2 : (l + tc::NC - 1) / tc::NC * tc::NC;
+}
+
 int power_tc_groups(View v, int l) {
+  const long long nslabs = (v.cols() + tc::BJ - 1) / tc::BJ;
+  if (use_cluster(v, l)) {
+    long long cl = num_sms() / 2;
+    return (int)std::max(1LL, std::min(cl, nslabs));
+  }
   TcShape s;
   if (!tc_shape(v.n, l, &s)) return 0;
   const int per_sm = (int)(512 / s.tmem_cols);
-  const long long nslabs = (v.cols() + tc::BJ - 1) / tc::BJ;
   long long groups = (long long)num_sms() * per_sm / s.cparts;
   groups = std::max(1LL, std::min(groups, nslabs));
   return (int)groups;
@@ -459,7 +857,7 @@ int power_tc_groups(View v, int l) {
 size_t power_tc_scratch(View v, int l) {
   TcShape s;
   if (!tc_shape(v.n, l, &s)) return 0;
-  return (size_t)s.nt * 128 * s.l_pad * sizeof(__nv_bfloat16) + 256;
+  return (size_t)s.nt * 128 * std::max(s.l_pad, tc::NC2) * sizeof(__nv_bfloat16) + 256;
 }
 
 cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void* scratch,
@@ -467,15 +865,42 @@ cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void*
   TcShape s;
   if (!tc_shape(v.n, l, &s)) return cudaErrorInvalidValue;
   const int n_pad = s.nt * 128;
+  const bool cluster = use_cluster(v, l);
+  const int l_pad = cluster ? tc::NC2 : s.l_pad;
   __nv_bfloat16* qt = (__nv_bfloat16*)scratch;
   {
-    const long long tot = (long long)n_pad * s.l_pad;
+    const long long tot = (long long)n_pad * l_pad;
     count_kernels(1);
-    tc::k_qt_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Q, (int)v.n, l, n_pad, s.l_pad,
+    tc::k_qt_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Q, (int)v.n, l, n_pad, l_pad,
                                                                   qt);
   }
   CUtensorMap mx, mq;
   if (!make_map_2d(&mx, X, (uint64_t)v.n, (uint64_t)v.cols(), 64, tc::BJ)) return cudaErrorUnknown;
+  if (cluster) {
+    Tc2Shape s2;
+    tc2_shape(v.n, l, &s2);
+    if (!make_map_2d(&mq, qt, (uint64_t)n_pad, (uint64_t)l_pad, 64, tc::NC2))
+      return cudaErrorUnknown;
+    tc::Params2 pr;
+    pr.n = (int)v.n;
+    pr.half = s2.half;
+    pr.nth = s2.nth;
+    pr.cols = v.cols();
+    pr.nslabs = (int)((v.cols() + tc::BJ - 1) / tc::BJ);
+    pr.l_pad = l_pad;
+    pr.tmem_cols = s2.tmem_cols;
+    static bool attr2 = false;
+    if (!attr2) {
+      cudaFuncSetAttribute(tc::k_power_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024 - 2048);
+      attr2 = true;
+    }
+    // one CTA per SM: the shared-memory request keeps a second one away
+    const size_t smem = std::max(s2.smem, (size_t)120 * 1024);
+    count_kernels(1);
+    tc::k_power_tc2<<<2 * groups, tc::THREADS2, smem, st>>>(mx, mq, pr, part, err);
+    return cudaGetLastError();
+  }
   if (!make_map_2d(&mq, qt, (uint64_t)n_pad, (uint64_t)s.l_pad, 64, tc::NC))
     return cudaErrorUnknown;
   tc::Params pr;

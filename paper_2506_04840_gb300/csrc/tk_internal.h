@@ -69,7 +69,7 @@ cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_e
 bool power_tc_supported(View v, int l, const void* X);
 int power_tc_groups(View v, int l);
 size_t power_tc_scratch(View v, int l);
-inline int power_tc_lpad(int l) { return (l + 31) / 32 * 32; }
+int power_tc_lpad(View v, int l);   // row stride of the partials
 cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void* scratch,
                             float* part, int groups, int* err, cudaStream_t st);
 

@@ -208,7 +208,7 @@ static tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, b
       p.shadow = std::max(p.shadow, (size_t)prod(cur) * 2);
       if (v.P == 1) {   // the fused tensor-core pass may run on this mode
         p.part = std::max(p.part, (size_t)power_tc_groups(v, (int)lk) * v.n *
-                                      power_tc_lpad((int)lk) * sizeof(float));
+                                      power_tc_lpad(v, (int)lk) * sizeof(float));
         p.small = std::max(p.small, power_tc_scratch(v, (int)lk));
       }
     }
@@ -310,7 +310,7 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     if (low && power_tc_supported(v, l, Xp)) {
       // one fused tensor-core pass over the bfloat16 copy
       const int groups = power_tc_groups(v, l);
-      const int lp = power_tc_lpad(l);
+      const int lp = power_tc_lpad(v, l);
       {
         ProfScope ps(TK_K_POWER_FUSED, N * 2.0, 4.0 * N * l, st);
         TK_TRY(launch_power_tc(Xp, v, w.Q, l, w.small, (float*)w.part, groups, w.status, st));
@@ -532,7 +532,7 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
   // bfloat16 mode-major tensors take the fused tensor-core pass
   const bool tc = xt == X_BF16 && power_tc_supported(v, l, A->data);
   const int groups = tc ? power_tc_groups(v, l) : 0;
-  const int lp = power_tc_lpad(l);
+  const int lp = power_tc_lpad(v, l);
   Arena b;
   const size_t o_w = b.offset(tc ? 0 : (size_t)v.cols() * l * asize(xt));
   const size_t o_part = b.offset(tc ? (size_t)groups * v.n * lp * sizeof(float)

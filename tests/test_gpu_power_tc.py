@@ -34,6 +34,8 @@ def _bf16_device(A):
     ((400, 30, 30), 8, 30),       # one c-part
     ((136, 37, 11), 6, 16),       # ragged 128-row tile, small l
     ((256, 64, 33), 8, 70),       # three c-parts
+    ((520, 33, 29), 6, 20),       # cluster pair, odd tile count, ragged second half
+    ((768, 50, 21), 8, 64),       # cluster pair, full 64-wide Q
 ])
 @pytest.mark.parametrize("rule", [api.TK_SHIFT_NONE, api.TK_SHIFT_PAPER])
 def test_fused_bf16_power_step(lib, shape, rank, l, rule):
