@@ -51,15 +51,28 @@ WORKLOADS = {
                                             "a bfloat16 copy (precision form)",
                                        shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3,
                                        st=True, dtype="f32", prec=1),
+    "invradius512_bf16power_st": dict(desc="512^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise, r=(50,50,50), "
+                                           "p=10, q=3, precision form (a small profiling case)",
+                                      shape=[512, 512, 512], r=[50, 50, 50], s=10, q=3, st=True,
+                                      dtype="f32", prec=1),
     "hilbert100_fp64_t": dict(desc="100^3 FP64 Hilbert-type 1/(i+j+k-2); randomized T-HOSVD, "
                                    "r=(10,10,10), p=5, q=1", shape=[100, 100, 100],
                               r=[10, 10, 10], s=5, q=1, st=False, dtype="f64", prec=0),
 }
 DEFAULT_WORKLOAD = "tucker400_fp32_st"
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture (see
-# profiles/); None until measured for the current kernel.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (summaries under profiles/); absent = not measured.
+#  * small_svd at 400^3: k_svd_one, n = 400, l = 30 (162,048 B read, 0 written);
+#  * power_fused at 1000^3: k_power_tc2 captured at 512^3 (268.58 MB read,
+#    3.80 MB written), reads scaled by the column count (1000^3 / 512^3) and
+#    the partial writes by the row count (1000 / 512).
+NCU_TRAFFIC = {
+    ("tucker400_fp32_st", "small_svd"): 162048.0,
+    ("invradius512_bf16power_st", "power_fused"): 268.57984e6 + 3.802112e6,
+    ("invradius1000_bf16power_st", "power_fused"): 268.57984e6 * (1000 ** 3 / 512 ** 3) +
+                                                   3.802112e6 * (1000 / 512),
+}
 
 
 def make_input(name, rank=0):
@@ -68,8 +81,8 @@ def make_input(name, rank=0):
     if name.startswith("tucker400"):
         return I.tucker_plus_noise(w["shape"], w["r"], seed=2 + 1000 * rank, noise=1e-4,
                                    decay=0.8, dtype=np.float32)
-    if name.startswith("invradius1000"):
-        return I.inverse_radius(1000, seed=3 + 1000 * rank, noise=1e-6)
+    if name.startswith("invradius"):
+        return I.inverse_radius(w["shape"][0], seed=3 + 1000 * rank, noise=1e-6)
     if name.startswith("hilbert100"):
         return I.hilbert(w["shape"])
     raise KeyError(name)
@@ -330,6 +343,17 @@ def main():
                    "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0)}
                for k, v in kinds.items() if v["launches"]}
 
+    # the shifted-power pass (fused, or the two CUDA-core halves) as HBM GB/s
+    pw = [kinds[k] for k in ("power_fused", "power_w", "power_y") if kinds[k]["launches"]]
+    pw_ms = sum(v["ms"] for v in pw)
+    pw_gbs = ((kinds["power_fused"]["bytes"] + kinds["power_w"]["bytes"]) / (pw_ms / 1e3) / 1e9
+              if pw_ms > 0 else 0.0)
+    power_pass = {"gbs": pw_gbs, "frac_of_measured_hbm": pw_gbs / float(pk["hbm_gbs"]),
+                  "fused_traffic_per_launch": NCU_TRAFFIC.get((args.workload, "power_fused")),
+                  "ms_per_step": pw_ms / args.steps,
+                  "note": "algorithmic bytes of X read once per power step / summed time of "
+                          "the power kernels"}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -342,7 +366,7 @@ def main():
                        "l2": "input (%d MB) larger than L2 (129 MB)" % (Ad.numel() *
                                                                        Ad.element_size() >> 20)
                        if Ad.numel() * Ad.element_size() > 129e6 else "input fits L2"},
-            "roofline": roof, "kernels": kernels,
+            "roofline": roof, "power_pass": power_pass, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "clocks": clk, "gpu_launches": prof["kernels"]}
