@@ -179,6 +179,89 @@ tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, vo
 tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const void* const* U,
                        double* rel_err, void* stream);
 
+/* ---- many independent problems: batched launches and a serving loop ------
+ * The paper treats one tensor at a time; these entry points run Algorithm 3
+ * (shifted randomized ST-HOSVD, modes in natural order, plain precision) on
+ * many tensors at once.  Each step kind runs as ONE launch over a work list
+ * holding every problem's blocks of that step (a persistent grid strides over
+ * them), so uneven shapes share the GPU.  A problem's blocks do exactly the
+ * work the single-problem call does, in the same order: its results are
+ * bitwise those of tucker_rsthosvd (+ tucker_error) on the same arguments,
+ * whatever else shares the launches. */
+typedef struct {
+  tk_tensor A;             /* F64 or F32, device, caller-owned */
+  int r[TK_MAX_D];         /* Tucker rank, 1 <= r_k < n_k */
+  int s[TK_MAX_D];         /* oversampling s_k */
+  int q;                   /* power steps, 0 <= q <= TK_MAX_Q */
+  uint64_t seed;           /* Omega key */
+  uint32_t tag;            /* Omega stream tag, < 2^24 (e.g. the item index) */
+  void* core;              /* out: r_1 x ... x r_d, A's dtype (device) */
+  void* U[TK_MAX_D];       /* out: U[k] n_k x r_k, A's dtype (device) */
+  double* rel_err;         /* out: RE of (core, U) as tucker_error computes
+                              it (one FP64, device), or NULL = not computed */
+} tk_item;
+
+typedef struct tk_batch_s* tk_batch;
+
+/* Plans a batch: validates every item (TK_EINVAL names nothing; check each
+ * item with tucker_rsthosvd's rules), allocates the device workspace and job
+ * tables (owned by the batch) and, if use_graph != 0, captures the launches
+ * into a CUDA graph.  All items share one dtype.  Items must stay valid
+ * (tensors readable, outputs writable) for every run. */
+tk_status tucker_batch_create(const tk_item* items, int count, tk_shift rule, int use_graph,
+                              tk_batch* out);
+/* Runs the batch on `stream` (asynchronous).  Runs of one batch must not
+ * overlap: they share its workspace. */
+tk_status tucker_batch_run(tk_batch b, void* stream);
+/* Waits for the last run and copies each item's device status into
+ * status[count] (host; NULL = skip).  Returns the first non-OK status. */
+tk_status tucker_batch_wait(tk_batch b, int* status);
+/* Launches per run and device bytes the batch holds (host outputs, NULL = skip). */
+tk_status tucker_batch_info(tk_batch b, int64_t* launches, size_t* device_bytes);
+tk_status tucker_batch_destroy(tk_batch b);
+/* One-shot: create (no graph), run on `stream`, wait, destroy. */
+tk_status tucker_batch_rsthosvd(const tk_item* items, int count, tk_shift rule, void* stream);
+
+/* Serving loop.  A worker thread admits submitted requests in arrival order
+ * while their workspace fits in a reserved device pool and fewer than
+ * max_active are in flight, then advances every admitted request by one
+ * phase (sketch, one power step, finish of a mode, error) per tick, each tick
+ * being one batched launch per step kind over all admitted requests; ticks
+ * are pipelined on the server's stream.  A request's result does not depend
+ * on what it shares ticks with (see above). */
+typedef struct {
+  size_t pool_bytes;       /* device pool for request workspaces (0: half of
+                              the free memory at creation) */
+  int max_active;          /* most requests in flight (0: 256) */
+  tk_shift rule;
+} tk_server_opts;
+
+typedef struct {
+  uint64_t id;             /* as returned by tucker_server_submit */
+  int status;              /* tk_status of the request */
+  double submit_s;         /* host clock (seconds since the server started) */
+  double admit_s;
+  double done_s;           /* when the worker saw the request's last tick end */
+} tk_completion;
+
+typedef struct tk_server_s* tk_server;
+
+/* Creates the server on the current device; reserves the pool. */
+tk_status tucker_server_create(const tk_server_opts* o, tk_server* out);
+/* Queues a request (validated here: TK_EINVAL; TK_ENOMEM if its workspace
+ * can never fit the pool).  The item's buffers stay caller-owned and must
+ * stay valid until its completion has been returned by tucker_server_poll. */
+tk_status tucker_server_submit(tk_server s, const tk_item* item, uint64_t* id);
+/* Returns up to `max` completions (host array), oldest first; never blocks. */
+int tucker_server_poll(tk_server s, tk_completion* out, int max);
+/* Blocks until every submitted request has completed or timeout_s passed
+ * (TK_ETIMEOUT). */
+tk_status tucker_server_drain(tk_server s, double timeout_s);
+/* Server clock (seconds since creation), for arrival bookkeeping. */
+double tucker_server_clock(tk_server s);
+/* Finishes the requests in flight, stops the worker, frees the pool. */
+tk_status tucker_server_destroy(tk_server s);
+
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark)
  * When enabled, every launch of the kernel classes below is bracketed by
  * CUDA events recorded on the launch stream, together with the algorithmic

@@ -54,6 +54,21 @@ class tk_profile(ctypes.Structure):
                 ("flops", c_double * 8), ("kernels", c_int64)]
 
 
+class tk_item(ctypes.Structure):
+    _fields_ = [("A", tk_tensor), ("r", c_int * TK_MAX_D), ("s", c_int * TK_MAX_D), ("q", c_int),
+                ("seed", c_uint64), ("tag", c_uint32), ("core", c_void_p),
+                ("U", c_void_p * TK_MAX_D), ("rel_err", c_void_p)]
+
+
+class tk_server_opts(ctypes.Structure):
+    _fields_ = [("pool_bytes", c_size_t), ("max_active", c_int), ("rule", c_int)]
+
+
+class tk_completion(ctypes.Structure):
+    _fields_ = [("id", c_uint64), ("status", c_int), ("submit_s", c_double),
+                ("admit_s", c_double), ("done_s", c_double)]
+
+
 class TuckerError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -83,6 +98,20 @@ SIGNATURES = {
     "tucker_error": (c_int, [ctypes.POINTER(tk_tensor), c_void_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
     "tucker_to_bf16": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+    "tucker_batch_create": (c_int, [ctypes.POINTER(tk_item), c_int, c_int, c_int,
+                                    ctypes.POINTER(c_void_p)]),
+    "tucker_batch_run": (c_int, [c_void_p, c_void_p]),
+    "tucker_batch_wait": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "tucker_batch_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_size_t)]),
+    "tucker_batch_destroy": (c_int, [c_void_p]),
+    "tucker_batch_rsthosvd": (c_int, [ctypes.POINTER(tk_item), c_int, c_int, c_void_p]),
+    "tucker_server_create": (c_int, [ctypes.POINTER(tk_server_opts), ctypes.POINTER(c_void_p)]),
+    "tucker_server_submit": (c_int, [c_void_p, ctypes.POINTER(tk_item),
+                                     ctypes.POINTER(c_uint64)]),
+    "tucker_server_poll": (c_int, [c_void_p, ctypes.POINTER(tk_completion), c_int]),
+    "tucker_server_drain": (c_int, [c_void_p, c_double]),
+    "tucker_server_clock": (c_double, [c_void_p]),
+    "tucker_server_destroy": (c_int, [c_void_p]),
     "tucker_profile_enable": (c_int, [c_int]),
     "tucker_profile_read": (c_int, [ctypes.POINTER(tk_profile)]),
 }
@@ -247,6 +276,99 @@ def tucker_error(A, dims, core, r, U, rel_err, stream=None):
 def tucker_to_bf16(x, out, stream=None):
     _check(load().tucker_to_bf16(_ptr(x), int(x.numel()), _ptr(out), _stream(stream)),
            "tucker_to_bf16")
+
+
+def make_item(A, dims, r, s, q, core, U, rel_err=None, seed=0, tag=0):
+    """tk_item for one problem of a batch or one serving request."""
+    it = tk_item()
+    it.A = tensor_desc(A, dims)
+    d = len(dims)
+    svals = [s] * d if np.isscalar(s) else list(s)
+    for k in range(d):
+        it.r[k] = int(r[k])
+        it.s[k] = int(svals[k])
+        it.U[k] = int(U[k].data_ptr())
+    it.q = int(q)
+    it.seed = int(seed)
+    it.tag = int(tag)
+    it.core = int(core.data_ptr())
+    it.rel_err = None if rel_err is None else int(rel_err.data_ptr())
+    return it
+
+
+def _items(items):
+    arr = (tk_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = it
+    return arr
+
+
+def tucker_batch_create(items, rule=TK_SHIFT_PAPER, use_graph=True):
+    h = c_void_p()
+    _check(load().tucker_batch_create(_items(items), len(items), int(rule), 1 if use_graph else 0,
+                                      ctypes.byref(h)), "tucker_batch_create")
+    return h
+
+
+def tucker_batch_run(h, stream=None):
+    _check(load().tucker_batch_run(h, _stream(stream)), "tucker_batch_run")
+
+
+def tucker_batch_wait(h, count):
+    st = (c_int * count)()
+    status = load().tucker_batch_wait(h, st)
+    return status, [int(x) for x in st]
+
+
+def tucker_batch_info(h):
+    n, b = c_int64(), c_size_t()
+    _check(load().tucker_batch_info(h, ctypes.byref(n), ctypes.byref(b)), "tucker_batch_info")
+    return int(n.value), int(b.value)
+
+
+def tucker_batch_destroy(h):
+    _check(load().tucker_batch_destroy(h), "tucker_batch_destroy")
+
+
+def tucker_batch_rsthosvd(items, rule=TK_SHIFT_PAPER, stream=None):
+    _check(load().tucker_batch_rsthosvd(_items(items), len(items), int(rule), _stream(stream)),
+           "tucker_batch_rsthosvd")
+
+
+def tucker_server_create(pool_bytes=0, max_active=0, rule=TK_SHIFT_PAPER):
+    o = tk_server_opts()
+    o.pool_bytes = int(pool_bytes)
+    o.max_active = int(max_active)
+    o.rule = int(rule)
+    h = c_void_p()
+    _check(load().tucker_server_create(ctypes.byref(o), ctypes.byref(h)), "tucker_server_create")
+    return h
+
+
+def tucker_server_submit(h, item):
+    rid = c_uint64()
+    _check(load().tucker_server_submit(h, ctypes.byref(item), ctypes.byref(rid)),
+           "tucker_server_submit")
+    return int(rid.value)
+
+
+def tucker_server_poll(h, max_n=256):
+    arr = (tk_completion * max_n)()
+    n = load().tucker_server_poll(h, arr, max_n)
+    return [dict(id=int(c.id), status=int(c.status), submit_s=c.submit_s, admit_s=c.admit_s,
+                 done_s=c.done_s) for c in arr[:n]]
+
+
+def tucker_server_drain(h, timeout_s=60.0):
+    _check(load().tucker_server_drain(h, float(timeout_s)), "tucker_server_drain")
+
+
+def tucker_server_clock(h):
+    return float(load().tucker_server_clock(h))
+
+
+def tucker_server_destroy(h):
+    _check(load().tucker_server_destroy(h), "tucker_server_destroy")
 
 
 def tucker_profile_enable(on):

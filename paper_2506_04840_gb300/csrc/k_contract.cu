@@ -15,6 +15,7 @@
 // X(p, i, s) sits at p + P*(i + n*s); column j = p + P*s of X_(k).
 #include <algorithm>
 
+#include "tk_batch.h"
 #include "tk_common.cuh"
 #include "tk_internal.h"
 
@@ -23,11 +24,14 @@ namespace tk {
 constexpr int XB_TJ = 32;   // column chunk of k_xb (FP32 accumulation; FP64 uses 16)
 template <typename TA> struct xb_tj { static constexpr int value = sizeof(TA) == 8 ? 16 : XB_TJ; };
 
+// Block (bx, by) of the product: rows bx*TI.., columns of split by.
 template <typename TX, int LC, int TM, bool OMEGA>
-__global__ void __launch_bounds__(TK_THREADS)
-k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
-     const typename acc_of<TX>::type* __restrict__ W, int l, uint64_t seed, uint32_t tag,
-     int mode, int64_t cols_per_split, typename acc_of<TX>::type* __restrict__ part) {
+__device__ __forceinline__ void xb_body(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
+                                        const typename acc_of<TX>::type* __restrict__ W, int l,
+                                        uint64_t seed, uint32_t tag, int mode,
+                                        int64_t cols_per_split,
+                                        typename acc_of<TX>::type* __restrict__ part,
+                                        unsigned bx, unsigned by) {
   typedef typename acc_of<TX>::type TA;
   constexpr int TN = LC / 16;
   constexpr int TI = 16 * TM;
@@ -39,9 +43,9 @@ k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
 
   const int tid = threadIdx.x;
   const int ti = tid & 15, tc = tid >> 4;
-  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  const int64_t i0 = (int64_t)bx * TI;
   const int64_t ncols = P * S;
-  const int64_t jb = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t jb = (int64_t)by * cols_per_split;
   const int64_t je = min(ncols, jb + cols_per_split);
 
   TA acc[TM][TN];
@@ -106,7 +110,7 @@ k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
     }
     __syncthreads();
   }
-  TA* dst = part + (int64_t)blockIdx.y * n * LC;
+  TA* dst = part + (int64_t)by * n * LC;
 #pragma unroll
   for (int m = 0; m < TM; ++m) {
     const int64_t i = i0 + ti + 16 * m;
@@ -117,13 +121,23 @@ k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
   }
 }
 
+template <typename TX, int LC, int TM, bool OMEGA>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
+     const typename acc_of<TX>::type* __restrict__ W, int l, uint64_t seed, uint32_t tag,
+     int mode, int64_t cols_per_split, typename acc_of<TX>::type* __restrict__ part) {
+  xb_body<TX, LC, TM, OMEGA>(X, P, n, S, W, l, seed, tag, mode, cols_per_split, part, blockIdx.x,
+                             blockIdx.y);
+}
+
 template <typename TA>
-__global__ void k_reduce(const TA* __restrict__ part, int splits, int64_t n, int l, int lc,
-                         const double* __restrict__ Q, const double* __restrict__ alpha,
-                         double* __restrict__ Y) {
+__device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int splits, int64_t n,
+                                            int l, int lc, const double* __restrict__ Q,
+                                            const double* __restrict__ alpha,
+                                            double* __restrict__ Y, unsigned bx) {
   // consecutive threads take consecutive columns c of one row: coalesced
   // reads of the [split][i][c] partials
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = (int64_t)bx * 256 + threadIdx.x;
   if (idx >= n * l) return;
   const int c = (int)(idx % l);
   const int64_t i = idx / l;
@@ -133,14 +147,25 @@ __global__ void k_reduce(const TA* __restrict__ part, int splits, int64_t n, int
   Y[i + n * c] = s;
 }
 
+template <typename TA>
+__global__ void __launch_bounds__(256)
+k_reduce(const TA* __restrict__ part, int splits, int64_t n, int l, int lc,
+         const double* __restrict__ Q, const double* __restrict__ alpha, double* __restrict__ Y) {
+  reduce_body<TA>(part, splits, n, l, lc, Q, alpha, Y, blockIdx.x);
+}
+
 // out[j, c] = sum_i X(p, i, s) B(i, c) for a tile of TJ columns and LC
 // outputs.  EPI = 0 stores out in the (P, m, S) layout; EPI = 1 (S == 1)
 // compares with A(p, c) and accumulates the two squared sums.
+// Block (bx, by) of a gx-wide grid: columns bx*TJ.., outputs by*LC..
 template <typename TX, int LC, int EPI>
-__global__ void __launch_bounds__(TK_THREADS)
-k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* __restrict__ B,
-      int64_t b_ri, int64_t b_cm, int m, typename acc_of<TX>::type* __restrict__ out,
-      const typename acc_of<TX>::type* __restrict__ A, double* __restrict__ err_part) {
+__device__ __forceinline__ void xtb_body(const TX* __restrict__ X, int64_t P, int64_t n,
+                                         int64_t S, const double* __restrict__ B, int64_t b_ri,
+                                         int64_t b_cm, int m,
+                                         typename acc_of<TX>::type* __restrict__ out,
+                                         const typename acc_of<TX>::type* __restrict__ A,
+                                         double* __restrict__ err_part, unsigned bx, unsigned by,
+                                         unsigned gx) {
   typedef typename acc_of<TX>::type TA;
   constexpr int TN = LC / 16;
   constexpr int TMJ = 8;
@@ -157,8 +182,8 @@ k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* _
   const int tj = cfast ? (tid >> 4) : (tid & 15);
   const int tc = cfast ? (tid & 15) : (tid >> 4);
   const int64_t ncols = P * S;
-  const int64_t j0 = (int64_t)blockIdx.x * TJ;
-  const int c0 = blockIdx.y * LC;
+  const int64_t j0 = (int64_t)bx * TJ;
+  const int c0 = by * LC;
 
   if (tid < TJ) {
     const int64_t j = j0 + tid;
@@ -259,25 +284,34 @@ k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* _
         se += red[0][w];
         sa += red[1][w];
       }
-      const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+      const int64_t b = (int64_t)by * gx + bx;
       err_part[2 * b] = se;
       err_part[2 * b + 1] = sa;
     }
   }
 }
 
-__global__ void k_error_final(const double* __restrict__ part, int blocks,
-                              double* __restrict__ rel) {
+template <typename TX, int LC, int EPI>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xtb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S, const double* __restrict__ B,
+      int64_t b_ri, int64_t b_cm, int m, typename acc_of<TX>::type* __restrict__ out,
+      const typename acc_of<TX>::type* __restrict__ A, double* __restrict__ err_part) {
+  xtb_body<TX, LC, EPI>(X, P, n, S, B, b_ri, b_cm, m, out, A, err_part, blockIdx.x, blockIdx.y,
+                        gridDim.x);
+}
+
+__device__ __forceinline__ void error_final_body(const double* __restrict__ part, int blocks,
+                                                 double* __restrict__ rel) {
   __shared__ double se[TK_THREADS], sa[TK_THREADS];
   double e = 0.0, a = 0.0;
-  for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+  for (int b = threadIdx.x; b < blocks; b += TK_THREADS) {
     e += part[2 * b];
     a += part[2 * b + 1];
   }
   se[threadIdx.x] = e;
   sa[threadIdx.x] = a;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = TK_THREADS / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
       se[threadIdx.x] += se[threadIdx.x + o];
       sa[threadIdx.x] += sa[threadIdx.x + o];
@@ -285,6 +319,116 @@ __global__ void k_error_final(const double* __restrict__ part, int blocks,
     __syncthreads();
   }
   if (threadIdx.x == 0) rel[0] = sa[0] > 0.0 ? sqrt(se[0] / sa[0]) : 0.0;
+}
+
+__global__ void __launch_bounds__(TK_THREADS)
+k_error_final(const double* __restrict__ part, int blocks, double* __restrict__ rel) {
+  error_final_body(part, blocks, rel);
+}
+
+// ---------------------------------------------------------------------------
+// Work-list launches: a persistent grid strides over the concatenated blocks
+// of all jobs; each job's block runs the single-problem body unchanged.
+// ---------------------------------------------------------------------------
+template <typename TX, int LC, int TM, bool OMEGA>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xb_batch(const XbJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+           uint32_t total) {
+  typedef typename acc_of<TX>::type TA;
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const XbJob J = jobs[j];
+    const uint32_t lb = b - __ldg(start + j);
+    xb_body<TX, LC, TM, OMEGA>((const TX*)J.X, J.P, J.n, J.S, (const TA*)J.W, J.l, J.seed, J.tag,
+                               J.mode, J.cps, (TA*)J.part, lb % (uint32_t)J.gx,
+                               lb / (uint32_t)J.gx);
+    __syncthreads();
+  }
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(256)
+k_reduce_batch(const ReduceJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+               uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const ReduceJob J = jobs[j];
+    reduce_body<TA>((const TA*)J.part, J.splits, J.n, J.l, J.lc, J.Q, J.alpha, J.Y,
+                    b - __ldg(start + j));
+  }
+}
+
+template <typename TX, int LC, int EPI>
+__global__ void __launch_bounds__(TK_THREADS)
+k_xtb_batch(const XtbJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+            uint32_t total) {
+  typedef typename acc_of<TX>::type TA;
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const XtbJob J = jobs[j];
+    const uint32_t lb = b - __ldg(start + j);
+    xtb_body<TX, LC, EPI>((const TX*)J.X, J.P, J.n, J.S, J.B, J.b_ri, J.b_cm, J.m, (TA*)J.out,
+                          (const TA*)J.A, J.err, lb % (uint32_t)J.gx, lb / (uint32_t)J.gx,
+                          (uint32_t)J.gx);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(TK_THREADS)
+k_error_final_batch(const ErrFinalJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                    int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const ErrFinalJob J = jobs[batch_job(start, njobs, b)];
+    error_final_body(J.part, J.blocks, J.rel);
+    __syncthreads();
+  }
+}
+
+template <typename TX, int EPI>
+static cudaError_t xtb_batch_lc(const BatchLaunch& b, cudaStream_t st) {
+  switch (b.tile) {
+    case 16: return run_batch(k_xtb_batch<TX, 16, EPI>, b, TK_THREADS, st);
+    case 32: return run_batch(k_xtb_batch<TX, 32, EPI>, b, TK_THREADS, st);
+    default: return run_batch(k_xtb_batch<TX, 64, EPI>, b, TK_THREADS, st);
+  }
+}
+
+template <typename TX, bool OMEGA>
+static cudaError_t xb_batch_lc(const BatchLaunch& b, cudaStream_t st) {
+  switch (b.tile) {
+    case 16: return run_batch(k_xb_batch<TX, 16, 8, OMEGA>, b, TK_THREADS, st);
+    case 32: return run_batch(k_xb_batch<TX, 32, 8, OMEGA>, b, TK_THREADS, st);
+    case 64: return run_batch(k_xb_batch<TX, 64, 8, OMEGA>, b, TK_THREADS, st);
+    default: return run_batch(k_xb_batch<TX, 128, 4, OMEGA>, b, TK_THREADS, st);
+  }
+}
+
+template <typename TX>
+static cudaError_t xb_batch_go(const BatchLaunch& b, cudaStream_t st) {
+  return b.flag ? xb_batch_lc<TX, true>(b, st) : xb_batch_lc<TX, false>(b, st);
+}
+
+cudaError_t launch_batch_contract(const BatchLaunch& b, cudaStream_t st) {
+  switch (b.kind) {
+    case BK_XB:
+      if (b.xt == X_F64) return xb_batch_go<double>(b, st);
+      if (b.xt == X_F32) return xb_batch_go<float>(b, st);
+      return xb_batch_go<__nv_bfloat16>(b, st);
+    case BK_REDUCE:
+      if (b.xt == X_F64) return run_batch(k_reduce_batch<double>, b, 256, st);
+      return run_batch(k_reduce_batch<float>, b, 256, st);
+    case BK_XTB:
+      if (b.xt == X_F64)
+        return b.flag ? xtb_batch_lc<double, 1>(b, st) : xtb_batch_lc<double, 0>(b, st);
+      if (b.xt == X_F32)
+        return b.flag ? xtb_batch_lc<float, 1>(b, st) : xtb_batch_lc<float, 0>(b, st);
+      if (b.flag) return cudaErrorInvalidValue;
+      return xtb_batch_lc<__nv_bfloat16, 0>(b, st);
+    case BK_ERRFIN:
+      return run_batch(k_error_final_batch, b, TK_THREADS, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -295,6 +439,14 @@ int xb_lc(int l) { return l <= 16 ? 16 : (l <= 32 ? 32 : (l <= 64 ? 64 : 128)); 
 static int xb_tm(int lc) { return lc <= 64 ? 8 : 4; }
 
 static int xb_ti(int lc) { return 16 * xb_tm(lc); }
+
+int xb_grid_x(View v, int l) { return (int)((v.n + xb_ti(xb_lc(l)) - 1) / xb_ti(xb_lc(l))); }
+
+int64_t xb_cols_per_split(XType xt, View v, int splits) {
+  const int64_t tj = xt == X_F64 ? 16 : XB_TJ;
+  int64_t cps = (v.cols() + splits - 1) / splits;
+  return (cps + tj - 1) / tj * tj;
+}
 
 int xb_splits(View v, int l) {
   const int lc = xb_lc(l);
@@ -365,6 +517,8 @@ cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int
 }
 
 static int xtb_lc(int m) { return m <= 16 ? 16 : (m <= 32 ? 32 : 64); }
+
+int xtb_tile(int m) { return xtb_lc(m); }
 
 template <typename TX, int LC, int EPI>
 static cudaError_t xtb_go(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,

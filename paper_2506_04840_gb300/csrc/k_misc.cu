@@ -1,6 +1,7 @@
 // Small elementwise kernels: Omega tiles for inspection, the bfloat16
 // shadow of the precision form, factor/core copies with type conversion.
 #include "tk_common.cuh"
+#include "tk_batch.h"
 #include "tk_internal.h"
 
 namespace tk {
@@ -71,12 +72,20 @@ cudaError_t launch_to_bf16(const float* x, int64_t count, uint16_t* out, cudaStr
 }
 
 template <typename TO>
-__global__ void k_copy_matrix(const double* __restrict__ src, int64_t lds, TO* __restrict__ dst,
-                              int64_t ldd, int64_t rows, int64_t cols) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void copy_matrix_body(const double* __restrict__ src, int64_t lds,
+                                                 TO* __restrict__ dst, int64_t ldd, int64_t rows,
+                                                 int64_t cols, unsigned bx) {
+  const int64_t idx = (int64_t)bx * 256 + threadIdx.x;
   if (idx >= rows * cols) return;
   const int64_t i = idx % rows, c = idx / rows;
   dst[i + ldd * c] = (TO)src[i + lds * c];
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(256)
+k_copy_matrix(const double* __restrict__ src, int64_t lds, TO* __restrict__ dst, int64_t ldd,
+              int64_t rows, int64_t cols) {
+  copy_matrix_body<TO>(src, lds, dst, ldd, rows, cols, blockIdx.x);
 }
 
 cudaError_t launch_copy_matrix(const double* src, int64_t ld_src, void* dst, int64_t ld_dst,
@@ -90,6 +99,52 @@ cudaError_t launch_copy_matrix(const double* src, int64_t ld_src, void* dst, int
   else
     k_copy_matrix<float><<<blocks, 256, 0, st>>>(src, ld_src, (float*)dst, ld_dst, rows, cols);
   return cudaGetLastError();
+}
+
+// ROUND: the FP64 destination receives the value rounded to FP32 first (an
+// FP64 copy of a factor returned in FP32).
+template <typename TO, bool ROUND>
+__global__ void __launch_bounds__(256)
+k_copy_batch(const CopyJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+             uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const CopyJob J = jobs[j];
+    const int64_t idx = (int64_t)(b - __ldg(start + j)) * 256 + threadIdx.x;
+    if (ROUND) {
+      if (idx < J.rows * J.cols) {
+        const int64_t i = idx % J.rows, c = idx / J.rows;
+        ((TO*)J.dst)[i + J.ldd * c] = (TO)(float)J.src[i + J.lds * c];
+      }
+    } else {
+      copy_matrix_body<TO>(J.src, J.lds, (TO*)J.dst, J.ldd, J.rows, J.cols,
+                           b - __ldg(start + j));
+    }
+  }
+}
+
+cudaError_t launch_batch_misc(const BatchLaunch& b, cudaStream_t st) {
+  if (b.kind != BK_COPY) return cudaErrorInvalidValue;
+  if (b.xt == X_F64)
+    return b.flag ? run_batch(k_copy_batch<double, true>, b, 256, st)
+                  : run_batch(k_copy_batch<double, false>, b, 256, st);
+  return run_batch(k_copy_batch<float, false>, b, 256, st);
+}
+
+cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
+  switch (b.kind) {
+    case BK_XB:
+    case BK_REDUCE:
+    case BK_XTB:
+    case BK_ERRFIN:
+      return launch_batch_contract(b, st);
+    case BK_SVD:
+    case BK_GRAM:
+    case BK_POLISH:
+      return launch_batch_small(b, st);
+    default:
+      return launch_batch_misc(b, st);
+  }
 }
 
 cudaError_t launch_copy_tensor(const void* src, void* dst, int64_t count, XType dt,

@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "tk_common.cuh"
+#include "tk_batch.h"
 #include "tk_internal.h"
 
 namespace tk {
@@ -357,11 +358,13 @@ __device__ void sign_fix_block(double* Q, int64_t n, int l) {
 // smem: A (n*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_svd_one(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
-                          double* __restrict__ sigma, int shift_rule, int update_shift,
-                          int basis_only, double* __restrict__ alpha,
-                          double* __restrict__ alpha_hist, double* __restrict__ sigl_hist,
-                          int* __restrict__ status) {
+__device__ __forceinline__ void svd_one_body(const double* __restrict__ Y, int n, int l,
+                                             double* __restrict__ Q, double* __restrict__ sigma,
+                                             int shift_rule, int update_shift, int basis_only,
+                                             double* __restrict__ alpha,
+                                             double* __restrict__ alpha_hist,
+                                             double* __restrict__ sigl_hist,
+                                             int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* J = A + (int64_t)n * l;
@@ -424,6 +427,16 @@ __global__ void k_svd_one(const double* __restrict__ Y, int n, int l, double* __
   }
   if (tid == 0 && update_shift)
     shift_update((double)sg[perm[l - 1]] / scale, shift_rule, alpha, alpha_hist, sigl_hist);
+}
+
+template <typename T>
+__global__ void k_svd_one(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
+                          double* __restrict__ sigma, int shift_rule, int update_shift,
+                          int basis_only, double* __restrict__ alpha,
+                          double* __restrict__ alpha_hist, double* __restrict__ sigl_hist,
+                          int* __restrict__ status) {
+  svd_one_body<T>(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha, alpha_hist,
+                  sigl_hist, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -578,11 +591,11 @@ __global__ void k_sign(double* __restrict__ Q, int64_t n, int l, int Pb,
 // ---------------------------------------------------------------------------
 constexpr int kPolishRows = 64;
 
-__global__ void k_gram_part(const double* __restrict__ U, int64_t n, int r,
-                            double* __restrict__ part) {
+__device__ __forceinline__ void gram_part_body(const double* __restrict__ U, int64_t n, int r,
+                                               double* __restrict__ part, unsigned bx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Ub = reinterpret_cast<double*>(smem_raw);     // kPolishRows x r
-  const int b = blockIdx.x;
+  const int b = (int)bx;
   const int64_t r0 = (int64_t)b * kPolishRows;
   const int rows = (int)min((int64_t)kPolishRows, n - r0);
   for (int e = threadIdx.x; e < kPolishRows * r; e += blockDim.x) {
@@ -599,15 +612,21 @@ __global__ void k_gram_part(const double* __restrict__ U, int64_t n, int r,
   }
 }
 
+__global__ void k_gram_part(const double* __restrict__ U, int64_t n, int r,
+                            double* __restrict__ part) {
+  gram_part_body(U, n, r, part, blockIdx.x);
+}
+
 // smem: R (r*r) | block rows (kPolishRows*r)
-__global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
-                         const double* __restrict__ part, int* __restrict__ status) {
+__device__ __forceinline__ void polish_body(double* __restrict__ U, int64_t n, int r, int nblk,
+                                            const double* __restrict__ part,
+                                            int* __restrict__ status, unsigned bx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* R = reinterpret_cast<double*>(smem_raw);
   double* Ub = R + (int64_t)r * r;
   __shared__ int bad;
   const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.x * kPolishRows;
+  const int64_t r0 = (int64_t)bx * kPolishRows;
   const int rows = (int)min((int64_t)kPolishRows, n - r0);
   if (tid == 0) bad = 0;
   for (int e = tid; e < r * r; e += blockDim.x) {
@@ -638,7 +657,7 @@ __global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
     __syncthreads();
   }
   if (bad) {
-    if (tid == 0 && blockIdx.x == 0) atomicExch(status, (int)TK_EBREAKDOWN);
+    if (tid == 0 && bx == 0) atomicExch(status, (int)TK_EBREAKDOWN);
     return;
   }
   // rows of this block: u <- u R^{-1} (forward substitution on R^T), in smem
@@ -654,6 +673,11 @@ __global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
     const int i = e % kPolishRows, c = e / kPolishRows;
     if (i < rows) U[(r0 + i) + n * c] = Ub[e];
   }
+}
+
+__global__ void k_polish(double* __restrict__ U, int64_t n, int r, int nblk,
+                         const double* __restrict__ part, int* __restrict__ status) {
+  polish_body(U, n, r, nblk, part, status, blockIdx.x);
 }
 
 size_t polish_scratch(int64_t n, int r) {
@@ -763,6 +787,76 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
                                                       colidx);
   k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Work-list launches (one CTA per svd job; polish as in launch_polish).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                            int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const SvdJob J = jobs[batch_job(start, njobs, b)];
+    svd_one_body<T>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
+                    J.alpha, J.ahist, J.shist, J.status);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_gram_batch(const GramJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+             uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const GramJob J = jobs[j];
+    gram_part_body(J.U, J.n, J.r, J.part, b - __ldg(start + j));
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(64)
+k_polish_batch(const PolishJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+               uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const PolishJob J = jobs[j];
+    polish_body(J.U, J.n, J.r, J.nblk, J.part, J.status, b - __ldg(start + j));
+    __syncthreads();
+  }
+}
+
+int svd_threads(int64_t n, int l) { return (int64_t)n * l >= 4096 ? 1024 : 256; }
+size_t svd_smem(int64_t n, int l, bool fp64) { return one_smem(n, l, fp64 ? 8 : 4); }
+int polish_blocks(int64_t n) { return (int)((n + kPolishRows - 1) / kPolishRows); }
+size_t gram_smem(int r) { return (size_t)kPolishRows * r * sizeof(double); }
+size_t polish_smem(int r) { return ((size_t)r * r + (size_t)kPolishRows * r) * sizeof(double); }
+
+// Raises the dynamic shared-memory limit of the work-list kernels (once per
+// process; call before capturing launches into a graph).
+void batch_kernels_init() {
+  static bool attr = false;
+  if (attr) return;
+  const int mx = (int)kSmemBudget + 4096;
+  cudaFuncSetAttribute(k_svd_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_svd_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_gram_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_polish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  attr = true;
+}
+
+cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
+  batch_kernels_init();
+  switch (b.kind) {
+    case BK_SVD:
+      if (b.xt == X_F64) return run_batch(k_svd_batch<double>, b, b.tile, st);
+      return run_batch(k_svd_batch<float>, b, b.tile, st);
+    case BK_GRAM:
+      return run_batch(k_gram_batch, b, 256, st);
+    case BK_POLISH:
+      return run_batch(k_polish_batch, b, 64, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,

@@ -1,0 +1,145 @@
+// Work-list ("batched") launches: one launch runs the same step kind for many
+// independent problems.  Each job is one problem's launch of that step (its
+// grid given by `blocks`); a launch's blocks are the concatenation of its
+// jobs' blocks, and a persistent grid strides over them.  A job computes
+// exactly what the single-problem launch of that step computes, with the same
+// block decomposition, so its result does not depend on what else shares the
+// launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "tk_internal.h"
+
+namespace tk {
+
+// Y_part = X_(k) B (B = Omega_k when W == NULL), grid gx x splits.
+struct XbJob {
+  const void* X;
+  int64_t P, n, S;
+  const void* W;
+  int64_t cps;          // columns per split (multiple of the column chunk)
+  void* part;
+  uint64_t seed;
+  uint32_t tag;
+  int l, mode, gx;
+};
+
+// Y = sum of partials - alpha Q, grid ceil(n l / 256).
+struct ReduceJob {
+  const void* part;
+  int64_t n;
+  const double* Q;
+  const double* alpha;
+  double* Y;
+  int splits, l, lc;
+};
+
+// svd of an n x l iterate in one CTA (+ shift update), grid 1.
+struct SvdJob {
+  const double* Y;
+  double* Q;
+  double* sigma;
+  double* alpha;
+  double* ahist;
+  double* shist;
+  int* status;
+  int n, l, shift_rule, update_shift, basis_only;
+};
+
+// out = X x_k B^T (EPI 0) or the fused error expansion (EPI 1), grid gx x gy.
+struct XtbJob {
+  const void* X;
+  int64_t P, n, S;
+  const double* B;
+  int64_t b_ri, b_cm;
+  void* out;
+  const void* A;
+  double* err;
+  int m, gx;
+};
+
+// CholeskyQR polish of an n x r factor: Gram partials, then the update.
+struct GramJob {
+  const double* U;
+  double* part;
+  int64_t n;
+  int r;
+};
+struct PolishJob {
+  double* U;
+  const double* part;
+  int* status;
+  int64_t n;
+  int r, nblk;
+};
+
+// dst (rows x cols) = src converted to the destination type.
+struct CopyJob {
+  const double* src;
+  void* dst;
+  int64_t lds, ldd, rows, cols;
+};
+
+// rel = sqrt(sum e^2 / sum a^2) over `blocks` partial pairs, grid 1.
+struct ErrFinalJob {
+  const double* part;
+  double* rel;
+  int blocks;
+};
+
+enum BatchKind { BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN };
+
+constexpr size_t kJobBytes = 128;   // every job struct fits
+
+struct BatchLaunch {
+  int kind;           // BatchKind
+  int xt;             // XType of the data (copy: of the destination)
+  int tile;           // xb / xtb: column tile LC; svd: threads per CTA
+  int flag;           // xb: 1 = Omega; xtb: EPI
+  const void* jobs;   // device array of njobs job structs
+  const uint32_t* start;   // device: first block of each job
+  int njobs;
+  uint32_t total;     // blocks over all jobs
+  size_t smem;        // dynamic shared memory per CTA
+};
+
+cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st);
+void batch_kernels_init();
+// per-file dispatchers
+cudaError_t launch_batch_contract(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_misc(const BatchLaunch& b, cudaStream_t st);
+
+// Per-job launch shapes, as the single-problem launchers choose them.
+int xb_grid_x(View v, int l);
+int64_t xb_cols_per_split(XType xt, View v, int splits);
+int xtb_tile(int m);
+int svd_threads(int64_t n, int l);
+size_t svd_smem(int64_t n, int l, bool fp64);
+int polish_blocks(int64_t n);
+size_t gram_smem(int r);
+size_t polish_smem(int r);
+
+#ifdef __CUDACC__
+// Launch a work-list kernel on a persistent grid: as many CTAs as fit on the
+// GPU at once, but no more than there are blocks of work.
+template <typename Job>
+cudaError_t run_batch(void (*kern)(const Job*, const uint32_t*, int, uint32_t),
+                      const BatchLaunch& b, int threads, cudaStream_t st) {
+  if (b.total == 0 || b.njobs == 0) return cudaSuccess;
+  int per = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, b.smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t cap = (uint64_t)per * (uint64_t)num_sms();
+  const unsigned grid = (unsigned)(b.total < cap ? b.total : cap);
+  count_kernels(1);
+  kern<<<grid, threads, b.smem, st>>>((const Job*)b.jobs, b.start, b.njobs, b.total);
+  return cudaGetLastError();
+}
+#endif
+
+}  // namespace tk

@@ -144,4 +144,17 @@ template <> __device__ __forceinline__ float load_as<float, __nv_bfloat16>(const
 template <typename TX> struct acc_of { typedef float type; };
 template <> struct acc_of<double> { typedef double type; };
 
+// Work-list launches: the job whose block range [start[j], start[j+1])
+// holds block b (start ascending, start[0] == 0).
+__device__ __forceinline__ int batch_job(const uint32_t* __restrict__ start, int njobs,
+                                         uint32_t b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 }  // namespace tk

@@ -1,0 +1,325 @@
+// Compiles one problem of Algorithm 3 into phases of work-list jobs and
+// merges any problems' phases into batched launches (tk_program.h).
+#include <algorithm>
+#include <cstring>
+
+#include "tk_program.h"
+
+namespace tk {
+
+namespace {
+
+template <typename J>
+Op make_op(int pos, int prof, int kind, XType xt, int tile, int flag, size_t smem,
+           uint32_t blocks, double bytes, double flops, const J& job) {
+  static_assert(sizeof(J) <= kJobBytes, "job struct too large");
+  Op o;
+  std::memset(&o, 0, sizeof(o));
+  o.pos = pos;
+  o.prof = prof;
+  o.key.kind = kind;
+  o.key.xt = (int)xt;
+  o.key.tile = tile;
+  o.key.flag = flag;
+  o.key.smem = smem;
+  o.blocks = blocks;
+  o.bytes = bytes;
+  o.flops = flops;
+  std::memcpy(o.job, &job, sizeof(J));
+  return o;
+}
+
+size_t job_size(int kind) {
+  switch (kind) {
+    case BK_XB: return sizeof(XbJob);
+    case BK_REDUCE: return sizeof(ReduceJob);
+    case BK_SVD: return sizeof(SvdJob);
+    case BK_XTB: return sizeof(XtbJob);
+    case BK_GRAM: return sizeof(GramJob);
+    case BK_POLISH: return sizeof(PolishJob);
+    case BK_COPY: return sizeof(CopyJob);
+    default: return sizeof(ErrFinalJob);
+  }
+}
+
+uint32_t cdiv(int64_t a, int64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+// Extra per-problem buffers beyond the single-call workspace.
+struct Extras {
+  size_t state, qd[TK_MAX_D], tb[2], ep;
+  int eblocks;
+};
+
+size_t layout(const tk_item& it, const HosvdPlan& p, Extras* ex) {
+  Arena a;
+  const size_t hos = carve(p, nullptr, nullptr);
+  a.offset(hos);
+  ex->state = a.offset(sizeof(ItemState));
+  ex->eblocks = 0;
+  ex->tb[0] = ex->tb[1] = ex->ep = 0;
+  for (int k = 0; k < TK_MAX_D; ++k) ex->qd[k] = 0;
+  if (it.rel_err) {
+    const int d = p.d;
+    const size_t es = xsize(p.xt);
+    for (int k = 0; k < d; ++k) ex->qd[k] = a.offset((size_t)p.n[k] * p.r[k] * sizeof(double));
+    std::vector<int64_t> cur(p.r.begin(), p.r.end());
+    size_t tbuf = 0;
+    for (int k = 0; k < d - 1; ++k) {
+      cur[k] = p.n[k];
+      tbuf = std::max(tbuf, (size_t)prod(cur) * es);
+    }
+    ex->tb[0] = a.offset(tbuf);
+    ex->tb[1] = a.offset(tbuf);
+    std::vector<int64_t> last(p.r.begin(), p.r.end());
+    for (int k = 0; k < d - 1; ++k) last[k] = p.n[k];
+    ex->eblocks = xtb_error_blocks(view_of(last, d - 1), (int)p.n[d - 1]);
+    ex->ep = a.offset((size_t)ex->eblocks * 2 * sizeof(double));
+  }
+  return al(a.off);
+}
+
+}  // namespace
+
+tk_status problem_plan(const tk_item& it, tk_shift rule, Problem* pr) {
+  if (it.A.dtype != TK_F32 && it.A.dtype != TK_F64) return TK_EINVAL;
+  if (!it.core) return TK_EINVAL;
+  for (int k = 0; k < it.A.d && k < TK_MAX_D; ++k)
+    if (!it.U[k]) return TK_EINVAL;
+  tk_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.q = it.q;
+  for (int k = 0; k < TK_MAX_D; ++k) o.s[k] = it.s[k];
+  o.seed = it.seed;
+  o.tag = it.tag;
+  o.shift = rule;
+  o.prec = TK_PREC_PLAIN;
+  o.order[0] = -1;
+  tk_status s = make_plan(&it.A, it.r, &o, true, pr->p);
+  if (s != TK_OK) return s;
+  for (int k = 0; k < pr->p.d; ++k)
+    if (pr->p.sp[k].Pb != 1) return TK_ENOTIMPL;   // one-CTA svd only
+  Extras ex;
+  pr->ws_bytes = layout(it, pr->p, &ex);
+  return TK_OK;
+}
+
+tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
+  const HosvdPlan& p = pr->p;
+  Extras ex;
+  layout(it, p, &ex);
+  carve(p, base, &pr->w);
+  HosvdWs& w = pr->w;
+  ItemState* stt = (ItemState*)(base + ex.state);
+  pr->state = stt;
+  w.status = &stt->status;
+  const XType xt = p.xt;
+  const bool fp64 = xt == X_F64;
+  const size_t es = xsize(xt);
+  const int d = p.d;
+  double* qd[TK_MAX_D] = {nullptr};
+  if (it.rel_err)
+    for (int k = 0; k < d; ++k) qd[k] = (double*)(base + ex.qd[k]);
+  std::vector<Phase>& prog = pr->prog;
+  prog.clear();
+  pr->slot.clear();
+  const int per_step = TK_MAX_Q + 2;
+
+  const void* X = it.A.data;
+  std::vector<int64_t> cur = p.n;
+  int pp = 0;
+  for (int step = 0; step < d; ++step) {
+    const int k = p.order[step];
+    const View v = view_of(cur, k);
+    const int l = p.l[k];
+    const int lc = xb_lc(l);
+    const int splits = xb_splits(v, l);
+    const int gx = xb_grid_x(v, l);
+    const int64_t cps = xb_cols_per_split(xt, v, splits);
+    const double N = (double)v.P * (double)v.n * (double)v.S;
+    const double nl = (double)v.n * l;
+    const double red_bytes = (double)splits * v.n * lc * asize(xt) + nl * 8.0;
+    const double svd_flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
+    const XType acc = fp64 ? X_F64 : X_F32;
+    double* sig = stt->sig + (size_t)k * TK_MAX_L;
+    double* alpha = stt->alpha + k;
+    const int sthreads = svd_threads(v.n, l);
+    const size_t ssmem = svd_smem(v.n, l, fp64);
+    const int xtile = xtb_tile(l);
+    const int xgx = (int)cdiv(v.cols(), 128);
+
+    // ---- sketch phase
+    {
+      Phase ph;
+      XbJob xb{X, v.P, v.n, v.S, nullptr, cps, w.part, it.seed, it.tag, l, k, gx};
+      ph.push_back(make_op(0, TK_K_SKETCH, BK_XB, xt, lc, 1, 0, (uint32_t)gx * splits, N * es,
+                           2.0 * N * l, xb));
+      ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc};
+      ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
+                           red_bytes, (double)splits * nl, rd));
+      SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,
+                0, p.q >= 1 ? 1 : 0};
+      ph.push_back(make_op(2, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+                           2.0 * nl * 8.0, svd_flops, sv));
+      prog.push_back(ph);
+      pr->slot.push_back(step * per_step);
+    }
+    // ---- power phases
+    for (int t = 1; t <= p.q; ++t) {
+      Phase ph;
+      XtbJob xw{X, v.P, v.n, v.S, w.Q, 1, v.n, w.w, nullptr, nullptr, l, xgx};
+      ph.push_back(make_op(0, TK_K_POWER_W, BK_XTB, xt, xtile, 0, 0,
+                           (uint32_t)xgx * cdiv(l, xtile), N * es, 2.0 * N * l, xw));
+      XbJob xy{X, v.P, v.n, v.S, w.w, cps, w.part, it.seed, it.tag, l, k, gx};
+      ph.push_back(make_op(1, TK_K_POWER_Y, BK_XB, xt, lc, 0, 0, (uint32_t)gx * splits, N * es,
+                           2.0 * N * l, xy));
+      ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc};
+      ph.push_back(make_op(2, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
+                           red_bytes, (double)splits * nl, rd));
+      SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
+                stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,
+                (int)p.rule, 1, 0};
+      ph.push_back(make_op(3, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+                           2.0 * nl * 8.0, svd_flops, sv));
+      prog.push_back(ph);
+      pr->slot.push_back(step * per_step + t);
+    }
+    // ---- finish phase: U_k, TTM shrink
+    {
+      Phase ph;
+      const int r = p.r[k];
+      if (!fp64) {
+        const int nblk = polish_blocks(v.n);
+        GramJob gj{w.Q, (double*)w.small, v.n, r};
+        ph.push_back(make_op(0, TK_K_CONVERT, BK_GRAM, X_F64, 0, 0, gram_smem(r),
+                             (uint32_t)nblk, 2.0 * v.n * r * 8.0, 2.0 * v.n * r * r, gj));
+        PolishJob pj{w.Q, (const double*)w.small, w.status, v.n, r, nblk};
+        ph.push_back(make_op(1, TK_K_CONVERT, BK_POLISH, X_F64, 0, 0, polish_smem(r),
+                             (uint32_t)nblk, 0.0, 0.0, pj));
+      }
+      CopyJob cu{w.Q, it.U[k], v.n, v.n, v.n, r};
+      ph.push_back(make_op(2, TK_K_CONVERT, BK_COPY, xt, 0, 0, 0, cdiv(v.n * r, 256),
+                           (double)v.n * r * (8.0 + es), 0.0, cu));
+      if (qd[k]) {
+        // the error pass reads the returned factor (rounded to A's dtype)
+        CopyJob cq{w.Q, qd[k], v.n, v.n, v.n, r};
+        ph.push_back(make_op(2, TK_K_CONVERT, BK_COPY, X_F64, 0, fp64 ? 0 : 1, 0,
+                             cdiv(v.n * r, 256), (double)v.n * r * 16.0, 0.0, cq));
+      }
+      void* out = (step == d - 1) ? it.core : w.g[pp];
+      const int mt = xtb_tile(r);
+      XtbJob tt{X, v.P, v.n, v.S, w.Q, 1, v.n, out, nullptr, nullptr, r, xgx};
+      ph.push_back(make_op(3, TK_K_TTM, BK_XTB, xt, mt, 0, 0, (uint32_t)xgx * cdiv(r, mt),
+                           (N + N / v.n * r) * es, 2.0 * N * r, tt));
+      prog.push_back(ph);
+      pr->slot.push_back(step * per_step + TK_MAX_Q + 1);
+      X = out;
+      pp ^= 1;
+      cur[k] = r;
+    }
+  }
+  // ---- error phase (tucker_error on the returned core and factors)
+  if (it.rel_err) {
+    Phase ph;
+    std::vector<int64_t> dims(p.r.begin(), p.r.end());
+    const void* Xe = it.core;
+    void* tb[2] = {base + ex.tb[0], base + ex.tb[1]};
+    for (int k = 0; k < d - 1; ++k) {
+      const View v = view_of(dims, k);
+      const int m = (int)p.n[k];
+      const int mt = xtb_tile(m);
+      const int egx = (int)cdiv(v.cols(), 128);
+      const double cin = (double)v.P * v.n * v.S;
+      XtbJob ej{Xe, v.P, v.n, v.S, qd[k], p.n[k], 1, tb[k & 1], nullptr, nullptr, m, egx};
+      ph.push_back(make_op(k, TK_K_ERROR, BK_XTB, xt, mt, 0, 0, (uint32_t)egx * cdiv(m, mt),
+                           (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n, ej));
+      Xe = tb[k & 1];
+      dims[k] = p.n[k];
+    }
+    const View vl = view_of(dims, d - 1);
+    const int m = (int)p.n[d - 1];
+    const int mt = xtb_tile(m);
+    const int egx = (int)cdiv(vl.cols(), 128);
+    const double Nf = (double)vl.P * (double)m;
+    double* ep = (double*)(base + ex.ep);
+    XtbJob ej{Xe, vl.P, vl.n, vl.S, qd[d - 1], p.n[d - 1], 1, nullptr, it.A.data, ep, m, egx};
+    ph.push_back(make_op(d - 1, TK_K_ERROR, BK_XTB, xt, mt, 1, 0, (uint32_t)egx * cdiv(m, mt),
+                         Nf * es + (double)vl.P * vl.n * es, 2.0 * Nf * vl.n, ej));
+    ErrFinalJob fj{ep, it.rel_err, ex.eblocks};
+    ph.push_back(make_op(d, TK_K_ERROR, BK_ERRFIN, X_F64, 0, 0, 0, 1, 0.0, 0.0, fj));
+    prog.push_back(ph);
+    pr->slot.push_back(TK_MAX_D * per_step);
+  }
+  return TK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Merging.
+// ---------------------------------------------------------------------------
+static bool key_less(const Op* a, const Op* b) {
+  if (a->pos != b->pos) return a->pos < b->pos;
+  if (a->prof != b->prof) return a->prof < b->prof;
+  if (a->key.kind != b->key.kind) return a->key.kind < b->key.kind;
+  if (a->key.xt != b->key.xt) return a->key.xt < b->key.xt;
+  if (a->key.tile != b->key.tile) return a->key.tile < b->key.tile;
+  return a->key.flag < b->key.flag;
+}
+
+static bool key_eq(const Op* a, const Op* b) { return !key_less(a, b) && !key_less(b, a); }
+
+static size_t blob_take(std::vector<unsigned char>& blob, size_t bytes) {
+  const size_t off = (blob.size() + 15) & ~(size_t)15;
+  blob.resize(off + bytes);
+  return off;
+}
+
+void merge_ops(const std::vector<const Op*>& ops_in, std::vector<unsigned char>& blob,
+               std::vector<LaunchRec>& out) {
+  std::vector<const Op*> ops(ops_in);
+  std::stable_sort(ops.begin(), ops.end(), key_less);
+  size_t i = 0;
+  while (i < ops.size()) {
+    size_t j = i + 1;
+    while (j < ops.size() && key_eq(ops[i], ops[j])) ++j;
+    LaunchRec r;
+    std::memset(&r, 0, sizeof(r));
+    r.b = ops[i]->key;
+    r.prof = ops[i]->prof;
+    const size_t js = job_size(r.b.kind);
+    const int nj = (int)(j - i);
+    r.jobs_off = blob_take(blob, js * nj);
+    r.start_off = blob_take(blob, sizeof(uint32_t) * nj);
+    uint32_t total = 0;
+    size_t smem = 0;
+    for (int t = 0; t < nj; ++t) {
+      const Op* o = ops[i + t];
+      std::memcpy(blob.data() + r.jobs_off + js * t, o->job, js);
+      std::memcpy(blob.data() + r.start_off + sizeof(uint32_t) * t, &total, sizeof(uint32_t));
+      total += o->blocks;
+      smem = std::max(smem, o->key.smem);
+      r.bytes += o->bytes;
+      r.flops += o->flops;
+    }
+    r.b.njobs = nj;
+    r.b.total = total;
+    r.b.smem = smem;
+    out.push_back(r);
+    i = j;
+  }
+}
+
+void resolve(std::vector<LaunchRec>& recs, const unsigned char* dev_blob) {
+  for (auto& r : recs) {
+    r.b.jobs = dev_blob + r.jobs_off;
+    r.b.start = (const uint32_t*)(dev_blob + r.start_off);
+  }
+}
+
+cudaError_t issue(const LaunchRec& r, cudaStream_t st, bool profile) {
+  if (profile) {
+    ProfScope ps(r.prof, r.bytes, r.flops, st);
+    return launch_batch(r.b, st);
+  }
+  return launch_batch(r.b, st);
+}
+
+}  // namespace tk

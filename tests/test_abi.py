@@ -40,6 +40,9 @@ def test_ctypes_structs_match_header():
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tk_tensor), sizeof(tk_opts), sizeof(tk_stats),
          offsetof(tk_opts, seed), offsetof(tk_opts, workspace), offsetof(tk_stats, sigma));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tk_item), offsetof(tk_item, q),
+         offsetof(tk_item, core), offsetof(tk_item, rel_err), sizeof(tk_server_opts),
+         sizeof(tk_completion), offsetof(tk_completion, done_s));
   return 0;
 }
 """
@@ -50,7 +53,10 @@ int main(void) {
         subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     want = [ctypes.sizeof(api.tk_tensor), ctypes.sizeof(api.tk_opts), ctypes.sizeof(api.tk_stats),
-            api.tk_opts.seed.offset, api.tk_opts.workspace.offset, api.tk_stats.sigma.offset]
+            api.tk_opts.seed.offset, api.tk_opts.workspace.offset, api.tk_stats.sigma.offset,
+            ctypes.sizeof(api.tk_item), api.tk_item.q.offset, api.tk_item.core.offset,
+            api.tk_item.rel_err.offset, ctypes.sizeof(api.tk_server_opts),
+            ctypes.sizeof(api.tk_completion), api.tk_completion.done_s.offset]
     assert [int(x) for x in out] == want
 
 
@@ -129,3 +135,30 @@ def test_workspace_size_is_host_only_and_monotone():
     bad = (ctypes.c_int * 3)(80, 5, 5)
     assert lib.tucker_workspace_size(ctypes.byref(_fake_tensor([80, 80, 80])), bad,
                                      ctypes.byref(api.make_opts(3, 2, 5)), 1) == 0
+
+
+def test_batch_validation_before_allocation():
+    """A batch with an invalid item is rejected on the host (nothing is
+    allocated or launched): rank >= size, mixed dtypes, bad shift rule."""
+    lib = api.load()
+
+    def item(dims, r, dtype=api.TK_F32):
+        it = api.tk_item()
+        it.A = _fake_tensor(dims, dtype)
+        for k in range(len(dims)):
+            it.r[k] = r[k]
+            it.s[k] = 2
+            it.U[k] = 0x2000
+        it.q = 1
+        it.core = 0x3000
+        return it
+
+    h = ctypes.c_void_p()
+    good = item([10, 9, 8], [3, 3, 3])
+    bad_rank = item([10, 9, 8], [3, 9, 3])
+    other = item([10, 9, 8], [3, 3, 3], api.TK_F64)
+    for items, rule in (([good, bad_rank], 0), ([good, other], 0), ([good], 7)):
+        arr = (api.tk_item * len(items))(*items)
+        assert lib.tucker_batch_create(arr, len(items), rule, 0, ctypes.byref(h)) == api.TK_EINVAL
+        assert not h.value
+    assert lib.tucker_batch_create(None, 0, 0, 0, ctypes.byref(h)) == api.TK_EINVAL

@@ -1,0 +1,135 @@
+"""Batched problems (one launch per step kind over a work list, optionally
+under a CUDA graph).
+
+Every item's job blocks run the single-problem kernels' bodies with the same
+block decomposition, so a batch must reproduce tucker_rsthosvd +
+tucker_error on each item BITWISE, whatever the batch holds; and, through
+them, the oracle (Algorithm 3 in FP64) within the FP32 path's tolerances.
+"""
+import numpy as np
+import pytest
+
+from oracle import tucker as T
+from paper_2506_04840_gb300 import api
+from paper_2506_04840_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _alloc(A, r, dtype):
+    dims = list(A.shape)
+    core = torch.full((int(np.prod(r)),), float("nan"), dtype=dtype, device="cuda")
+    U = [torch.full((dims[k] * r[k],), float("nan"), dtype=dtype, device="cuda")
+         for k in range(A.ndim)]
+    rel = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    return core, U, rel
+
+
+def _single(A, r, s, q, tag, rule=api.TK_SHIFT_PAPER):
+    dt = torch.float64 if A.dtype == np.float64 else torch.float32
+    Ad = api.to_device(A)
+    core, U, rel = _alloc(A, r, dt)
+    opts = api.make_opts(A.ndim, q, s, seed=0, tag=tag, shift=rule)
+    api.tucker_rsthosvd(Ad, list(A.shape), r, opts, core, U)
+    api.tucker_error(Ad, list(A.shape), core, r, U, rel)
+    torch.cuda.synchronize()
+    return core.cpu(), [u.cpu() for u in U], rel.cpu()
+
+
+def _instances(count, seed, dtype=np.float32):
+    out = []
+    for i, (A, r) in enumerate(I.batch_instances(count, seed, lo=6, hi=36, rank_lo=2, rank_hi=6,
+                                                 dtype=dtype)):
+        out.append((A, r, 3, [0, 1, 2][i % 3]))
+    return out
+
+
+def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1):
+    dt = torch.float64 if insts[0][0].dtype == np.float64 else torch.float32
+    keep, items = [], []
+    for i, (A, r, s, q) in enumerate(insts):
+        Ad = api.to_device(A)
+        core, U, rel = _alloc(A, r, dt)
+        keep.append((Ad, core, U, rel))
+        items.append(api.make_item(Ad, list(A.shape), r, s, q, core, U, rel, seed=0, tag=i))
+    h = api.tucker_batch_create(items, rule, use_graph)
+    try:
+        outs = []
+        for _ in range(runs):
+            api.tucker_batch_run(h)
+            status, per = api.tucker_batch_wait(h, len(items))
+            assert status == api.TK_OK and per == [0] * len(items)
+            outs.append([(c.cpu().clone(), [u.cpu().clone() for u in U], rel.cpu().clone())
+                         for (_, c, U, rel) in keep])
+        launches, nbytes = api.tucker_batch_info(h)
+    finally:
+        api.tucker_batch_destroy(h)
+    return outs, launches
+
+
+def _same(a, b):
+    ca, Ua, ra = a
+    cb, Ub, rb = b
+    return (torch.equal(ca, cb) and all(torch.equal(x, y) for x, y in zip(Ua, Ub))
+            and torch.equal(ra, rb))
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_calls_bitwise(lib, use_graph):
+    insts = _instances(14, seed=41)
+    outs, launches = _run_batch(insts, use_graph, runs=2)
+    assert _same_all(outs[0], outs[1])          # a replayed run is identical
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+    # one launch per (schedule slot, position, step kind, tile class): far
+    # fewer than the ~40 launches each item's own calls make
+    assert launches < 14 * 8
+
+
+def _same_all(xs, ys):
+    return all(_same(a, b) for a, b in zip(xs, ys))
+
+
+def test_batch_fp64_and_no_shift_bitwise(lib):
+    insts = _instances(6, seed=5, dtype=np.float64)
+    outs, _ = _run_batch(insts, True, rule=api.TK_SHIFT_NONE)
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i, rule=api.TK_SHIFT_NONE)), i
+
+
+def test_batch_matches_oracle(lib):
+    """Each item against Algorithm 3 in FP64 on the same tensor and the same
+    Omega (tag = item index): RE within 1e-6, factors orthonormal to 1e-6,
+    leading separated subspaces within 1e-5."""
+    insts = _instances(9, seed=77)
+    outs, _ = _run_batch(insts, True)
+    for i, (A, r, s, q) in enumerate(insts):
+        core, U, rel = outs[0][i]
+        G, Us, st = T.rsthosvd(A.astype(np.float64), r, [s] * A.ndim, q, seed=0, tag=i)
+        re_o = T.rel_error(A.astype(np.float64), G, Us)
+        assert abs(rel.item() - re_o) <= 1e-6, (i, rel.item(), re_o)
+        for k in range(A.ndim):
+            Ug = U[k].double().numpy().reshape((A.shape[k], r[k]), order="F")
+            assert np.abs(Ug.T @ Ug - np.eye(r[k])).max() <= 1e-6
+            sig = np.asarray(st[k]["sigma"])
+            if q == 0:
+                sig = sig ** 2      # sigma(A Omega) is linear in A: compare squared gaps
+            j = T.separated_block(sig, r[k])
+            if j:
+                tol = 1e-5 if q else 1e-4   # sketch-only factors see FP32 noise at first order
+                assert T.principal_sines(Ug[:, :j], Us[k][:, :j]).max() <= tol, (i, k)
+
+
+def test_batch_many_items_share_the_grid(lib):
+    """More job blocks than resident CTAs: the persistent grid strides over
+    the work list; results still bitwise equal to the single calls."""
+    insts = []
+    for i, (A, r) in enumerate(I.batch_instances(40, seed=9, lo=20, hi=48, rank_lo=3,
+                                                 rank_hi=8)):
+        insts.append((A, r, 4, 2))
+    outs, _ = _run_batch(insts, True)
+    for i in (0, 7, 19, 39):
+        A, r, s, q = insts[i]
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
