@@ -59,6 +59,20 @@ WORKLOADS = {
                                    "r=(10,10,10), p=5, q=1", shape=[100, 100, 100],
                               r=[10, 10, 10], s=5, q=1, st=False, dtype="f64", prec=0),
 }
+WORKLOADS.update({
+    "batch256_fp32_st": dict(desc="256 uneven FP32 instances, order 3 or 4 (1/2 each), sides "
+                                  "U[32,160], core ranks U[4,16] (clamped), N(0,1) core, Haar "
+                                  "factors, 1e-3 relative noise; randomized ST-HOSVD r = core "
+                                  "ranks, p=5, q=2, adaptive shifts, one launch per step kind "
+                                  "(work list) inside one CUDA graph", kind="batch", count=256,
+                             seed=4, s=5, q=2, dtype="f32"),
+    "serve_poisson200": dict(desc="serving loop: Poisson arrivals at 200 req/s of FP32 3-way "
+                                  "tensors, sides from {64,128,256,512,768} per mode, Hilbert-type "
+                                  "or Tucker(+1e-3 noise) content 50/50, ranks U[5,40] (< side), "
+                                  "q in {1,2,3}, p=10; admission by free pool memory",
+                             kind="serve", rate=200.0, duration=60.0, seed=5, s=10,
+                             dtype="f32"),
+})
 DEFAULT_WORKLOAD = "tucker400_fp32_st"
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
@@ -168,8 +182,64 @@ def cpu_baseline(A, w, budget_s=12.0, max_samples=4):
                       % (n, el), "rel_err": re}
 
 
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def _oracle_sample_batch(w, budget_s):
+    """The oracle on the smallest instances of the batch workload (host copies
+    made with the host generator of the same recipe), until budget_s."""
+    from oracle import tucker as T
+    from paper_2506_04840_gb300 import inputs as I
+    specs = sorted(I.batch_specs(w["count"], w["seed"]), key=lambda x: int(np.prod(x[0])))
+    n, t0, re = 0, time.perf_counter(), None
+    for shape, ranks, sub in specs:
+        A = I.tucker_plus_noise(shape, ranks, sub, noise=1e-3, noise_mode="relative",
+                                dtype=np.float32).astype(np.float64)
+        G, Us, _ = T.rsthosvd(A, ranks, w["s"], w["q"])
+        re = T.rel_error(A, G, Us)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n, el, "the %d smallest of the 256 instances (oracle FP64, %.1f s)" % (n, el), re
+
+
+def _oracle_sample_serve(w, budget_s):
+    from oracle import tucker as T
+    from paper_2506_04840_gb300 import inputs as I
+    reqs = sorted(I.serving_requests(400, w["seed"], rate=w["rate"]),
+                  key=lambda r: int(np.prod(r["shape"])))
+    n, t0, re = 0, time.perf_counter(), None
+    for rq in reqs:
+        A = I.request_tensor(rq).astype(np.float64)
+        G, Us, _ = T.rsthosvd(A, rq["ranks"], w["s"], rq["q"])
+        re = T.rel_error(A, G, Us)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n, el, "the %d smallest of 400 requests (oracle FP64, %.1f s)" % (n, el), re
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
+        return 0
+    if w.get("kind") in ("batch", "serve"):
+        fn = _oracle_sample_batch if w["kind"] == "batch" else _oracle_sample_serve
+        fn(w, 1.0)                                   # warm-up
+        n, el, sample, re = fn(w, 20.0)
+        value = n / el
+        line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": args.gpus,
+                "steps": 1, "warmup": 1, "ms_per_step": 1e3 * el, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": args.workload, "desc": w["desc"], "rel_err": re},
+                "cpu_baseline": {"kind": "oracle", "cores": _cores(), "value": value,
+                                 "unit": "tensors/s", "sample": sample},
+                "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return 0
     A = make_input(args.workload)
     for _ in range(args.warmup):
@@ -194,6 +264,242 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def _roofline(prof, pk, pk_src, fp64=False):
+    kinds = prof["kinds"]
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    kd = kinds[dom]
+    avg_s = kd["ms"] / max(kd["launches"], 1) / 1e3
+    per_b = kd["bytes"] / max(kd["launches"], 1)
+    per_f = kd["flops"] / max(kd["launches"], 1)
+    if dom == "power_fused":
+        bound, unit, achieved = "hbm", "GB/s", per_b / avg_s / 1e9
+        peak, note = float(pk["hbm_gbs"]), "HBM copy bandwidth (%s)" % pk_src
+    elif fp64:
+        bound, unit, achieved = "alu", "TFLOP/s", per_f / avg_s / 1e12
+        peak, note = FP64_TFLOPS, "FP64 nominal 1.25 TFLOP/s (recipe table)"
+    else:
+        bound, unit, achieved = "alu", "TFLOP/s", per_f / avg_s / 1e12
+        peak, note = FP32_ALU_TFLOPS, "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+    return dom, {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                 "frac": achieved / peak, "kernel": dom, "launches": kd["launches"],
+                 "avg_launch_ms": avg_s * 1e3, "bytes_per_launch": per_b,
+                 "flops_per_launch": per_f, "peak_source": note}
+
+
+def _kernels(prof, steps):
+    return {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
+                "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
+                "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0}
+            for k, v in prof["kinds"].items() if v["launches"]}
+
+
+def run_batch_workload(args, w, local, world):
+    """Many uneven instances as one batch: one launch per step kind over the
+    work list, the whole run replayed as one CUDA graph."""
+    import torch
+    from paper_2506_04840_gb300 import api
+    from paper_2506_04840_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    api.load()
+    rank = int(os.environ.get("RANK", "0"))
+    specs = I.batch_specs(w["count"], w["seed"] + 1000 * rank)
+    Ads, cores, Us, rels, items = [], [], [], [], []
+    for i, (shape, ranks, sub) in enumerate(specs):
+        A = I.tucker_plus_noise_device(shape, ranks, sub, noise=1e-3)
+        Ads.append(A)
+        cores.append(torch.empty(int(np.prod(ranks)), dtype=torch.float32, device="cuda"))
+        Us.append([torch.empty(shape[k] * ranks[k], dtype=torch.float32, device="cuda")
+                   for k in range(len(shape))])
+        rels.append(torch.zeros(1, dtype=torch.float64, device="cuda"))
+        items.append(api.make_item(A, shape, ranks, w["s"], w["q"], cores[-1], Us[-1], rels[-1],
+                                   seed=0, tag=i))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    h = api.tucker_batch_create(items, api.TK_SHIFT_PAPER, True)
+    launches, dev_bytes = api.tucker_batch_info(h)
+    for _ in range(args.warmup):
+        api.tucker_batch_run(h, stream)
+    status, _ = api.tucker_batch_wait(h, len(items))
+    assert status == api.TK_OK, status
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        api.tucker_batch_run(h, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    value = world * w["count"] * args.steps / (ms / 1e3)
+    re = np.array([float(r.item()) for r in rels])
+
+    # per-kind breakdown: the same launches without the graph, profiled
+    he = api.tucker_batch_create(items, api.TK_SHIFT_PAPER, False)
+    api.tucker_profile_enable(True)
+    api.tucker_batch_run(he, stream)
+    api.tucker_batch_wait(he, len(items))
+    prof = api.tucker_profile_read()
+    api.tucker_profile_enable(False)
+    api.tucker_batch_destroy(he)
+
+    # end to end: inputs from pinned host memory, results back to the host
+    try:
+        pins = [torch.empty(A.numel(), dtype=torch.float32).pin_memory() for A in Ads]
+        pinned = True
+    except RuntimeError:
+        pins = [torch.empty(A.numel(), dtype=torch.float32) for A in Ads]
+        pinned = False
+    for pn, A in zip(pins, Ads):
+        pn.copy_(A)
+    dev_out = cores + [u for U in Us for u in U] + rels
+    outs = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in dev_out]
+    h2d = sum(p.numel() * 4 for p in pins)
+    d2h = sum(t.numel() * t.element_size() for t in dev_out)
+
+    def e2e_step():
+        for pn, A in zip(pins, Ads):
+            A.copy_(pn, non_blocking=True)
+        api.tucker_batch_run(h, stream)
+        for o, t in zip(outs, dev_out):
+            o.copy_(t, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 4)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 4)
+    api.tucker_batch_destroy(h)
+    pk, pk_src = peaks()
+    dom, roof = _roofline(prof, pk, pk_src)
+    roof["traffic"] = NCU_TRAFFIC.get((args.workload, dom))
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (device-generated, seeded)",
+            "config": {"workload": args.workload, "desc": w["desc"], "instances": w["count"],
+                       "tensor_gb": sum(A.numel() * 4 for A in Ads) / 1e9,
+                       "rel_err_median": float(np.median(re)), "rel_err_max": float(re.max()),
+                       "launches_per_step": launches, "device_gb": dev_bytes / 1e9,
+                       "l2": "inputs (%.1f GB) larger than L2 (129 MB)"
+                             % (sum(A.numel() * 4 for A in Ads) / 1e9)},
+            "roofline": roof, "kernels": _kernels(prof, 1),
+            "e2e": {"value": w["count"] / e2e_s, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "host_memory": "pinned" if pinned else "pageable (pinning failed)"},
+            "clocks": clk, "gpu_launches": launches * args.steps}
+    if world == 1 and not args.no_cpu_baseline:
+        n, el, sample, re_o = _oracle_sample_batch(w, 15.0)
+        line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_workload(args, w, local, world):
+    """Poisson arrivals into the serving loop; latency = completion - submit."""
+    import torch
+    from paper_2506_04840_gb300 import api
+    from paper_2506_04840_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    api.load()
+    rank = int(os.environ.get("RANK", "0"))
+    duration = args.duration if args.duration else w["duration"]
+    count = int(w["rate"] * duration)
+    reqs = I.serving_requests(count, w["seed"] + 1000 * rank, rate=w["rate"])
+    hil = {}
+    # warm-up: a few requests through a scratch server
+    srv = api.tucker_server_create(0, 256, api.TK_SHIFT_PAPER)
+    live = {}
+
+    def make(rq, tag):
+        shape = rq["shape"]
+        if rq["kind"] == "hilbert":
+            key = tuple(shape)
+            if key not in hil:
+                hil[key] = I.hilbert_device(shape)
+            A = hil[key]
+        else:
+            A = I.tucker_plus_noise_device(shape, rq["ranks"], rq["seed"], noise=1e-3)
+        core = torch.empty(int(np.prod(rq["ranks"])), dtype=torch.float32, device="cuda")
+        U = [torch.empty(shape[k] * rq["ranks"][k], dtype=torch.float32, device="cuda")
+             for k in range(3)]
+        rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+        it = api.make_item(A, shape, rq["ranks"], w["s"], rq["q"], core, U, rel, seed=0,
+                           tag=tag % (1 << 24))
+        return it, (A, core, U, rel)
+
+    for i, rq in enumerate(reqs[:max(args.warmup, 3)]):
+        it, keep = make(rq, i)
+        torch.cuda.current_stream().synchronize()
+        live[api.tucker_server_submit(srv, it)] = keep
+    api.tucker_server_drain(srv, 600.0)
+    api.tucker_server_poll(srv, 1 << 16)
+    live.clear()
+
+    api.tucker_profile_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    t_start = api.tucker_server_clock(srv)
+    comps, lag, rels = [], [], {}
+    for i, rq in enumerate(reqs):
+        while api.tucker_server_clock(srv) - t_start < rq["arrival"]:
+            for c in api.tucker_server_poll(srv, 4096):
+                comps.append(c)
+                rels[c["id"]] = live.pop(c["id"])[3]
+            time.sleep(0.0002)
+        it, keep = make(rq, i)
+        torch.cuda.current_stream().synchronize()   # content ready before the server reads it
+        rid = api.tucker_server_submit(srv, it)
+        live[rid] = keep
+        lag.append(api.tucker_server_clock(srv) - t_start - rq["arrival"])
+    api.tucker_server_drain(srv, 1200.0)
+    for c in api.tucker_server_poll(srv, 1 << 16):
+        comps.append(c)
+        rels[c["id"]] = live.pop(c["id"])[3]
+    clk = clocks.stop()
+    prof = api.tucker_profile_read()
+    api.tucker_profile_enable(False)
+    api.tucker_server_destroy(srv)
+    lat = np.array([c["done_s"] - c["submit_s"] for c in comps]) * 1e3
+    span = max(c["done_s"] for c in comps) - min(c["submit_s"] for c in comps)
+    value = len(comps) / span
+    re = np.array([float(r.item()) for r in rels.values()])
+    bad = sum(1 for c in comps if c["status"] != 0)
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
+            "steps": len(comps), "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (device-generated per request, seeded)",
+            "config": {"workload": args.workload, "desc": w["desc"], "duration_s": duration,
+                       "offered_rps": w["rate"], "requests": len(comps), "failed": bad,
+                       "rel_err_median": float(np.median(re)), "rel_err_max": float(re.max()),
+                       "l2": "request tensors mostly larger than L2"},
+            "serve": {"p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)),
+                      "mean_ms": float(lat.mean()),
+                      "submit_lag_p99_ms": float(np.percentile(np.array(lag) * 1e3, 99))},
+            "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0,
+                    "note": "requests are served from device memory; content is made on the "
+                            "device per request (no host copies)"},
+            "clocks": clk, "gpu_launches": prof["kernels"]}
+    if world == 1 and not args.no_cpu_baseline:
+        n, el, sample, _ = _oracle_sample_serve(w, 15.0)
+        line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +508,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--duration", type=float, default=0.0,
+                    help="serving workload: seconds of arrivals (default: the workload's)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -211,6 +519,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
+    if w.get("kind") == "batch":
+        return run_batch_workload(args, w, local, world)
+    if w.get("kind") == "serve":
+        return run_serve_workload(args, w, local, world)
 
     import torch
     from paper_2506_04840_gb300 import api

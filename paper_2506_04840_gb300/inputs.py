@@ -121,6 +121,67 @@ def superdiagonal(n, kind, seed, d=3, dtype=np.float64):
     return np.asfortranarray(X.astype(dtype))
 
 
+def batch_specs(count, seed, lo=32, hi=160, rank_lo=4, rank_hi=16, max_elems=None):
+    """Shapes, core ranks and content seeds of ``batch_instances``."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        d = 3 if rng.random() < 0.5 else 4
+        shape = [int(rng.integers(lo, hi + 1)) for _ in range(d)]
+        if max_elems is not None:
+            while int(np.prod(shape)) > max_elems:
+                m = int(np.argmax(shape))
+                shape[m] = max(lo // 2, shape[m] // 2)
+        ranks = [int(rng.integers(rank_lo, rank_hi + 1)) for _ in range(d)]
+        for m in range(d):
+            other = int(np.prod([ranks[x] for x in range(d) if x != m]))
+            ranks[m] = min(ranks[m], other, shape[m] - 1)
+        out.append((shape, ranks, int(rng.integers(0, 2**31 - 1))))
+    return out
+
+
+def tucker_plus_noise_device(shape, ranks, seed, noise=1e-3, dtype=None, device="cuda"):
+    """Device-side G x_1 U_1 ... x_d U_d + E with ||E|| = noise * ||X||, made
+    with torch's seeded generator (for workloads too large to build on the
+    host).  Returns a flat torch tensor in column-major (i_1 fastest) order.
+    The draws differ from ``tucker_plus_noise`` for the same seed."""
+    import torch
+    dtype = torch.float32 if dtype is None else dtype
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    d = len(shape)
+    # torch is row-major: hold the tensor with reversed axes, so its flat
+    # storage runs i_1 fastest
+    X = torch.randn(tuple(reversed(ranks)), generator=g, device=device, dtype=torch.float64)
+    for k in range(d):
+        Z = torch.randn((shape[k], ranks[k]), generator=g, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(Z)
+        sgn = torch.sign(torch.diagonal(R))
+        sgn[sgn == 0] = 1.0
+        Uk = (Q * sgn).to(torch.float32)
+        ax = d - 1 - k
+        X = torch.movedim(torch.tensordot(Uk, X.to(torch.float32), dims=([1], [ax])), 0, ax)
+    X = X.contiguous()
+    E = torch.randn(X.shape, generator=g, device=device, dtype=torch.float32)
+    E *= noise * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(E)
+    X += E
+    return X.reshape(-1).to(dtype)
+
+
+def hilbert_device(shape, dtype=None, device="cuda"):
+    """Device-side Hilbert-type tensor 1/(i_1 + ... + i_d - d + 1), flat,
+    column-major."""
+    import torch
+    dtype = torch.float32 if dtype is None else dtype
+    s = torch.zeros((1,) * len(shape), dtype=torch.float64, device=device)
+    for k, n in enumerate(reversed(shape)):
+        ax = torch.arange(n, dtype=torch.float64, device=device)
+        view = [1] * len(shape)
+        view[k] = n
+        s = s + ax.reshape(view)
+    return (1.0 / (s + 1.0)).to(dtype).reshape(-1)
+
+
 def batch_instances(count, seed, lo=32, hi=160, rank_lo=4, rank_hi=16, noise=1e-3,
                     dtype=np.float32, max_elems=None):
     """Uneven instances: order 3 or 4 (probability 1/2 each), sides uniform in
@@ -152,14 +213,18 @@ def serving_requests(count, seed, rate=200.0, sides=(64, 128, 256, 512, 768),
     """Request descriptors for the serving loop: Poisson arrival times at
     ``rate`` per second, per-mode sides uniform over ``sides``, content kind
     (Hilbert-type or random Tucker plus 1e-3 relative noise) 50/50, per-mode
-    ranks uniform in [rank_lo, rank_hi] clamped below the side, q uniform
-    over ``qs``.  Content is made by ``request_tensor``."""
+    ranks uniform in [rank_lo, rank_hi] clamped below the side and to the
+    product of the other ranks, q uniform over ``qs``.  Content is made by ``request_tensor``."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
     reqs = []
     for i in range(count):
         shape = [int(rng.choice(sides)) for _ in range(3)]
         ranks = [int(min(rng.integers(rank_lo, rank_hi + 1), shape[m] - 1)) for m in range(3)]
+        # a Tucker rank needs r_m <= prod of the other ranks (else the last
+        # mode's unfolding has fewer columns than r_m)
+        for m in range(3):
+            ranks[m] = int(min(ranks[m], np.prod([ranks[x] for x in range(3) if x != m])))
         reqs.append(dict(id=i, arrival=float(t[i]), shape=shape, ranks=ranks,
                          q=int(rng.choice(qs)), kind="hilbert" if rng.random() < 0.5 else "tucker",
                          seed=int(rng.integers(0, 2**31 - 1))))
