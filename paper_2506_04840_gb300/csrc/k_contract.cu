@@ -448,7 +448,8 @@ int64_t xb_cols_per_split(XType xt, View v, int splits) {
   return (cps + tj - 1) / tj * tj;
 }
 
-int xb_splits(View v, int l) {
+int xb_splits(XType xt, View v, int l) {
+  if (xtb32_ok(xt, v, (const void*)1)) return xb32_shape(v, l).splits;
   const int lc = xb_lc(l);
   const int64_t itiles = (v.n + xb_ti(lc) - 1) / xb_ti(lc);
   const int64_t target = 4LL * num_sms();
@@ -493,8 +494,12 @@ static cudaError_t xb_lc_dispatch(const void* X, View v, const void* W, int l, u
 }
 
 cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
-                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st) {
+                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st,
+                      int64_t ka, int64_t kb) {
   if (v.n <= 0 || v.cols() <= 0 || l <= 0) return cudaSuccess;
+  if (xtb32_ok(xt, v, X))
+    return launch_xb32(X, v, W, l, seed, tag, mode, part, splits, st, ka, kb);
+  if (ka > 0 && W == nullptr && ka != v.cols()) return cudaErrorInvalidValue;
   switch (xt) {
     case X_F64: return xb_lc_dispatch<double>(X, v, W, l, seed, tag, mode, part, splits, st);
     case X_F32: return xb_lc_dispatch<float>(X, v, W, l, seed, tag, mode, part, splits, st);
@@ -542,8 +547,11 @@ static cudaError_t xtb_lc_go(const void* X, View v, const double* B, int64_t b_r
 }
 
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
-                       int64_t b_cm, int m, void* out, cudaStream_t st) {
+                       int64_t b_cm, int m, void* out, cudaStream_t st, int tout,
+                       void* scratch) {
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
+  if (xtb32_ok(xt, v, X)) return launch_xtb32(X, v, B, b_ri, b_cm, m, out, st, tout, scratch);
+  if (tout) return cudaErrorInvalidValue;
   switch (xt) {
     case X_F64: return xtb_lc_go<double, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);
     case X_F32: return xtb_lc_go<float, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);

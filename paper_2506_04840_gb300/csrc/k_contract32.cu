@@ -1,0 +1,519 @@
+// FP32 mode-major contractions on CUDA cores (FFMA), register-tiled.
+//
+// For a mode-major view (P == 1: X_(k) is n x cols, column j contiguous) and
+// FP32 data, the two products of the power step, the sketch and the TTM run
+// here instead of the generic strided kernels of k_contract.cu:
+//   k_xtb32  out[j, c] = sum_i X[i, j] B[i, c]       (W = X^T Q; TTM)
+//   k_xb32   part[s][i][c] = sum_{j in split s} X[i, j] B[j, c]
+//            (Y = X W, or Y = X Omega_k with Omega generated in registers)
+// Each thread accumulates an 8 x 4 tile; a warp is laid out 8 (rows) x 4
+// (outputs) so that every shared-memory read is a 16-byte vector hitting at
+// most 128 distinct bytes (one wavefront); tiles of X are staged through
+// registers into a double-buffered shared-memory slab, so global loads of
+// the next slab overlap the FMAs of the current one.  Summation order per
+// output is fixed (i or j ascending within a block), so results are
+// deterministic and independent of what else runs.
+#include <algorithm>
+
+#include "tk_batch.h"
+#include "tk_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+namespace c32 {
+
+constexpr int KS = 16;   // contraction rows staged per slab
+
+// ---------------------------------------------------------------------------
+// out[j, c] = sum_i X[i + n j] B[i*b_ri + c*b_cm],  block (bx, by):
+// columns j0 = bx*MJ.., outputs c0 = by*MC..  (MJ = 64 WJ, MC = 16 WC).
+// out is written in the (1, m, cols) layout out[c + m j], or with tout in
+// the (cols, m) layout out[j + cols c] (the mode just contracted moves last).
+// ---------------------------------------------------------------------------
+template <int WJ, int WC>
+__device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
+                                           const double* __restrict__ B, int64_t b_ri,
+                                           int64_t b_cm, int m, float* __restrict__ out,
+                                           int tout, int64_t ib, int64_t ie, unsigned bx,
+                                           unsigned by) {
+  constexpr int MJ = 64 * WJ, MC = 16 * WC, T = 32 * WJ * WC;
+  constexpr int XPT = KS * MJ / T;          // X elements each thread stages per slab
+  constexpr int BPT = (KS * MC + T - 1) / T;
+  __shared__ __align__(16) float Xs[2][KS][MJ + 4];
+  __shared__ __align__(16) float Bs[2][KS][MC];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wj = w % WJ, wc = w / WJ;
+  const int lj = lane >> 2, lc = lane & 3;
+  const int64_t j0 = (int64_t)bx * MJ;
+  const int c0 = (int)by * MC;
+  const int ja = wj * 64 + lj * 4;          // thread's columns: ja..ja+3, ja+32..ja+35
+  const int cb = wc * 16 + lc * 4;          // thread's outputs: cb..cb+3
+
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+
+  float xr[XPT], br[BPT];
+  auto load = [&](int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      const int ii = e % KS, jj = e / KS;
+      const int64_t i = i0 + ii, j = j0 + jj;
+      xr[r] = (i < ie && j < cols) ? __ldg(X + j * n + i) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < BPT; ++r) {
+      const int e = tid + r * T;
+      float v = 0.f;
+      if (e < KS * MC) {
+        const int c = e % MC, ii = e / MC;
+        const int64_t i = i0 + ii;
+        if (i < ie && c0 + c < m) v = (float)B[i * b_ri + (int64_t)(c0 + c) * b_cm];
+      }
+      br[r] = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      Xs[buf][e % KS][e / KS] = xr[r];
+    }
+#pragma unroll
+    for (int r = 0; r < BPT; ++r) {
+      const int e = tid + r * T;
+      if (e < KS * MC) Bs[buf][e / MC][e % MC] = br[r];
+    }
+  };
+
+  const int nsl = ie > ib ? (int)((ie - ib + KS - 1) / KS) : 0;
+  if (nsl > 0) {
+    load(ib);
+    store(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < nsl; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < nsl) load(ib + (int64_t)(s + 1) * KS);
+#pragma unroll
+    for (int ii = 0; ii < KS; ++ii) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][ii][ja]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][ii][ja + 32]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][ii][cb]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+    }
+    if (s + 1 < nsl) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t j = j0 + ja + (a < 4 ? a : 28 + a);
+    if (j >= cols) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + cb + q;
+      if (c < m) out[tout ? j + cols * c : (int64_t)c + (int64_t)m * j] = acc[a][q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// part[(split*n + i)*lc + c] = sum_{j in split} X[i + n j] B(j, c), block
+// (bx, by, bz): rows i0 = bx*MI.., outputs c0 = by*MC.., split bz over
+// columns [bz*cps, (bz+1)*cps).  B(j, c) = W[c + l j] or Omega_k(jk, c), where
+// jk = j / ka + kb (j % ka) maps the layout's column order to the unfolding's
+// (ka = columns, kb = 1 for the natural layout).
+// ---------------------------------------------------------------------------
+template <int WI, int WC, bool OMEGA>
+__device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
+                                          const float* __restrict__ W, int l, int lc,
+                                          uint64_t seed, uint32_t tag, int mode, int64_t cps,
+                                          int64_t ka, int64_t kb, float* __restrict__ part,
+                                          unsigned bx, unsigned by, unsigned bz) {
+  constexpr int MI = 64 * WI, MC = 16 * WC, T = 32 * WI * WC;
+  constexpr int XPT = KS * MI / T;
+  constexpr int BPT = (KS * MC + T - 1) / T;
+  constexpr int OPT = (KS * (MC / 4) + T - 1) / T;   // Omega groups of 4 per thread
+  __shared__ __align__(16) float Xs[2][KS][MI + 4];
+  __shared__ __align__(16) float Bs[2][KS][MC];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wi = w % WI, wc = w / WI;
+  const int li = lane >> 2, lcn = lane & 3;
+  const int64_t i0 = (int64_t)bx * MI;
+  const int c0 = (int)by * MC;
+  const int64_t jb = (int64_t)bz * cps;
+  const int64_t je = min(cols, jb + cps);
+  const int ia = wi * 64 + li * 4;
+  const int cb = wc * 16 + lcn * 4;
+
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+
+  float xr[XPT], br[OMEGA ? 4 * OPT : BPT];
+  auto load = [&](int64_t j0) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      const int ii = e % MI, jj = e / MI;
+      const int64_t i = i0 + ii, j = j0 + jj;
+      xr[r] = (i < n && j < je) ? __ldg(X + j * n + i) : 0.f;
+    }
+    if (OMEGA) {
+#pragma unroll
+      for (int r = 0; r < OPT; ++r) {
+        const int e = tid + r * T;
+        float w4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (e < KS * (MC / 4)) {
+          const int jj = e % KS, g = e / KS;
+          const int64_t j = j0 + jj;
+          // Omega's row is the column's index in the unfolding's own order:
+          // column j = a + ka*b of this layout is row b + kb*a
+          if (j < je && c0 + 4 * g < l)
+            omega4((uint64_t)(j / ka + kb * (j % ka)), (c0 >> 2) + g, mode, tag, seed, w4);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) br[4 * r + q] = w4[q];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < BPT; ++r) {
+        const int e = tid + r * T;
+        float v = 0.f;
+        if (e < KS * MC) {
+          const int c = e % MC, jj = e / MC;
+          const int64_t j = j0 + jj;
+          if (j < je && c0 + c < l) v = W[(int64_t)(c0 + c) + (int64_t)l * j];
+        }
+        br[r] = v;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      Xs[buf][e / MI][e % MI] = xr[r];
+    }
+    if (OMEGA) {
+#pragma unroll
+      for (int r = 0; r < OPT; ++r) {
+        const int e = tid + r * T;
+        if (e < KS * (MC / 4)) {
+          const int jj = e % KS, g = e / KS;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            Bs[buf][jj][4 * g + q] = (c0 + 4 * g + q < l) ? br[4 * r + q] : 0.f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < BPT; ++r) {
+        const int e = tid + r * T;
+        if (e < KS * MC) Bs[buf][e / MC][e % MC] = br[r];
+      }
+    }
+  };
+
+  const int nsl = je > jb ? (int)((je - jb + KS - 1) / KS) : 0;
+  if (nsl > 0) {
+    load(jb);
+    store(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < nsl; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < nsl) load(jb + (int64_t)(s + 1) * KS);
+#pragma unroll
+    for (int jj = 0; jj < KS; ++jj) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][jj][ia]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][jj][ia + 32]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][jj][cb]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+    }
+    if (s + 1 < nsl) store(buf ^ 1);
+    __syncthreads();
+  }
+  float* dst = part + (int64_t)bz * n * lc;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + ia + (a < 4 ? a : 28 + a);
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + cb + q;
+      if (c < lc) dst[i * lc + c] = acc[a][q];
+    }
+  }
+}
+
+template <int WJ, int WC>
+__global__ void __launch_bounds__(32 * WJ * WC)
+k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const double* __restrict__ B,
+        int64_t b_ri, int64_t b_cm, int m, float* __restrict__ out, int tout, int64_t kps,
+        float* __restrict__ part) {
+  // split z of the rows writes its partial sums to part (layout c + m j)
+  const int64_t ib = (int64_t)blockIdx.z * kps, ie = min(n, ib + kps);
+  float* o = part ? part + (int64_t)blockIdx.z * cols * m : out;
+  xtb32_body<WJ, WC>(X, n, cols, B, b_ri, b_cm, m, o, part ? 0 : tout, ib, ie, blockIdx.x,
+                     blockIdx.y);
+}
+
+// out = sum over the ks row splits of the partials, in a fixed order.
+__device__ __forceinline__ void xtb32_red_body(const float* __restrict__ part, int ks,
+                                               int64_t cols, int m, int tout,
+                                               float* __restrict__ out, unsigned bx) {
+  const int64_t e = (int64_t)bx * 256 + threadIdx.x;
+  if (e >= cols * m) return;
+  float s = 0.f;
+  for (int z = 0; z < ks; ++z) s += part[(int64_t)z * cols * m + e];
+  const int64_t c = e % m, j = e / m;
+  out[tout ? j + cols * c : e] = s;
+}
+
+__global__ void __launch_bounds__(256)
+k_xtb32_red(const float* __restrict__ part, int ks, int64_t cols, int m, int tout,
+            float* __restrict__ out) {
+  xtb32_red_body(part, ks, cols, m, tout, out, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_xtb32_red_batch(const Xtb32RedJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                  int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const Xtb32RedJob J = jobs[j];
+    xtb32_red_body((const float*)J.part, J.ks, J.cols, J.m, J.tout, (float*)J.out,
+                   b - __ldg(start + j));
+  }
+}
+
+template <int WI, int WC, bool OMEGA>
+__global__ void __launch_bounds__(32 * WI * WC)
+k_xb32(const float* __restrict__ X, int64_t n, int64_t cols, const float* __restrict__ W, int l,
+       int lc, uint64_t seed, uint32_t tag, int mode, int64_t cps, int64_t ka, int64_t kb,
+       float* __restrict__ part) {
+  xb32_body<WI, WC, OMEGA>(X, n, cols, W, l, lc, seed, tag, mode, cps, ka, kb, part, blockIdx.x,
+                           blockIdx.y, blockIdx.z);
+}
+
+template <int WJ, int WC>
+__global__ void __launch_bounds__(32 * WJ * WC)
+k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+              uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const Xtb32Job J = jobs[j];
+    const uint32_t lb = b - __ldg(start + j);
+    const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy, z = lb / gxy, r = lb % gxy;
+    const int64_t ib = (int64_t)z * J.kps, ie = min(J.n, ib + J.kps);
+    float* o = J.part ? (float*)J.part + (int64_t)z * J.cols * J.m : (float*)J.out;
+    xtb32_body<WJ, WC>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
+                       J.part ? 0 : J.tout, ib, ie, r % (uint32_t)J.gx, r / (uint32_t)J.gx);
+    __syncthreads();
+  }
+}
+
+template <int WI, int WC, bool OMEGA>
+__global__ void __launch_bounds__(32 * WI * WC)
+k_xb32_batch(const Xb32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+             uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const Xb32Job J = jobs[j];
+    const uint32_t lb = b - __ldg(start + j);
+    const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy;
+    const uint32_t r = lb % gxy;
+    xb32_body<WI, WC, OMEGA>((const float*)J.X, J.n, J.cols, (const float*)J.W, J.l, J.lc,
+                             J.seed, J.tag, J.mode, J.cps, J.ka, J.kb, (float*)J.part,
+                             r % (uint32_t)J.gx, r / (uint32_t)J.gx, lb / gxy);
+    __syncthreads();
+  }
+}
+
+}  // namespace c32
+
+// ---------------------------------------------------------------------------
+// Shapes.  Outputs per block: 16 WC (WC = 1, 2, 4 for up to 16, 32, 64
+// outputs; more outputs take several blocks along y).  Rows per block for
+// k_xb32: 64 WI with WI = 1, 2 or 4 by n.
+// ---------------------------------------------------------------------------
+static int wc_of(int m) { return m <= 16 ? 1 : (m <= 32 ? 2 : 4); }
+static int wi_of(int64_t n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }
+static int wj_of(int wc) { return wc == 4 ? 2 : 4; }
+
+bool xtb32_ok(XType xt, View v, const void* X) {
+  return xt == X_F32 && v.P == 1 && v.n >= 1 && v.cols() >= 1 && X != nullptr;
+}
+
+Xtb32Shape xtb32_shape(View v, int m, bool allow_split) {
+  Xtb32Shape s;
+  s.wc = wc_of(m);
+  s.wj = wj_of(s.wc);
+  s.gx = (int)((v.cols() + 64 * s.wj - 1) / (64 * s.wj));
+  s.gy = (m + 16 * s.wc - 1) / (16 * s.wc);
+  s.threads = 32 * s.wj * s.wc;
+  // few column tiles: split the rows too (partials + a fixed-order sum),
+  // so that about two CTAs per SM work; each split keeps >= 64 rows
+  s.ks = 1;
+  const int64_t tiles = (int64_t)s.gx * s.gy;
+  if (allow_split && tiles < num_sms()) {
+    const int64_t want = (2LL * num_sms() + tiles - 1) / tiles;
+    const int64_t maxk = std::max<int64_t>(1, v.n / 64);
+    s.ks = (int)std::max<int64_t>(1, std::min(want, maxk));
+  }
+  int64_t kps = (v.n + s.ks - 1) / s.ks;
+  kps = (kps + c32::KS - 1) / c32::KS * c32::KS;
+  s.kps = kps;
+  s.ks = (int)((v.n + kps - 1) / kps);
+  return s;
+}
+
+size_t xtb32_scratch(View v, int m) {
+  const Xtb32Shape s = xtb32_shape(v, m, true);
+  return s.ks > 1 ? (size_t)s.ks * v.cols() * m * sizeof(float) : 0;
+}
+
+Xb32Shape xb32_shape(View v, int l, int splits_req) {
+  Xb32Shape s;
+  s.lc = xb_lc(l);
+  s.wc = wc_of(std::min(s.lc, 64));
+  s.wi = wi_of(v.n);
+  s.gx = (int)((v.n + 64 * s.wi - 1) / (64 * s.wi));
+  s.gy = (s.lc + 16 * s.wc - 1) / (16 * s.wc);
+  int64_t splits = splits_req;
+  if (splits <= 0) {
+    // about 3 CTAs per SM in total, at least 4 slabs of columns per split
+    const int64_t target = 3LL * num_sms();
+    splits = (target + (int64_t)s.gx * s.gy - 1) / ((int64_t)s.gx * s.gy);
+    const int64_t maxs = std::max<int64_t>(1, (v.cols() + 4 * c32::KS - 1) / (4 * c32::KS));
+    splits = std::max<int64_t>(1, std::min(splits, maxs));
+  }
+  int64_t cps = (v.cols() + splits - 1) / splits;
+  cps = (cps + c32::KS - 1) / c32::KS * c32::KS;
+  // every split writes its partial block (splits past the last column write
+  // zeros), so the reduction may sum exactly `splits` blocks
+  s.splits = (int)splits;
+  s.cps = cps;
+  s.threads = 32 * s.wi * s.wc;
+  return s;
+}
+
+template <int WJ, int WC>
+static void xtb32_go(const float* X, View v, const double* B, int64_t b_ri, int64_t b_cm, int m,
+                     float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
+  c32::k_xtb32<WJ, WC><<<dim3(s.gx, s.gy, s.ks), 32 * WJ * WC, 0, st>>>(
+      X, v.n, v.cols(), B, b_ri, b_cm, m, out, tout, s.kps, s.ks > 1 ? part : nullptr);
+}
+
+cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                         int m, void* out, cudaStream_t st, int tout, void* scratch) {
+  if (v.cols() <= 0 || m <= 0) return cudaSuccess;
+  const Xtb32Shape s = xtb32_shape(v, m, scratch != nullptr);
+  float* part = (float*)scratch;
+  count_kernels(s.ks > 1 ? 2 : 1);
+  const float* x = (const float*)X;
+  float* o = (float*)out;
+  switch (s.wc) {
+    case 1: xtb32_go<4, 1>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
+    case 2: xtb32_go<4, 2>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
+    default: xtb32_go<2, 4>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
+  }
+  if (s.ks > 1) {
+    const int64_t tot = v.cols() * m;
+    c32::k_xtb32_red<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, s.ks, v.cols(), m,
+                                                                      tout, o);
+  }
+  return cudaGetLastError();
+}
+
+template <int WI, int WC>
+static void xb32_go(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
+                    int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
+                    cudaStream_t st) {
+  const dim3 grid(s.gx, s.gy, s.splits);
+  if (W == nullptr)
+    c32::k_xb32<WI, WC, true><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), nullptr, l, s.lc,
+                                                             seed, tag, mode, s.cps, ka, kb, part);
+  else
+    c32::k_xb32<WI, WC, false><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), W, l, s.lc,
+                                                              seed, tag, mode, s.cps, ka, kb,
+                                                              part);
+}
+
+template <int WI>
+static void xb32_wc(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
+                    int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
+                    cudaStream_t st) {
+  switch (s.wc) {
+    case 1: xb32_go<WI, 1>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
+    case 2: xb32_go<WI, 2>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
+    default: xb32_go<WI, 4>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
+  }
+}
+
+cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
+                        int mode, void* part, int splits, cudaStream_t st, int64_t ka,
+                        int64_t kb) {
+  if (ka <= 0) {   // natural layout: the identity map
+    ka = v.cols();
+    kb = 1;
+  }
+  if (v.n <= 0 || v.cols() <= 0 || l <= 0) return cudaSuccess;
+  const Xb32Shape s = xb32_shape(v, l, splits);
+  count_kernels(1);
+  const float* x = (const float*)X;
+  const float* w = (const float*)W;
+  float* p = (float*)part;
+  switch (s.wi) {
+    case 1: xb32_wc<1>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
+    case 2: xb32_wc<2>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
+    default: xb32_wc<4>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
+  }
+  return cudaGetLastError();
+}
+
+// Work-list launches: tile = WC, flag = (omega ? 1 : 0) | (WI or WJ) << 1.
+cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st) {
+  const int wc = b.tile, wx = b.flag >> 1, omega = b.flag & 1;
+  if (b.kind == BK_XTB32RED) return run_batch(c32::k_xtb32_red_batch, b, 256, st);
+  if (b.kind == BK_XTB32) {
+    if (wc == 1) return run_batch(c32::k_xtb32_batch<4, 1>, b, 128, st);
+    if (wc == 2) return run_batch(c32::k_xtb32_batch<4, 2>, b, 256, st);
+    return run_batch(c32::k_xtb32_batch<2, 4>, b, 256, st);
+  }
+  if (b.kind != BK_XB32) return cudaErrorInvalidValue;
+#define TK_XB32_CASE(WI, WC)                                                              \
+  if (wx == WI && wc == WC)                                                               \
+    return omega ? run_batch(c32::k_xb32_batch<WI, WC, true>, b, 32 * WI * WC, st)        \
+                 : run_batch(c32::k_xb32_batch<WI, WC, false>, b, 32 * WI * WC, st);
+  TK_XB32_CASE(1, 1)
+  TK_XB32_CASE(1, 2)
+  TK_XB32_CASE(1, 4)
+  TK_XB32_CASE(2, 1)
+  TK_XB32_CASE(2, 2)
+  TK_XB32_CASE(2, 4)
+  TK_XB32_CASE(4, 1)
+  TK_XB32_CASE(4, 2)
+  TK_XB32_CASE(4, 4)
+#undef TK_XB32_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tk

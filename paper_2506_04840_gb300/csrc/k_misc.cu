@@ -142,6 +142,9 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
     case BK_GRAM:
     case BK_POLISH:
       return launch_batch_small(b, st);
+    case BK_XTB32:
+    case BK_XB32:
+      return launch_batch_c32(b, st);
     default:
       return launch_batch_misc(b, st);
   }

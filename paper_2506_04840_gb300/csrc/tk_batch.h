@@ -90,7 +90,38 @@ struct ErrFinalJob {
   int blocks;
 };
 
-enum BatchKind { BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN };
+// FP32 mode-major (P == 1) register-tiled contractions (k_contract32.cu).
+struct Xtb32Job {
+  const void* X;
+  int64_t n, cols;
+  const double* B;
+  int64_t b_ri, b_cm;
+  void* out;
+  void* part;           // non-null: row splits write partials here (ks > 1)
+  int64_t kps;          // rows per split
+  int m, gx, gy, tout;
+};
+struct Xtb32RedJob {
+  const void* part;
+  void* out;
+  int64_t cols;
+  int m, ks, tout;
+};
+struct Xb32Job {
+  const void* X;
+  int64_t n, cols;
+  const void* W;
+  int64_t cps, ka, kb;
+  void* part;
+  uint64_t seed;
+  uint32_t tag;
+  int l, lc, mode, gx, gy;
+};
+
+enum BatchKind {
+  BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
+  BK_XB32, BK_XTB32RED
+};
 
 constexpr size_t kJobBytes = 128;   // every job struct fits
 
@@ -98,7 +129,8 @@ struct BatchLaunch {
   int kind;           // BatchKind
   int xt;             // XType of the data (copy: of the destination)
   int tile;           // xb / xtb: column tile LC; svd: threads per CTA
-  int flag;           // xb: 1 = Omega; xtb: EPI
+  int flag;           // xb: 1 = Omega; xtb: EPI; copy: 1 = round through FP32;
+                      // xb32 / xtb32: (Omega) | (warps along rows) << 1
   const void* jobs;   // device array of njobs job structs
   const uint32_t* start;   // device: first block of each job
   int njobs;
@@ -112,6 +144,21 @@ void batch_kernels_init();
 cudaError_t launch_batch_contract(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_misc(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st);
+
+// Launch shapes of the FP32 mode-major kernels.
+struct Xtb32Shape {
+  int wj, wc, gx, gy, threads, ks;
+  int64_t kps;
+};
+struct Xb32Shape {
+  int wi, wc, lc, gx, gy, splits, threads;
+  int64_t cps;
+};
+// allow_split: rows may be split (needs xtb32_scratch bytes of scratch).
+Xtb32Shape xtb32_shape(View v, int m, bool allow_split);
+// splits = 0: the default split count; else that many column splits.
+Xb32Shape xb32_shape(View v, int l, int splits = 0);
 
 // Per-job launch shapes, as the single-problem launchers choose them.
 int xb_grid_x(View v, int l);

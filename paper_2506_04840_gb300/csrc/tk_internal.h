@@ -39,18 +39,39 @@ struct ProfScope {
 // Partial products Y_part[split][i][c] of Y = X_(k) B with B = Omega_k
 // (generated) or B = W stored in the (P, l, S) layout.  Returns the number
 // of splits used; part must hold splits*n*lc accumulation-type values.
-int xb_splits(View v, int l);
+int xb_splits(XType xt, View v, int l);
 int xb_lc(int l);
+// FP32 mode-major (P == 1) register-tiled versions (k_contract32.cu), used
+// by launch_xb / launch_xtb when they apply.
+bool xtb32_ok(XType xt, View v, const void* X);
+// tout: write out[j + cols*c] (the contracted mode moves last) instead of
+// out[c + m*j].  ka, kb: Omega's row for layout column j is j/ka + kb*(j%ka)
+// (ka = 0: the natural layout, row j).
+// scratch (may be NULL): xtb32_scratch bytes; lets few-column products split
+// their rows over more CTAs.
+cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                         int m, void* out, cudaStream_t st, int tout = 0,
+                         void* scratch = nullptr);
+size_t xtb32_scratch(View v, int m);
+cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
+                        int mode, void* part, int splits, cudaStream_t st, int64_t ka = 0,
+                        int64_t kb = 1);
+// ka, kb: Omega row map of a rotated layout (see launch_xb32; FP32
+// mode-major views only; ka = 0 is the natural layout).
 cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
-                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st);
+                      uint32_t tag, int mode, void* part, int splits, cudaStream_t st,
+                      int64_t ka = 0, int64_t kb = 1);
 // Y = sum_split part - alpha*Q (Q, alpha may be NULL): n x l FP64.
 cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int l, int lc,
                           const double* Q, const double* alpha, double* Y, cudaStream_t st);
 // out(P, m, S) = X x_k B^T with B(i, c) at B[i*b_ri + c*b_cm] (FP64):
 // out[j, c] = sum_i X(p, i, s) B(i, c).  Output in the accumulation type of
 // X (or `out_bf16` when non-null: BF16 output is not supported here).
+// tout = 1 (FP32 mode-major views only): out[j + cols*c] instead of the
+// (P, m, S) layout.
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
-                       int64_t b_cm, int m, void* out, cudaStream_t st);
+                       int64_t b_cm, int m, void* out, cudaStream_t st, int tout = 0,
+                       void* scratch = nullptr);
 // Fused last-mode expansion and error sums: for S == 1, a_hat(p, c) =
 // sum_i T(p, i) B(i, c); accumulates (A - a_hat)^2 and A^2 per block into
 // err_part[2*block].  Returns the number of blocks via *blocks.

@@ -86,11 +86,38 @@ struct HosvdPlan {
   int q = 0;
   bool bf16 = false;
   tk_shift rule = TK_SHIFT_PAPER;
+  // rot (ST-HOSVD, FP32, modes in natural order): every TTM writes its output
+  // with the contracted mode moved last, so each step sees its mode first
+  // (a mode-major view) and the core comes out in natural order.
+  bool rot = false;
   // sizes (bytes)
   size_t gbuf = 0, shadow = 0, wbuf = 0, part = 0, ymat = 0, small = 0, qd = 0;
   std::vector<SmallPlan> sp;
   std::vector<std::vector<int64_t>> dims_at;  // tensor dims seen by each step
 };
+
+// View of mode k of the current tensor (dims cur, in natural mode order).
+// Natural layout: the strided view, ka = 0.  Rotated layout (p.rot): the
+// layout is (k, k+1..d, 1..k-1), the view is mode-major and column j of it
+// is row j/ka + kb*(j%ka) of Omega_k (the unfolding's own column order).
+inline View step_view(const HosvdPlan& p, const std::vector<int64_t>& cur, int k, int64_t* ka,
+                      int64_t* kb) {
+  if (!p.rot) {
+    *ka = 0;
+    *kb = 1;
+    return view_of(cur, k);
+  }
+  int64_t a = 1, b = 1;
+  for (size_t m = k + 1; m < cur.size(); ++m) a *= cur[m];
+  for (int m = 0; m < k; ++m) b *= cur[m];
+  *ka = a;
+  *kb = b;
+  View v;
+  v.P = 1;
+  v.n = cur[k];
+  v.S = a * b;
+  return v;
+}
 
 struct HosvdWs {
   void* g[2];

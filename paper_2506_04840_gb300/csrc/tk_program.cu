@@ -38,11 +38,63 @@ size_t job_size(int kind) {
     case BK_GRAM: return sizeof(GramJob);
     case BK_POLISH: return sizeof(PolishJob);
     case BK_COPY: return sizeof(CopyJob);
+    case BK_XTB32: return sizeof(Xtb32Job);
+    case BK_XTB32RED: return sizeof(Xtb32RedJob);
+    case BK_XB32: return sizeof(Xb32Job);
     default: return sizeof(ErrFinalJob);
   }
 }
 
 uint32_t cdiv(int64_t a, int64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+// out = X x_k B^T (EPI 0) as the single-problem launch_xtb runs it (with the
+// same scratch): the FP32 mode-major kernel where it applies (+ the sum of its
+// row splits at position pos + 1), else the generic one.
+void xtb_ops(Phase& ph, int pos, int prof, XType xt, const void* X, View v, const double* B,
+             int64_t b_ri, int64_t b_cm, int m, void* out, double bytes, double flops,
+             int tout = 0, void* scratch = nullptr) {
+  if (xtb32_ok(xt, v, X)) {
+    const Xtb32Shape sh = xtb32_shape(v, m, scratch != nullptr);
+    void* part = sh.ks > 1 ? scratch : nullptr;
+    Xtb32Job j{X, v.n, v.cols(), B, b_ri, b_cm, out, part, sh.kps, m, sh.gx, sh.gy, tout};
+    ph.push_back(make_op(pos, prof, BK_XTB32, xt, sh.wc, sh.wj << 1, 0,
+                         (uint32_t)sh.gx * sh.gy * sh.ks, bytes, flops, j));
+    if (part) {
+      Xtb32RedJob rj{part, out, v.cols(), m, sh.ks, tout};
+      ph.push_back(make_op(pos + 1, prof, BK_XTB32RED, xt, 0, 0, 0, cdiv(v.cols() * m, 256),
+                           0.0, 0.0, rj));
+    }
+    return;
+  }
+  const int mt = xtb_tile(m);
+  const int gx = (int)cdiv(v.cols(), 128);
+  XtbJob j{X, v.P, v.n, v.S, B, b_ri, b_cm, out, nullptr, nullptr, m, gx};
+  ph.push_back(make_op(pos, prof, BK_XTB, xt, mt, 0, 0, (uint32_t)gx * cdiv(m, mt), bytes, flops,
+                       j));
+}
+
+// partials of Y = X_(k) B (B = W, or Omega_k when W == NULL) as launch_xb runs them.
+Op xb_op(int pos, int prof, XType xt, const void* X, View v, const void* W, int l,
+         uint64_t seed, uint32_t tag, int mode, void* part, int splits, double bytes,
+         double flops, int64_t ka = 0, int64_t kb = 1) {
+  if (xtb32_ok(xt, v, X)) {
+    const Xb32Shape sh = xb32_shape(v, l, splits);
+    if (ka <= 0) {
+      ka = v.cols();
+      kb = 1;
+    }
+    Xb32Job j{X, v.n, v.cols(), W, sh.cps, ka, kb, part, seed, tag, l, sh.lc, mode, sh.gx,
+              sh.gy};
+    return make_op(pos, prof, BK_XB32, xt, sh.wc, (W == nullptr ? 1 : 0) | (sh.wi << 1), 0,
+                   (uint32_t)sh.gx * sh.gy * sh.splits, bytes, flops, j);
+  }
+  const int lc = xb_lc(l);
+  const int gx = xb_grid_x(v, l);
+  const int64_t cps = xb_cols_per_split(xt, v, splits);
+  XbJob j{X, v.P, v.n, v.S, W, cps, part, seed, tag, l, mode, gx};
+  return make_op(pos, prof, BK_XB, xt, lc, W == nullptr ? 1 : 0, 0, (uint32_t)gx * splits, bytes,
+                 flops, j);
+}
 
 // Extra per-problem buffers beyond the single-call workspace.
 struct Extras {
@@ -129,12 +181,11 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
   int pp = 0;
   for (int step = 0; step < d; ++step) {
     const int k = p.order[step];
-    const View v = view_of(cur, k);
+    int64_t ka, kb;
+    const View v = step_view(p, cur, k, &ka, &kb);
     const int l = p.l[k];
     const int lc = xb_lc(l);
-    const int splits = xb_splits(v, l);
-    const int gx = xb_grid_x(v, l);
-    const int64_t cps = xb_cols_per_split(xt, v, splits);
+    const int splits = xb_splits(xt, v, l);
     const double N = (double)v.P * (double)v.n * (double)v.S;
     const double nl = (double)v.n * l;
     const double red_bytes = (double)splits * v.n * lc * asize(xt) + nl * 8.0;
@@ -144,15 +195,12 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     double* alpha = stt->alpha + k;
     const int sthreads = svd_threads(v.n, l);
     const size_t ssmem = svd_smem(v.n, l, fp64);
-    const int xtile = xtb_tile(l);
-    const int xgx = (int)cdiv(v.cols(), 128);
 
     // ---- sketch phase
     {
       Phase ph;
-      XbJob xb{X, v.P, v.n, v.S, nullptr, cps, w.part, it.seed, it.tag, l, k, gx};
-      ph.push_back(make_op(0, TK_K_SKETCH, BK_XB, xt, lc, 1, 0, (uint32_t)gx * splits, N * es,
-                           2.0 * N * l, xb));
+      ph.push_back(xb_op(0, TK_K_SKETCH, xt, X, v, nullptr, l, it.seed, it.tag, k, w.part, splits,
+                         N * es, 2.0 * N * l, ka, kb));
       ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc};
       ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
                            red_bytes, (double)splits * nl, rd));
@@ -166,19 +214,16 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     // ---- power phases
     for (int t = 1; t <= p.q; ++t) {
       Phase ph;
-      XtbJob xw{X, v.P, v.n, v.S, w.Q, 1, v.n, w.w, nullptr, nullptr, l, xgx};
-      ph.push_back(make_op(0, TK_K_POWER_W, BK_XTB, xt, xtile, 0, 0,
-                           (uint32_t)xgx * cdiv(l, xtile), N * es, 2.0 * N * l, xw));
-      XbJob xy{X, v.P, v.n, v.S, w.w, cps, w.part, it.seed, it.tag, l, k, gx};
-      ph.push_back(make_op(1, TK_K_POWER_Y, BK_XB, xt, lc, 0, 0, (uint32_t)gx * splits, N * es,
-                           2.0 * N * l, xy));
+      xtb_ops(ph, 0, TK_K_POWER_W, xt, X, v, w.Q, 1, v.n, l, w.w, N * es, 2.0 * N * l, 0, w.part);
+      ph.push_back(xb_op(2, TK_K_POWER_Y, xt, X, v, w.w, l, it.seed, it.tag, k, w.part, splits,
+                         N * es, 2.0 * N * l));
       ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc};
-      ph.push_back(make_op(2, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
+      ph.push_back(make_op(3, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
                 stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,
                 (int)p.rule, 1, 0};
-      ph.push_back(make_op(3, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+      ph.push_back(make_op(4, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
                            2.0 * nl * 8.0, svd_flops, sv));
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + t);
@@ -206,10 +251,8 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
                              cdiv(v.n * r, 256), (double)v.n * r * 16.0, 0.0, cq));
       }
       void* out = (step == d - 1) ? it.core : w.g[pp];
-      const int mt = xtb_tile(r);
-      XtbJob tt{X, v.P, v.n, v.S, w.Q, 1, v.n, out, nullptr, nullptr, r, xgx};
-      ph.push_back(make_op(3, TK_K_TTM, BK_XTB, xt, mt, 0, 0, (uint32_t)xgx * cdiv(r, mt),
-                           (N + N / v.n * r) * es, 2.0 * N * r, tt));
+      xtb_ops(ph, 3, TK_K_TTM, xt, X, v, w.Q, 1, v.n, r, out, (N + N / v.n * r) * es,
+              2.0 * N * r, p.rot ? 1 : 0, w.part);
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + TK_MAX_Q + 1);
       X = out;
@@ -226,12 +269,9 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     for (int k = 0; k < d - 1; ++k) {
       const View v = view_of(dims, k);
       const int m = (int)p.n[k];
-      const int mt = xtb_tile(m);
-      const int egx = (int)cdiv(v.cols(), 128);
       const double cin = (double)v.P * v.n * v.S;
-      XtbJob ej{Xe, v.P, v.n, v.S, qd[k], p.n[k], 1, tb[k & 1], nullptr, nullptr, m, egx};
-      ph.push_back(make_op(k, TK_K_ERROR, BK_XTB, xt, mt, 0, 0, (uint32_t)egx * cdiv(m, mt),
-                           (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n, ej));
+      xtb_ops(ph, k, TK_K_ERROR, xt, Xe, v, qd[k], p.n[k], 1, m, tb[k & 1],
+              (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n);
       Xe = tb[k & 1];
       dims[k] = p.n[k];
     }

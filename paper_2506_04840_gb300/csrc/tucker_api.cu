@@ -106,6 +106,9 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     if (!st)
       for (int k = 0; k < p.d; ++k) p.order[k] = k;   // T-HOSVD: order is immaterial
   }
+  bool natural = true;
+  for (int k = 0; k < p.d; ++k) natural = natural && p.order[k] == k;
+  p.rot = st && natural && p.xt == X_F32;
   const size_t es = xsize(p.xt), ta = asize(p.xt);
   p.l.assign(p.d, 0);
   p.sp.assign(p.d, SmallPlan{});
@@ -114,7 +117,8 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
   for (int step = 0; step < p.d; ++step) {
     const int k = p.order[step];
     p.dims_at[k] = cur;
-    const View v = view_of(cur, k);
+    int64_t ka, kb;
+    const View v = step_view(p, cur, k, &ka, &kb);
     const int64_t cols = v.cols();
     const int64_t lk = std::min<int64_t>({(int64_t)p.r[k] + p.s[k], v.n, cols});
     if (lk < p.r[k]) return TK_EINVAL;        // U_k = Q(:, 1:r_k) needs l_k >= r_k
@@ -125,8 +129,12 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     p.small = std::max(p.small, p.sp[k].scratch_bytes);
     if (p.xt != X_F64) p.small = std::max(p.small, polish_scratch(v.n, p.r[k]));
     const int lc = xb_lc((int)lk);
-    const int splits = xb_splits(v, (int)lk);
+    const int splits = xb_splits(p.xt, v, (int)lk);
     p.part = std::max(p.part, (size_t)splits * v.n * lc * ta);
+    if (xtb32_ok(p.xt, v, (const void*)1)) {   // row-split scratch of W = X^T Q and the TTM
+      p.part = std::max(p.part, xtb32_scratch(v, (int)lk));
+      p.part = std::max(p.part, xtb32_scratch(v, p.r[k]));
+    }
     if (p.q > 0) p.wbuf = std::max(p.wbuf, (size_t)cols * lk * ta);
     p.ymat = std::max(p.ymat, (size_t)v.n * lk * sizeof(double));
     if (p.bf16 && p.q >= 2) {
@@ -178,10 +186,11 @@ size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
 // Sketch, q shifted power steps and the final svd for mode k of X
 // (Algorithm 2/3 steps for one k).  Leaves Q (n x l) and Sigma in ws.
 static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt, View v,
-                             uint64_t seed, uint32_t tag, const HosvdWs& w, cudaStream_t st) {
+                             int64_t ka, int64_t kb, uint64_t seed, uint32_t tag,
+                             const HosvdWs& w, cudaStream_t st) {
   const int l = p.l[k];
   const int lc = xb_lc(l);
-  const int splits = xb_splits(v, l);
+  const int splits = xb_splits(xt, v, l);
   const bool fp64 = xt == X_F64;
   double* sig = w.sig + (size_t)k * TK_MAX_L;
   const double N = (double)v.P * (double)v.n * (double)v.S;
@@ -190,7 +199,7 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
   const double svd_flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
   {
     ProfScope ps(TK_K_SKETCH, N * xsize(xt), 2.0 * N * l, st);
-    TK_TRY(launch_xb(xt, X, v, nullptr, l, seed, tag, k, w.part, splits, st));
+    TK_TRY(launch_xb(xt, X, v, nullptr, l, seed, tag, k, w.part, splits, st, ka, kb));
   }
   {
     ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
@@ -232,7 +241,7 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     } else {
       {
         ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
-        TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st));
+        TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st, 0, w.part));
       }
       {
         ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
@@ -256,10 +265,10 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
 // TTM shrink G <- G x_k U_k^T with U_k = Q(:, 1:r_k) (Algorithm 2/3, last
 // step of each k), instrumented.
 static cudaError_t ttm(XType xt, const void* X, View v, const double* U, int r, void* out,
-                       cudaStream_t st) {
+                       cudaStream_t st, int tout = 0, void* scratch = nullptr) {
   const double N = (double)v.P * (double)v.n * (double)v.S;
   ProfScope ps(TK_K_TTM, (N + N / v.n * r) * xsize(xt), 2.0 * N * r, st);
-  return launch_xtb(xt, X, v, U, 1, v.n, r, out, st);
+  return launch_xtb(xt, X, v, U, 1, v.n, r, out, st, tout, scratch);
 }
 
 static cudaError_t polish(double* Q, int64_t n, int r, void* scratch, int* status,
@@ -300,13 +309,14 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
       int pp = 0;
       for (int step = 0; step < p.d; ++step) {
         const int k = p.order[step];
-        const View v = view_of(cur, k);
-        tk_status e = factor_mode(p, k, X, p.xt, v, o->seed, o->tag, w, st);
+        int64_t ka, kb;
+        const View v = step_view(p, cur, k, &ka, &kb);
+        tk_status e = factor_mode(p, k, X, p.xt, v, ka, kb, o->seed, o->tag, w, st);
         if (e != TK_OK) return e;
         if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
         TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
         void* out = (step == p.d - 1) ? core : w.g[pp];
-        TK_TRY(ttm(p.xt, X, v, w.Q, p.r[k], out, st));
+        TK_TRY(ttm(p.xt, X, v, w.Q, p.r[k], out, st, p.rot ? 1 : 0, w.part));
         X = out;
         pp ^= 1;
         cur[k] = p.r[k];
@@ -318,7 +328,7 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
         qd[k] = (double*)((unsigned char*)w.qd + off);
         off += al((size_t)p.n[k] * p.r[k] * sizeof(double));
         const View v = view_of(p.n, k);
-        tk_status e = factor_mode(p, k, A->data, p.xt, v, o->seed, o->tag, w, st);
+        tk_status e = factor_mode(p, k, A->data, p.xt, v, 0, 1, o->seed, o->tag, w, st);
         if (e != TK_OK) return e;
         if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
         TK_TRY(launch_copy_matrix(w.Q, v.n, qd[k], v.n, v.n, p.r[k], X_F64, st));
@@ -411,7 +421,7 @@ tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_
   std::vector<int64_t> dims(A->n, A->n + A->d);
   const View v = view_of(dims, k);
   const XType xt = xtype(A->dtype);
-  const int splits = xb_splits(v, l);
+  const int splits = xb_splits(xt, v, l);
   const int lc = xb_lc(l);
   void* part = nullptr;
   TK_TRY(cudaMallocAsync(&part, (size_t)splits * v.n * lc * asize(xt), st));
@@ -436,7 +446,7 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
   const bool fp64 = xt == X_F64;
   const SmallPlan sp = small_plan(v.n, l, fp64);
   if (sp.Pb <= 0) return TK_ENOTIMPL;
-  const int splits = xb_splits(v, l);
+  const int splits = xb_splits(xt, v, l);
   const int lc = xb_lc(l);
   // bfloat16 mode-major tensors take the fused tensor-core pass
   const bool tc = xt == X_BF16 && power_tc_supported(v, l, A->data);

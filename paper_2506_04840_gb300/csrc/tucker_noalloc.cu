@@ -64,7 +64,7 @@ extern "C" tk_status tucker_sketch_noalloc(const tk_tensor* A, int k, int l, uin
   const int lc = xb_lc(l);
   const size_t per_split = (size_t)v.n * lc * asize(xt);
   if (per_split > (size_t)TK_NOALLOC_SCRATCH_BYTES) return TK_EWORKSPACE;
-  int splits = xb_splits(v, l);
+  int splits = xb_splits(xt, v, l);
   const int fit = (int)((size_t)TK_NOALLOC_SCRATCH_BYTES / per_split);
   if (splits > fit) splits = fit;
   void* part = nullptr;
