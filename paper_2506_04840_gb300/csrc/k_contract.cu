@@ -141,8 +141,18 @@ __device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int spl
   if (idx >= n * l) return;
   const int c = (int)(idx % l);
   const int64_t i = idx / l;
-  double s = 0.0;
-  for (int sp = 0; sp < splits; ++sp) s += (double)part[((int64_t)sp * n + i) * lc + c];
+  // eight independent partial sums keep eight loads in flight; combined in
+  // a fixed order
+  const TA* src = part + i * lc + c;
+  const int64_t stride = n * lc;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int sp = 0;
+  for (; sp + 8 <= splits; sp += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] += (double)src[(int64_t)(sp + u) * stride];
+  }
+  for (int u = 0; sp < splits; ++sp, ++u) a[u] += (double)src[(int64_t)sp * stride];
+  double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   if (Q != nullptr) s -= alpha[0] * Q[i + n * c];
   Y[i + n * c] = s;
 }

@@ -330,33 +330,17 @@ __device__ __forceinline__ void shift_update(double sl, int rule, double* alpha,
   if (sigl_hist) sigl_hist[0] = sl;
 }
 
-// Sign convention on columns of Q (n x l, global), one warp per column.
-__device__ void sign_fix_block(double* Q, int64_t n, int l) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < l; c += nw) {
-    double* q = Q + n * c;
-    double best = -1.0;
-    int64_t bi = 0;
-    for (int64_t i = lane; i < n; i += 32) {
-      const double v = fabs(q[i]);
-      if (v > best) { best = v; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    const bool neg = q[bi] < 0.0;
-    if (neg)
-      for (int64_t i = lane; i < n; i += 32) q[i] = -q[i];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Single-CTA path: Y (n x l) fits in shared memory.
-// smem: A (n*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l)
+// smem: A (n*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l) [| B (n*l)]
+// With room for B, Q = H_0 ... H_{l-1} [U_R; 0] is formed by applying the
+// reflectors to U_R directly (no separate Q_h and product).
 // ---------------------------------------------------------------------------
+constexpr size_t kSvdSmemBudget = 200 * 1024;
+
+__host__ __device__ __forceinline__ bool svd_fused_fits(int64_t n, int l, size_t es) {
+  return (2 * (size_t)n * l + 2 * (size_t)l * l + 2 * (size_t)l) * es <= kSvdSmemBudget;
+}
 template <typename T>
 __device__ __forceinline__ void svd_one_body(const double* __restrict__ Y, int n, int l,
                                              double* __restrict__ Q, double* __restrict__ sigma,
@@ -408,18 +392,86 @@ __device__ __forceinline__ void svd_one_body(const double* __restrict__ Y, int n
   jacobi_warp(J, Vp, l);
   __syncthreads();
   sigma_perm(J, l, sg, perm, Vp);
+  if (svd_fused_fits(n, l, sizeof(T))) {
+    T* Bm = ts + l;
+    // B = [U_R; 0] with U_R = Vp in perm order
+    for (int64_t e = tid; e < (int64_t)n * l; e += blockDim.x) {
+      const int i = (int)(e % n), c = (int)(e / n);
+      Bm[e] = i < l ? Vp[i + (int64_t)l * perm[c]] : (T)0;
+    }
+    __syncthreads();
+    // B <- H_0 H_1 ... H_{l-1} B (H_{l-1} first); H_j = I - tau_j v_j v_j^T,
+    // v_j = (0..0, 1, A[j+1:, j])
+    for (int j = l - 1; j >= 0; --j) {
+      const T tj = ts[j];
+      const T* v = A + (int64_t)n * j;
+      if (tj != (T)0) {
+        for (int c = warp; c < l; c += nw) {
+          T* y = Bm + (int64_t)n * c;
+          T w = lane == 0 ? y[j] : (T)0;
+          for (int i = j + 1 + lane; i < n; i += 32) w += v[i] * y[i];
+          w = warp_sum(w) * tj;
+          if (lane == 0) y[j] -= w;
+          for (int i = j + 1 + lane; i < n; i += 32) y[i] -= w * v[i];
+        }
+      }
+      __syncthreads();
+    }
+    // sign convention (entry of largest magnitude positive, lowest row on
+    // ties), one warp per column, then the FP64 store
+    for (int c = warp; c < l; c += nw) {
+      const T* y = Bm + (int64_t)n * c;
+      T best = (T)-1;
+      int bi = 0;
+      for (int i = lane; i < n; i += 32) {
+        const T av = (T)fabs(y[i]);
+        if (av > best) { best = av; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      const T sgn = y[bi] < (T)0 ? (T)-1 : (T)1;
+      for (int i = lane; i < n; i += 32) Q[i + (int64_t)n * c] = (double)(sgn * y[i]);
+    }
+  } else {
   form_q_inplace(A, n, l, ts);
-  // Q = Q_h U_R (U_R = Vp with columns in perm order), row by row
-  for (int i = tid; i < n; i += blockDim.x) {
-    for (int c = 0; c < l; ++c) {
-      const T* u = Vp + (int64_t)l * perm[c];
+  // Q = Q_h U_R (U_R = Vp with columns in perm order), one warp per column:
+  // a first pass finds the entry of largest magnitude (lowest row on ties),
+  // the second recomputes the column and stores it with that entry positive
+  for (int c = warp; c < l; c += nw) {
+    const T* u = Vp + (int64_t)l * perm[c];
+    T best = (T)-1;
+    int bi = 0;
+    for (int i = lane; i < n; i += 32) {
       T s = 0;
       for (int k = 0; k < l; ++k) s += A[i + (int64_t)n * k] * u[k];
-      Q[i + (int64_t)n * c] = (double)s;
+      const T av = (T)fabs(s);
+      if (av > best) { best = av; bi = i; }
+    }
+    T bval = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) {
+      T s = 0;
+      for (int k = 0; k < l; ++k) s += A[bi + (int64_t)n * k] * u[k];
+      bval = s;
+    }
+    bval = __shfl_sync(0xffffffffu, bval, 0);
+    const T sgn = bval < (T)0 ? (T)-1 : (T)1;
+    for (int i = lane; i < n; i += 32) {
+      T s = 0;
+      for (int k = 0; k < l; ++k) s += A[i + (int64_t)n * k] * u[k];
+      Q[i + (int64_t)n * c] = (double)(sgn * s);
     }
   }
-  __syncthreads();
-  sign_fix_block(Q, n, l);
+  }
   if (tid < l) {
     const double sv = (double)sg[perm[tid]] / scale;
     sigma[tid] = sv;
@@ -638,21 +690,31 @@ __device__ __forceinline__ void polish_body(double* __restrict__ U, int64_t n, i
     const int i = e % kPolishRows, c = e / kPolishRows;
     Ub[e] = i < rows ? U[(r0 + i) + n * c] : 0.0;
   }
+  __shared__ double rinv[TK_MAX_L];
   __syncthreads();
-  // Cholesky, upper factor in place: R(i, j) for i <= j, R^T R = G.
+  // Cholesky, upper factor in place: R(i, j) for i <= j, R^T R = G.  FP64
+  // division and square root are slow on this GPU, so each diagonal entry is
+  // inverted once (by the warp that forms it) and rows are scaled by it.
+  const int lane = tid & 31;
   for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      double d = R[j + r * j];
-      for (int k = 0; k < j; ++k) d -= R[k + r * j] * R[k + r * j];
-      if (!(d > 0.0)) { bad = 1; d = 1.0; }
-      R[j + r * j] = sqrt(d);
+    if (tid < 32) {
+      double d = 0.0;
+      for (int k = lane; k < j; k += 32) d += R[k + r * j] * R[k + r * j];
+      d = warp_sum(d);
+      if (lane == 0) {
+        double g = R[j + r * j] - d;
+        if (!(g > 0.0)) { bad = 1; g = 1.0; }
+        const double rj = sqrt(g);
+        R[j + r * j] = rj;
+        rinv[j] = 1.0 / rj;
+      }
     }
     __syncthreads();
-    const double djj = R[j + r * j];
+    const double ij = rinv[j];
     for (int c = j + 1 + tid; c < r; c += blockDim.x) {
       double s = R[j + r * c];
       for (int k = 0; k < j; ++k) s -= R[k + r * j] * R[k + r * c];
-      R[j + r * c] = s / djj;
+      R[j + r * c] = s * ij;
     }
     __syncthreads();
   }
@@ -665,7 +727,7 @@ __device__ __forceinline__ void polish_body(double* __restrict__ U, int64_t n, i
     for (int c = 0; c < r; ++c) {
       double s = Ub[i + kPolishRows * c];
       for (int k = 0; k < c; ++k) s -= Ub[i + kPolishRows * k] * R[k + r * c];
-      Ub[i + kPolishRows * c] = s / R[c + r * c];
+      Ub[i + kPolishRows * c] = s * rinv[c];
     }
   }
   __syncthreads();
@@ -703,12 +765,13 @@ cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* statu
 }
 
 // ---------------------------------------------------------------------------
-static const size_t kSmemBudget = 200 * 1024;
+static const size_t kSmemBudget = kSvdSmemBudget;
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t one_smem(int64_t n, int l, size_t es) {
-  return ((size_t)n * l + 2 * (size_t)l * l + 2 * (size_t)l) * es;
+  const size_t base = ((size_t)n * l + 2 * (size_t)l * l + 2 * (size_t)l) * es;
+  return svd_fused_fits(n, l, es) ? base + (size_t)n * l * es : base;
 }
 static size_t root_smem(int Pb, int l, size_t es) {
   return ((size_t)Pb * l * l + 2 * (size_t)l * l + 2 * (size_t)l) * es;
