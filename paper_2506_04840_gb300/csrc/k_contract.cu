@@ -130,31 +130,41 @@ k_xb(const TX* __restrict__ X, int64_t P, int64_t n, int64_t S,
                              blockIdx.y);
 }
 
+// Y[i, c] = sum over splits of part[split][i][c] (- alpha Q[i, c]).  A block
+// of 256 threads owns 32 consecutive outputs (c fastest: coalesced reads of
+// the partials); its 8 warps take every 8th split and the 8 warp sums are
+// added in a fixed order.
 template <typename TA>
 __device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int splits, int64_t n,
                                             int l, int lc, const double* __restrict__ Q,
                                             const double* __restrict__ alpha,
                                             double* __restrict__ Y, unsigned bx) {
-  // consecutive threads take consecutive columns c of one row: coalesced
-  // reads of the [split][i][c] partials
-  const int64_t idx = (int64_t)bx * 256 + threadIdx.x;
-  if (idx >= n * l) return;
-  const int c = (int)(idx % l);
-  const int64_t i = idx / l;
-  // eight independent partial sums keep eight loads in flight; combined in
-  // a fixed order
-  const TA* src = part + i * lc + c;
-  const int64_t stride = n * lc;
-  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int sp = 0;
-  for (; sp + 8 <= splits; sp += 8) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] += (double)src[(int64_t)(sp + u) * stride];
+  __shared__ double red[8][32];
+  const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t idx = (int64_t)bx * 32 + o;
+  const bool valid = idx < n * l;
+  const int c = valid ? (int)(idx % l) : 0;
+  const int64_t i = valid ? idx / l : 0;
+  double s0 = 0.0, s1 = 0.0;
+  if (valid) {
+    const TA* src = part + i * lc + c;
+    const int64_t stride = n * lc;
+    int sp = g;
+    for (; sp + 8 < splits; sp += 16) {
+      s0 += (double)src[(int64_t)sp * stride];
+      s1 += (double)src[(int64_t)(sp + 8) * stride];
+    }
+    if (sp < splits) s0 += (double)src[(int64_t)sp * stride];
   }
-  for (int u = 0; sp < splits; ++sp, ++u) a[u] += (double)src[(int64_t)sp * stride];
-  double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-  if (Q != nullptr) s -= alpha[0] * Q[i + n * c];
-  Y[i + n * c] = s;
+  red[g][o] = s0 + s1;
+  __syncthreads();
+  if (g == 0 && valid) {
+    double s = ((red[0][o] + red[1][o]) + (red[2][o] + red[3][o])) +
+               ((red[4][o] + red[5][o]) + (red[6][o] + red[7][o]));
+    if (Q != nullptr) s -= alpha[0] * Q[i + n * c];
+    Y[i + n * c] = s;
+  }
+  __syncthreads();
 }
 
 template <typename TA>
@@ -522,7 +532,7 @@ cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int
                           const double* Q, const double* alpha, double* Y, cudaStream_t st) {
   const int64_t tot = n * l;
   if (tot <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((tot + 255) / 256);
+  const unsigned blocks = (unsigned)((tot + 31) / 32);
   count_kernels(1);
   if (xt == X_F64)
     k_reduce<double><<<blocks, 256, 0, st>>>((const double*)part, splits, n, l, lc, Q, alpha, Y);

@@ -202,7 +202,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       ph.push_back(xb_op(0, TK_K_SKETCH, xt, X, v, nullptr, l, it.seed, it.tag, k, w.part, splits,
                          N * es, 2.0 * N * l, ka, kb));
       ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc};
-      ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
+      ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,
                 0, p.q >= 1 ? 1 : 0};
@@ -218,7 +218,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       ph.push_back(xb_op(2, TK_K_POWER_Y, xt, X, v, w.w, l, it.seed, it.tag, k, w.part, splits,
                          N * es, 2.0 * N * l));
       ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc};
-      ph.push_back(make_op(3, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 256),
+      ph.push_back(make_op(3, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
                 stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,

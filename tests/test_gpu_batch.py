@@ -133,3 +133,18 @@ def test_batch_many_items_share_the_grid(lib):
     for i in (0, 7, 19, 39):
         A, r, s, q = insts[i]
         assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+
+
+def test_batch_row_split_products_bitwise(lib):
+    """Items whose later modes have few columns and long rows: the FP32
+    mode-major products split their rows over several CTAs (partials summed
+    in a fixed order), in the batch exactly as in the single calls."""
+    insts = []
+    for i, shape in enumerate([(300, 40, 20), (256, 180, 30), (200, 150, 9, 12)]):
+        r = [min(8, n - 1) for n in shape]
+        A = I.tucker_plus_noise(list(shape), r, 50 + i, noise=1e-3, noise_mode="relative",
+                                dtype=np.float32)
+        insts.append((A, r, 4, 2))
+    outs, _ = _run_batch(insts, True)
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
