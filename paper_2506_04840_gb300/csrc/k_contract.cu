@@ -580,7 +580,8 @@ cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t
   }
 }
 
-int xtb_error_blocks(View v, int m) {
+int xtb_error_blocks(XType xt, View v, int m) {
+  if (err32_ok(xt, v)) return err32_blocks(v, m);
   const int lc = xtb_lc(m);
   return (int)(((v.cols() + 127) / 128) * ((m + lc - 1) / lc));
 }
@@ -588,8 +589,9 @@ int xtb_error_blocks(View v, int m) {
 cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
                              int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
                              cudaStream_t st) {
-  *blocks = xtb_error_blocks(v, m);
+  *blocks = xtb_error_blocks(xt, v, m);
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
+  if (err32_ok(xt, v)) return launch_err32(T, v, B, b_ri, b_cm, m, A, err_part, st);
   if (xt == X_F64) return xtb_lc_go<double, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
   return xtb_lc_go<float, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
 }

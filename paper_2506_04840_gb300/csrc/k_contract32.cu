@@ -347,6 +347,148 @@ k_xb32_batch(const Xb32Job* __restrict__ jobs, const uint32_t* __restrict__ star
   }
 }
 
+// ---------------------------------------------------------------------------
+// Last-mode expansion fused with the error sums (relative error, Section 5):
+// for S == 1, a_hat(p, c) = sum_{i < K} T[p + P i] B(i, c) with B(i, c) =
+// Bm[i*b_ri + c*b_cm]; the block adds (A[p + P c] - a_hat)^2 and A^2 over its
+// 128 x 64 tile (p, c) and writes the two sums to err[2 blk], blk = by gx + bx.
+// a_hat is never stored.  Thread tile 8 p x 4 c (lanes 8 x 4, warps 2 x 4).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t P, int K,
+                                           const double* __restrict__ Bm, int64_t b_ri,
+                                           int64_t b_cm, int m, const float* __restrict__ A,
+                                           double* __restrict__ err, unsigned bx, unsigned by,
+                                           unsigned gx) {
+  constexpr int MP = 128, MC = 64, T = 256;
+  constexpr int XPT = KS * MP / T;                  // 8
+  constexpr int BPT = KS * MC / T;                  // 4
+  __shared__ __align__(16) float Ts[2][KS][MP + 4];
+  __shared__ __align__(16) float Bs[2][KS][MC];
+  __shared__ double red[2][8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wp = w & 1, wc = w >> 1;
+  const int lp = lane >> 2, lc = lane & 3;
+  const int64_t p0 = (int64_t)bx * MP;
+  const int c0 = (int)by * MC;
+  const int pa = wp * 64 + lp * 4;
+  const int cb = wc * 16 + lc * 4;
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  float tr[XPT], br[BPT];
+  auto load = [&](int i0) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      const int pp = e % MP, ii = e / MP;
+      const int64_t p = p0 + pp;
+      const int i = i0 + ii;
+      tr[r] = (p < P && i < K) ? __ldg(Tt + p + P * i) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < BPT; ++r) {
+      const int e = tid + r * T;
+      const int c = e % MC, ii = e / MC;
+      const int i = i0 + ii;
+      br[r] = (i < K && c0 + c < m) ? (float)Bm[(int64_t)i * b_ri + (int64_t)(c0 + c) * b_cm]
+                                    : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < XPT; ++r) {
+      const int e = tid + r * T;
+      Ts[buf][e / MP][e % MP] = tr[r];
+    }
+#pragma unroll
+    for (int r = 0; r < BPT; ++r) {
+      const int e = tid + r * T;
+      Bs[buf][e / MC][e % MC] = br[r];
+    }
+  };
+  const int nsl = (K + KS - 1) / KS;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int s = 0; s < nsl; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < nsl) load((s + 1) * KS);
+#pragma unroll
+    for (int ii = 0; ii < KS; ++ii) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Ts[buf][ii][pa]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Ts[buf][ii][pa + 32]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][ii][cb]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+    }
+    if (s + 1 < nsl) store(buf ^ 1);
+    __syncthreads();
+  }
+  // squared differences: per-thread FP32 sums of 32 terms, then FP64
+  float e2t = 0.f, a2t = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = c0 + cb + q;
+    if (c >= m) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t p = p0 + pa + (a < 4 ? a : 28 + a);
+      if (p >= P) continue;
+      const float av = __ldg(A + p + P * c);
+      const float dv = av - acc[a][q];
+      e2t = fmaf(dv, dv, e2t);
+      a2t = fmaf(av, av, a2t);
+    }
+  }
+  double e2 = (double)e2t, a2 = (double)a2t;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    red[0][w] = e2;
+    red[1][w] = a2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double se = 0.0, sa = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      se += red[0][k];
+      sa += red[1][k];
+    }
+    const int64_t blk = (int64_t)by * gx + bx;
+    err[2 * blk] = se;
+    err[2 * blk + 1] = sa;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+k_err32(const float* __restrict__ Tt, int64_t P, int K, const double* __restrict__ Bm,
+        int64_t b_ri, int64_t b_cm, int m, const float* __restrict__ A,
+        double* __restrict__ err) {
+  err32_body(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+              uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const Err32Job J = jobs[j];
+    const uint32_t lb = b - __ldg(start + j);
+    err32_body((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A, J.err,
+               lb % (uint32_t)J.gx, lb / (uint32_t)J.gx, (uint32_t)J.gx);
+  }
+}
+
 }  // namespace c32
 
 // ---------------------------------------------------------------------------
@@ -489,10 +631,27 @@ cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t se
   return cudaGetLastError();
 }
 
+bool err32_ok(XType xt, View v) { return xt == X_F32 && v.S == 1 && v.P >= 1; }
+
+int err32_blocks(View v, int m) {
+  return (int)(((v.P + 127) / 128) * ((m + 63) / 64));
+}
+
+cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                         int m, const void* A, double* err_part, cudaStream_t st) {
+  if (v.P <= 0 || m <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((v.P + 127) / 128), (unsigned)((m + 63) / 64));
+  count_kernels(1);
+  c32::k_err32<<<grid, 256, 0, st>>>((const float*)T, v.P, (int)v.n, B, b_ri, b_cm, m,
+                                     (const float*)A, err_part);
+  return cudaGetLastError();
+}
+
 // Work-list launches: tile = WC, flag = (omega ? 1 : 0) | (WI or WJ) << 1.
 cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st) {
   const int wc = b.tile, wx = b.flag >> 1, omega = b.flag & 1;
   if (b.kind == BK_XTB32RED) return run_batch(c32::k_xtb32_red_batch, b, 256, st);
+  if (b.kind == BK_ERR32) return run_batch(c32::k_err32_batch, b, 256, st);
   if (b.kind == BK_XTB32) {
     if (wc == 1) return run_batch(c32::k_xtb32_batch<4, 1>, b, 128, st);
     if (wc == 2) return run_batch(c32::k_xtb32_batch<4, 2>, b, 256, st);

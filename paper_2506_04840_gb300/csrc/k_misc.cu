@@ -145,6 +145,7 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
     case BK_XTB32:
     case BK_XB32:
     case BK_XTB32RED:
+    case BK_ERR32:
       return launch_batch_c32(b, st);
     default:
       return launch_batch_misc(b, st);

@@ -101,6 +101,16 @@ struct Xtb32Job {
   int64_t kps;          // rows per split
   int m, gx, gy, tout;
 };
+// Last-mode expansion fused with the squared-difference sums (S == 1).
+struct Err32Job {
+  const void* T;
+  int64_t P;
+  const double* B;
+  int64_t b_ri, b_cm;
+  const void* A;
+  double* err;
+  int K, m, gx;
+};
 struct Xtb32RedJob {
   const void* part;
   void* out;
@@ -120,7 +130,7 @@ struct Xb32Job {
 
 enum BatchKind {
   BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
-  BK_XB32, BK_XTB32RED
+  BK_XB32, BK_XTB32RED, BK_ERR32
 };
 
 constexpr size_t kJobBytes = 128;   // every job struct fits

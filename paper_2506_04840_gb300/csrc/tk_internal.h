@@ -53,6 +53,12 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
                          int m, void* out, cudaStream_t st, int tout = 0,
                          void* scratch = nullptr);
 size_t xtb32_scratch(View v, int m);
+// FP32 last-mode expansion fused with the error sums (S == 1): err_part gets
+// err32_blocks(v, m) (e^2, a^2) pairs.
+bool err32_ok(XType xt, View v);
+int err32_blocks(View v, int m);
+cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                         int m, const void* A, double* err_part, cudaStream_t st);
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka = 0,
                         int64_t kb = 1);
@@ -78,7 +84,7 @@ cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t
 cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
                              int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
                              cudaStream_t st);
-int xtb_error_blocks(View v, int m);
+int xtb_error_blocks(XType xt, View v, int m);
 cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_err,
                                cudaStream_t st);
 

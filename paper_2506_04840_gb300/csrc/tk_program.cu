@@ -40,6 +40,7 @@ size_t job_size(int kind) {
     case BK_COPY: return sizeof(CopyJob);
     case BK_XTB32: return sizeof(Xtb32Job);
     case BK_XTB32RED: return sizeof(Xtb32RedJob);
+    case BK_ERR32: return sizeof(Err32Job);
     case BK_XB32: return sizeof(Xb32Job);
     default: return sizeof(ErrFinalJob);
   }
@@ -124,7 +125,7 @@ size_t layout(const tk_item& it, const HosvdPlan& p, Extras* ex) {
     ex->tb[1] = a.offset(tbuf);
     std::vector<int64_t> last(p.r.begin(), p.r.end());
     for (int k = 0; k < d - 1; ++k) last[k] = p.n[k];
-    ex->eblocks = xtb_error_blocks(view_of(last, d - 1), (int)p.n[d - 1]);
+    ex->eblocks = xtb_error_blocks(p.xt, view_of(last, d - 1), (int)p.n[d - 1]);
     ex->ep = a.offset((size_t)ex->eblocks * 2 * sizeof(double));
   }
   return al(a.off);
@@ -281,9 +282,17 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     const int egx = (int)cdiv(vl.cols(), 128);
     const double Nf = (double)vl.P * (double)m;
     double* ep = (double*)(base + ex.ep);
-    XtbJob ej{Xe, vl.P, vl.n, vl.S, qd[d - 1], p.n[d - 1], 1, nullptr, it.A.data, ep, m, egx};
-    ph.push_back(make_op(d - 1, TK_K_ERROR, BK_XTB, xt, mt, 1, 0, (uint32_t)egx * cdiv(m, mt),
-                         Nf * es + (double)vl.P * vl.n * es, 2.0 * Nf * vl.n, ej));
+    if (err32_ok(xt, vl)) {
+      const int gx = (int)cdiv(vl.P, 128);
+      Err32Job ej{Xe, vl.P, qd[d - 1], p.n[d - 1], 1, it.A.data, ep, (int)vl.n, m, gx};
+      ph.push_back(make_op(d - 1, TK_K_ERROR, BK_ERR32, xt, 0, 0, 0,
+                           (uint32_t)gx * cdiv(m, 64), Nf * es + (double)vl.P * vl.n * es,
+                           2.0 * Nf * vl.n, ej));
+    } else {
+      XtbJob ej{Xe, vl.P, vl.n, vl.S, qd[d - 1], p.n[d - 1], 1, nullptr, it.A.data, ep, m, egx};
+      ph.push_back(make_op(d - 1, TK_K_ERROR, BK_XTB, xt, mt, 1, 0, (uint32_t)egx * cdiv(m, mt),
+                           Nf * es + (double)vl.P * vl.n * es, 2.0 * Nf * vl.n, ej));
+    }
     ErrFinalJob fj{ep, it.rel_err, ex.eblocks};
     ph.push_back(make_op(d, TK_K_ERROR, BK_ERRFIN, X_F64, 0, 0, 0, 1, 0.0, 0.0, fj));
     prog.push_back(ph);

@@ -534,7 +534,7 @@ tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const
   std::vector<int64_t> last(r, r + d);
   for (int k = 0; k < d - 1; ++k) last[k] = A->n[k];
   const View vl = view_of(last, d - 1);
-  const int blocks = xtb_error_blocks(vl, (int)A->n[d - 1]);
+  const int blocks = xtb_error_blocks(xt, vl, (int)A->n[d - 1]);
   Arena a;
   const size_t t0 = a.offset(tbuf);
   const size_t t1 = a.offset(tbuf);
