@@ -138,7 +138,8 @@ template <typename TA>
 __device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int splits, int64_t n,
                                             int l, int lc, const double* __restrict__ Q,
                                             const double* __restrict__ alpha,
-                                            double* __restrict__ Y, unsigned bx) {
+                                            double* __restrict__ Y, unsigned bx,
+                                            const TA* __restrict__ part_lo = nullptr) {
   __shared__ double red[8][32];
   const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int64_t idx = (int64_t)bx * 32 + o;
@@ -155,6 +156,10 @@ __device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int spl
       s1 += (double)src[(int64_t)(sp + 8) * stride];
     }
     if (sp < splits) s0 += (double)src[(int64_t)sp * stride];
+    if (part_lo != nullptr) {
+      const TA* lo = part_lo + i * lc + c;
+      for (sp = g; sp < splits; sp += 8) s1 += (double)lo[(int64_t)sp * stride];
+    }
   }
   red[g][o] = s0 + s1;
   __syncthreads();
@@ -170,8 +175,9 @@ __device__ __forceinline__ void reduce_body(const TA* __restrict__ part, int spl
 template <typename TA>
 __global__ void __launch_bounds__(256)
 k_reduce(const TA* __restrict__ part, int splits, int64_t n, int l, int lc,
-         const double* __restrict__ Q, const double* __restrict__ alpha, double* __restrict__ Y) {
-  reduce_body<TA>(part, splits, n, l, lc, Q, alpha, Y, blockIdx.x);
+         const double* __restrict__ Q, const double* __restrict__ alpha, double* __restrict__ Y,
+         const TA* __restrict__ part_lo) {
+  reduce_body<TA>(part, splits, n, l, lc, Q, alpha, Y, blockIdx.x, part_lo);
 }
 
 // out[j, c] = sum_i X(p, i, s) B(i, c) for a tile of TJ columns and LC
@@ -515,10 +521,11 @@ static cudaError_t xb_lc_dispatch(const void* X, View v, const void* W, int l, u
 
 cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
                       uint32_t tag, int mode, void* part, int splits, cudaStream_t st,
-                      int64_t ka, int64_t kb) {
+                      int64_t ka, int64_t kb, void* part_lo) {
   if (v.n <= 0 || v.cols() <= 0 || l <= 0) return cudaSuccess;
   if (xtb32_ok(xt, v, X))
-    return launch_xb32(X, v, W, l, seed, tag, mode, part, splits, st, ka, kb);
+    return launch_xb32(X, v, W, l, seed, tag, mode, part, splits, st, ka, kb, part_lo);
+  if (part_lo != nullptr) return cudaErrorInvalidValue;
   if (ka > 0 && W == nullptr && ka != v.cols()) return cudaErrorInvalidValue;
   switch (xt) {
     case X_F64: return xb_lc_dispatch<double>(X, v, W, l, seed, tag, mode, part, splits, st);
@@ -529,15 +536,18 @@ cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uin
 }
 
 cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int l, int lc,
-                          const double* Q, const double* alpha, double* Y, cudaStream_t st) {
+                          const double* Q, const double* alpha, double* Y, cudaStream_t st,
+                          const void* part_lo) {
   const int64_t tot = n * l;
   if (tot <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((tot + 31) / 32);
   count_kernels(1);
   if (xt == X_F64)
-    k_reduce<double><<<blocks, 256, 0, st>>>((const double*)part, splits, n, l, lc, Q, alpha, Y);
+    k_reduce<double><<<blocks, 256, 0, st>>>((const double*)part, splits, n, l, lc, Q, alpha, Y,
+                                             (const double*)part_lo);
   else
-    k_reduce<float><<<blocks, 256, 0, st>>>((const float*)part, splits, n, l, lc, Q, alpha, Y);
+    k_reduce<float><<<blocks, 256, 0, st>>>((const float*)part, splits, n, l, lc, Q, alpha, Y,
+                                            (const float*)part_lo);
   return cudaGetLastError();
 }
 

@@ -133,12 +133,18 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 // jk = j / ka + kb (j % ka) maps the layout's column order to the unfolding's
 // (ka = columns, kb = 1 for the natural layout).
 // ---------------------------------------------------------------------------
-template <int WI, int WC, bool OMEGA>
+// COMP: compensated accumulation (Dot2: an exact product residual by FMA and
+// a TwoSum per term, with correctly rounded operations so nothing is
+// contracted), written as a (hi, lo) pair of partials: hi to part, lo to
+// part_lo.  Used where a product must resolve directions far below FP32
+// rounding of its running sums.
+template <int WI, int WC, bool OMEGA, bool COMP = false>
 __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
                                           const float* __restrict__ W, int l, int lc,
                                           uint64_t seed, uint32_t tag, int mode, int64_t cps,
                                           int64_t ka, int64_t kb, float* __restrict__ part,
-                                          unsigned bx, unsigned by, unsigned bz) {
+                                          unsigned bx, unsigned by, unsigned bz,
+                                          float* __restrict__ part_lo = nullptr) {
   constexpr int MI = 64 * WI, MC = 16 * WC, T = 32 * WI * WC;
   constexpr int XPT = KS * MI / T;
   constexpr int BPT = (KS * MC + T - 1) / T;
@@ -160,6 +166,11 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  float cmp[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cmp[a][q] = 0.f;
 
   float xr[XPT], br[OMEGA ? 4 * OPT : BPT];
   auto load = [&](int64_t j0) {
@@ -245,12 +256,25 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+        for (int q = 0; q < 4; ++q) {
+          if (COMP) {
+            const float pr = __fmul_rn(av[a], bv[q]);
+            const float pe = __fmaf_rn(av[a], bv[q], -pr);
+            const float t = __fadd_rn(acc[a][q], pr);
+            const float z = __fsub_rn(t, acc[a][q]);
+            const float se = __fadd_rn(__fsub_rn(acc[a][q], __fsub_rn(t, z)), __fsub_rn(pr, z));
+            acc[a][q] = t;
+            cmp[a][q] = __fadd_rn(cmp[a][q], __fadd_rn(se, pe));
+          } else {
+            acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+          }
+        }
     }
     if (s + 1 < nsl) store(buf ^ 1);
     __syncthreads();
   }
   float* dst = part + (int64_t)bz * n * lc;
+  float* dlo = COMP ? part_lo + (int64_t)bz * n * lc : nullptr;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int64_t i = i0 + ia + (a < 4 ? a : 28 + a);
@@ -258,7 +282,14 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = c0 + cb + q;
-      if (c < lc) dst[i * lc + c] = acc[a][q];
+      if (c >= lc) continue;
+      if (COMP) {
+        const float hi = __fadd_rn(acc[a][q], cmp[a][q]);
+        dst[i * lc + c] = hi;
+        dlo[i * lc + c] = __fadd_rn(__fsub_rn(acc[a][q], hi), cmp[a][q]);
+      } else {
+        dst[i * lc + c] = acc[a][q];
+      }
     }
   }
 }
@@ -304,13 +335,13 @@ k_xtb32_red_batch(const Xtb32RedJob* __restrict__ jobs, const uint32_t* __restri
   }
 }
 
-template <int WI, int WC, bool OMEGA>
+template <int WI, int WC, bool OMEGA, bool COMP = false>
 __global__ void __launch_bounds__(32 * WI * WC)
 k_xb32(const float* __restrict__ X, int64_t n, int64_t cols, const float* __restrict__ W, int l,
        int lc, uint64_t seed, uint32_t tag, int mode, int64_t cps, int64_t ka, int64_t kb,
-       float* __restrict__ part) {
-  xb32_body<WI, WC, OMEGA>(X, n, cols, W, l, lc, seed, tag, mode, cps, ka, kb, part, blockIdx.x,
-                           blockIdx.y, blockIdx.z);
+       float* __restrict__ part, float* __restrict__ part_lo) {
+  xb32_body<WI, WC, OMEGA, COMP>(X, n, cols, W, l, lc, seed, tag, mode, cps, ka, kb, part,
+                                 blockIdx.x, blockIdx.y, blockIdx.z, part_lo);
 }
 
 template <int WJ, int WC>
@@ -588,31 +619,35 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
 template <int WI, int WC>
 static void xb32_go(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
                     int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
-                    cudaStream_t st) {
+                    cudaStream_t st, float* part_lo) {
   const dim3 grid(s.gx, s.gy, s.splits);
   if (W == nullptr)
     c32::k_xb32<WI, WC, true><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), nullptr, l, s.lc,
-                                                             seed, tag, mode, s.cps, ka, kb, part);
+                                                             seed, tag, mode, s.cps, ka, kb, part,
+                                                             nullptr);
+  else if (part_lo != nullptr)
+    c32::k_xb32<WI, WC, false, true><<<grid, 32 * WI * WC, 0, st>>>(
+        X, v.n, v.cols(), W, l, s.lc, seed, tag, mode, s.cps, ka, kb, part, part_lo);
   else
     c32::k_xb32<WI, WC, false><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), W, l, s.lc,
                                                               seed, tag, mode, s.cps, ka, kb,
-                                                              part);
+                                                              part, nullptr);
 }
 
 template <int WI>
 static void xb32_wc(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
                     int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
-                    cudaStream_t st) {
+                    cudaStream_t st, float* part_lo) {
   switch (s.wc) {
-    case 1: xb32_go<WI, 1>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
-    case 2: xb32_go<WI, 2>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
-    default: xb32_go<WI, 4>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st); break;
+    case 1: xb32_go<WI, 1>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
+    case 2: xb32_go<WI, 2>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
+    default: xb32_go<WI, 4>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
   }
 }
 
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka,
-                        int64_t kb) {
+                        int64_t kb, void* part_lo) {
   if (ka <= 0) {   // natural layout: the identity map
     ka = v.cols();
     kb = 1;
@@ -623,10 +658,11 @@ cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t se
   const float* x = (const float*)X;
   const float* w = (const float*)W;
   float* p = (float*)part;
+  float* plo = W != nullptr ? (float*)part_lo : nullptr;
   switch (s.wi) {
-    case 1: xb32_wc<1>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
-    case 2: xb32_wc<2>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
-    default: xb32_wc<4>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st); break;
+    case 1: xb32_wc<1>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
+    case 2: xb32_wc<2>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
+    default: xb32_wc<4>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
   }
   return cudaGetLastError();
 }

@@ -61,15 +61,19 @@ cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, i
                          int m, const void* A, double* err_part, cudaStream_t st);
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka = 0,
-                        int64_t kb = 1);
+                        int64_t kb = 1, void* part_lo = nullptr);
 // ka, kb: Omega row map of a rotated layout (see launch_xb32; FP32
 // mode-major views only; ka = 0 is the natural layout).
+// part_lo (FP32 mode-major Y = X W only): compensated accumulation, the
+// partials as (hi in part, lo in part_lo) pairs.
 cudaError_t launch_xb(XType xt, const void* X, View v, const void* W, int l, uint64_t seed,
                       uint32_t tag, int mode, void* part, int splits, cudaStream_t st,
-                      int64_t ka = 0, int64_t kb = 1);
+                      int64_t ka = 0, int64_t kb = 1, void* part_lo = nullptr);
 // Y = sum_split part - alpha*Q (Q, alpha may be NULL): n x l FP64.
+// part_lo: optional second plane of partials added to the first.
 cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int l, int lc,
-                          const double* Q, const double* alpha, double* Y, cudaStream_t st);
+                          const double* Q, const double* alpha, double* Y, cudaStream_t st,
+                          const void* part_lo = nullptr);
 // out(P, m, S) = X x_k B^T with B(i, c) at B[i*b_ri + c*b_cm] (FP64):
 // out[j, c] = sum_i X(p, i, s) B(i, c).  Output in the accumulation type of
 // X (or `out_bf16` when non-null: BF16 output is not supported here).

@@ -253,3 +253,26 @@ def test_bf16_form_accuracy(lib):
     assert reb <= 1.01 * re
     Gw, Uw, _ = T.rsthosvd(A, r, 6, 3, bf16_power=True)
     assert abs(reb - T.rel_error(A, Gw, Uw)) <= 1e-6
+
+
+def _inverse_radius(shape, seed, noise):
+    idx = np.indices(shape, dtype=np.float64) + 1.0
+    A0 = 1.0 / np.sqrt((idx ** 2).sum(axis=0))
+    rng = np.random.default_rng(seed)
+    E = rng.standard_normal(shape) * noise * np.linalg.norm(A0.ravel()) / np.sqrt(A0.size)
+    return np.asfortranarray((A0 + E).astype(np.float32))
+
+
+@pytest.mark.parametrize("prec", [api.TK_PREC_PLAIN, api.TK_PREC_BF16_POWER])
+def test_long_mode_matches_oracle(lib, prec):
+    """A 1000-row mode with l = 60: the two-level TSQR svd path, and in the
+    precision form the cluster-pair tensor-core pass, against the oracle."""
+    A = _inverse_radius((1000, 60, 48), 3, 1e-6)
+    r = [50, 20, 20]
+    bf = prec == api.TK_PREC_BF16_POWER
+    Gw, Uw, sw = T.rsthosvd(A, r, 10, 3, bf16_power=bf)
+    G, Us, info = run_hosvd(A, r, 10, 3, prec=prec)
+    re_w, re_g = T.rel_error(A, Gw, Uw), T.rel_error(A, G, Us)
+    assert abs(re_g - re_w) <= 1e-6, (re_g, re_w)
+    if not bf:
+        _check_factors(Us, Uw, sw, np.float32)

@@ -81,3 +81,29 @@ def test_fused_pass_is_used_and_timed(lib):
     api.tucker_profile_enable(False)
     assert prof["kinds"]["power_fused"]["launches"] == 1
     assert prof["kinds"]["power_w"]["launches"] == 0
+
+
+@pytest.mark.parametrize("shape,l", [((1000, 60, 48), 60), ((1000, 40, 50), 60),
+                                     ((768, 50, 21), 64), ((520, 33, 29), 20)])
+def test_fused_step_matches_rounded_emulation(lib, shape, l):
+    """One fused step against its exact emulation: Y = X (bf16(X^T bf16(Q)))
+    in FP64 on the bfloat16 tensor, so only the FP32 accumulation order
+    differs: singular values to 1e-4 relative, every direction with
+    sigma > 1e-3 sigma_1 to sines 1e-3."""
+    A = I.tucker_plus_noise(list(shape), [8] * 3, seed=sum(shape) + 1, noise=1e-2, decay=0.9,
+                            dtype=np.float32)
+    Ab = T.round_bf16(A)
+    Q0, _ = T.svd_econ(T.sketch(Ab, 0, l))
+    Xk = T.unfold(Ab, 0)
+    W = T.round_bf16(Xk.T @ T.round_bf16(Q0))
+    Qw, Sw = T.svd_econ(Xk @ W)
+    Abd = _bf16_device(A)
+    Qd = api.to_device(Q0, np.float64)
+    sig = torch.zeros(l, dtype=torch.float64, device="cuda")
+    alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+    api.tucker_shifted_power(Abd, list(shape), 0, l, 1, api.TK_SHIFT_NONE, Qd, sig, alpha)
+    Sg = sig.cpu().numpy()
+    Qg = Qd.cpu().numpy().reshape((shape[0], l), order="F")
+    assert np.max(np.abs(Sg - Sw) / Sw[0]) <= 1e-4, np.max(np.abs(Sg - Sw) / Sw[0])
+    j = int(np.sum(Sw > 1e-3 * Sw[0]))
+    assert T.principal_sines(Qg[:, :j], Qw[:, :j]).max() <= 1e-3
