@@ -77,12 +77,10 @@ DEFAULT_WORKLOAD = "tucker400_fp32_st"
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (summaries under profiles/); absent = not measured.
-#  * small_svd at 400^3: k_svd_one, n = 400, l = 30 (162,048 B read, 0 written);
 #  * power_fused at 1000^3: k_power_tc2 captured at 512^3 (268.58 MB read,
 #    3.80 MB written), reads scaled by the column count (1000^3 / 512^3) and
 #    the partial writes by the row count (1000 / 512).
 NCU_TRAFFIC = {
-    ("tucker400_fp32_st", "small_svd"): 162048.0,
     ("invradius512_bf16power_st", "power_fused"): 268.57984e6 + 3.802112e6,
     ("invradius1000_bf16power_st", "power_fused"): 268.57984e6 * (1000 ** 3 / 512 ** 3) +
                                                    3.802112e6 * (1000 / 512),

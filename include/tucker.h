@@ -276,7 +276,9 @@ typedef enum {
   TK_K_TTM = 5,         /* G <- G x_k U_k^T */
   TK_K_ERROR = 6,       /* reconstruction-error passes */
   TK_K_CONVERT = 7,     /* bf16 shadow, copies, reductions, polish */
-  TK_K_KINDS = 8
+  TK_K_RITZ = 8,        /* Rayleigh-Ritz rotation of W before the precision
+                           form's FP32 step (Gram, l x l eigenvectors, W Z) */
+  TK_K_KINDS = 9
 } tk_kernel_kind;
 
 typedef struct {

@@ -46,12 +46,13 @@ class tk_stats(ctypes.Structure):
 
 
 TK_K_NAMES = ["sketch", "power_w", "power_y", "power_fused", "small_svd", "ttm", "error",
-              "convert"]
+              "convert", "ritz"]
 
 
 class tk_profile(ctypes.Structure):
-    _fields_ = [("launches", c_int64 * 8), ("ms", c_double * 8), ("bytes", c_double * 8),
-                ("flops", c_double * 8), ("kernels", c_int64)]
+    _fields_ = [("launches", c_int64 * len(TK_K_NAMES)), ("ms", c_double * len(TK_K_NAMES)),
+                ("bytes", c_double * len(TK_K_NAMES)), ("flops", c_double * len(TK_K_NAMES)),
+                ("kernels", c_int64)]
 
 
 class tk_item(ctypes.Structure):

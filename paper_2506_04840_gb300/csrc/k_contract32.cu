@@ -133,11 +133,13 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 // jk = j / ka + kb (j % ka) maps the layout's column order to the unfolding's
 // (ka = columns, kb = 1 for the natural layout).
 // ---------------------------------------------------------------------------
-// COMP: compensated accumulation (Dot2: an exact product residual by FMA and
-// a TwoSum per term, with correctly rounded operations so nothing is
-// contracted), written as a (hi, lo) pair of partials: hi to part, lo to
-// part_lo.  Used where a product must resolve directions far below FP32
-// rounding of its running sums.
+// COMP: slab-compensated accumulation.  Each slab of KS columns is summed in
+// FP32 from zero and folded into a (hi, lo) pair by TwoSum (correctly rounded
+// adds, so nothing is contracted); the pair is written as two partial planes,
+// hi to part and lo to part_lo.  Sequential FP32 sums over ~10^6 columns
+// carry rounding errors of the size of their running sums, which for the
+// weak directions of Y = X W are many times the result; with the fold only
+// the slab sums' own rounding (a few products' worth) is left.
 template <int WI, int WC, bool OMEGA, bool COMP = false>
 __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
                                           const float* __restrict__ W, int l, int lc,
@@ -246,6 +248,13 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
   for (int s = 0; s < nsl; ++s) {
     const int buf = s & 1;
     if (s + 1 < nsl) load(jb + (int64_t)(s + 1) * KS);
+    float sl[8][4];
+    if (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sl[a][q] = 0.f;
+    }
 #pragma unroll
     for (int jj = 0; jj < KS; ++jj) {
       const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][jj][ia]);
@@ -257,17 +266,21 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
       for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (COMP) {
-            const float pr = __fmul_rn(av[a], bv[q]);
-            const float pe = __fmaf_rn(av[a], bv[q], -pr);
-            const float t = __fadd_rn(acc[a][q], pr);
-            const float z = __fsub_rn(t, acc[a][q]);
-            const float se = __fadd_rn(__fsub_rn(acc[a][q], __fsub_rn(t, z)), __fsub_rn(pr, z));
-            acc[a][q] = t;
-            cmp[a][q] = __fadd_rn(cmp[a][q], __fadd_rn(se, pe));
-          } else {
-            acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
-          }
+          if (COMP) sl[a][q] = fmaf(av[a], bv[q], sl[a][q]);
+          else acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+        }
+    }
+    if (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float t = __fadd_rn(acc[a][q], sl[a][q]);
+          const float z = __fsub_rn(t, acc[a][q]);
+          const float se = __fadd_rn(__fsub_rn(acc[a][q], __fsub_rn(t, z)),
+                                     __fsub_rn(sl[a][q], z));
+          acc[a][q] = t;
+          cmp[a][q] = __fadd_rn(cmp[a][q], se);
         }
     }
     if (s + 1 < nsl) store(buf ^ 1);

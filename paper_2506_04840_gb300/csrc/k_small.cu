@@ -922,6 +922,261 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz rotation of W = X^T Q before the precision form's FP32 step.
+//
+// After the bfloat16 steps the weak columns of Q carry components along the
+// leading left singular directions of X at the copy's rounding level, so the
+// columns of Y = X X^T Q are dominated by sigma_1^2 times those components and
+// FP32 sums of Y = X W bury the weak directions under their rounding.  With
+// Z the eigenvectors of G = W^T W = Q^T X X^T Q (the Ritz vectors of X X^T in
+// span(Q)), Q Z has those cross components removed, and Y Z = X (W Z) spans
+// the same subspace as Y with the same singular values, so the step computes
+// X (W Z) instead.  G is summed in FP32 over 64-row tiles flushed to FP64
+// every 16 tiles, partial G's of up to kRitzBlocks row ranges are summed in a
+// fixed order, and the l x l eigenproblem is solved by one-sided Jacobi in
+// FP32 on G scaled to a unit largest diagonal entry.
+// ---------------------------------------------------------------------------
+constexpr int kRitzRows = 64;      // rows of W per shared-memory tile
+constexpr int kRitzBlocks = 304;   // row ranges (blocks) of the Gram pass
+constexpr int kRitzFlush = 16;     // tiles summed in FP32 between FP64 flushes
+
+__device__ __forceinline__ int64_t ritz_off(int64_t j, int64_t P, int l) {
+  return P == 1 ? j * l : (j % P) + P * (int64_t)l * (j / P);
+}
+
+// Partial G over rows [b R, min(cols, (b+1) R)) of W (b = blockIdx.x), block
+// (ba, bb) of 64 x 64 entries (blockIdx.y = ba + nbk bb, nbk = ceil(l / 64));
+// thread (ty, tx) of a 16 x 16 grid owns G(64 ba + 4 ty + i, 64 bb + 4 tx + j),
+// i, j < 4.  The tile holds all l columns at row stride S = 64 nbk.
+__global__ void __launch_bounds__(256) k_ritz_gram(const float* __restrict__ W, int64_t cols,
+                                                   int64_t P, int l, int64_t R,
+                                                   double* __restrict__ part) {
+  extern __shared__ __align__(16) float sgw[];     // kRitzRows x S
+  __shared__ int64_t offw[kRitzRows];
+  const int nbk = (l + 63) / 64, S = 64 * nbk;
+  const int ba = (int)blockIdx.y % nbk, bb = (int)blockIdx.y / nbk;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int ca = 64 * ba + 4 * ty, cb = 64 * bb + 4 * tx;
+  for (int e = tid; e < kRitzRows * S; e += 256) sgw[e] = 0.f;
+  float acc[4][4];
+  double accd[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f, accd[i][j] = 0.0;
+  const int64_t jb = (int64_t)blockIdx.x * R;
+  const int64_t je = min(cols, jb + R);
+  int tiles = 0;
+  for (int64_t j0 = jb; j0 < je; j0 += kRitzRows) {
+    __syncthreads();
+    if (tid < kRitzRows) {
+      const int64_t j = j0 + tid;
+      offw[tid] = j < je ? ritz_off(j, P, l) : -1;
+    }
+    __syncthreads();
+    for (int e = tid; e < kRitzRows * l; e += 256) {
+      int r, c;
+      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+      const int64_t o = offw[r];
+      sgw[r * S + c] = o >= 0 ? __ldg(W + o + P * c) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < kRitzRows; ++r) {
+      const float4 av = *reinterpret_cast<const float4*>(sgw + r * S + ca);
+      const float4 bv = *reinterpret_cast<const float4*>(sgw + r * S + cb);
+      const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (++tiles == kRitzFlush) {
+      tiles = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accd[i][j] += (double)acc[i][j], acc[i][j] = 0.f;
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * l * l;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = ca + i, b = cb + j;
+      if (a < l && b < l) out[a + (int64_t)l * b] = accd[i][j] + (double)acc[i][j];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ritz_sum(const double* __restrict__ part, int nb,
+                                                  int ll, double* __restrict__ G) {
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e >= ll) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * ll + e];
+  G[e] = s;
+}
+
+// Z (l x l, column c = eigenvector of the c-th largest eigenvalue of G).
+// smem: J (l*l) | Vp (l*l) | sg (l), FP32.
+__global__ void __launch_bounds__(256) k_ritz_eig(const double* __restrict__ G, int l,
+                                                  float* __restrict__ Z, int* __restrict__ status) {
+  extern __shared__ __align__(16) float sre[];
+  float* J = sre;
+  float* Vp = J + l * l;
+  float* sg = Vp + l * l;
+  __shared__ int perm[TK_MAX_L];
+  __shared__ double dmax;
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    double m = 0.0;
+    for (int i = tid; i < l; i += 32) m = fmax(m, G[i + (int64_t)l * i]);
+    m = warp_max(m);
+    if (tid == 0) dmax = m;
+  }
+  __syncthreads();
+  const double dm = dmax;
+  const bool ok = dm > 0.0 && isfinite(dm);
+  if (!ok && tid == 0 && !(dm == 0.0)) atomicExch(status, (int)TK_EBREAKDOWN);
+  const double sc = ok ? 1.0 / dm : 1.0;
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    J[e] = (float)(G[e] * sc);
+    Vp[e] = (e % l == e / l) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_warp(J, Vp, l);
+  __syncthreads();
+  sigma_perm(J, l, sg, perm, Vp);
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    Z[e] = Vp[i + l * perm[c]];
+  }
+}
+
+// W <- W Z in place, 64-row tiles; warp w of 8 owns output columns
+// [CW w, CW w + CW), lane the rows lane and lane + 32.
+// smem: Zs (l x 8 CW, row k = Z(k, :), zero beyond l) | T (kRitzRows x (l | 1)).
+template <int CW>
+__global__ void __launch_bounds__(256) k_ritz_apply(float* __restrict__ W, int64_t cols,
+                                                    int64_t P, int l,
+                                                    const float* __restrict__ Z) {
+  constexpr int ZS = 8 * CW;
+  extern __shared__ __align__(16) float sra[];
+  float* Zs = sra;
+  float* T = Zs + l * ZS;
+  const int TS = l | 1;
+  __shared__ int64_t offw[kRitzRows];
+  const int tid = threadIdx.x, lane = tid & 31, cg = tid >> 5;
+  for (int e = tid; e < l * ZS; e += 256) {
+    const int k = e / ZS, c = e - k * ZS;
+    Zs[e] = c < l ? Z[k + (int64_t)l * c] : 0.f;
+  }
+  const int64_t ntile = (cols + kRitzRows - 1) / kRitzRows;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t j0 = tile * kRitzRows;
+    __syncthreads();
+    if (tid < kRitzRows) {
+      const int64_t j = j0 + tid;
+      offw[tid] = j < cols ? ritz_off(j, P, l) : -1;
+    }
+    __syncthreads();
+    for (int e = tid; e < kRitzRows * l; e += 256) {
+      int r, c;
+      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+      const int64_t o = offw[r];
+      T[r * TS + c] = o >= 0 ? W[o + P * c] : 0.f;
+    }
+    __syncthreads();
+    float a0[CW], a1[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) a0[c] = 0.f, a1[c] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < l; ++k) {
+      const float x0 = T[lane * TS + k], x1 = T[(lane + 32) * TS + k];
+      const float4* z4 = reinterpret_cast<const float4*>(Zs + k * ZS + cg * CW);
+#pragma unroll
+      for (int q = 0; q < CW / 4; ++q) {
+        const float4 z = z4[q];
+        a0[4 * q] = fmaf(x0, z.x, a0[4 * q]);
+        a0[4 * q + 1] = fmaf(x0, z.y, a0[4 * q + 1]);
+        a0[4 * q + 2] = fmaf(x0, z.z, a0[4 * q + 2]);
+        a0[4 * q + 3] = fmaf(x0, z.w, a0[4 * q + 3]);
+        a1[4 * q] = fmaf(x1, z.x, a1[4 * q]);
+        a1[4 * q + 1] = fmaf(x1, z.y, a1[4 * q + 1]);
+        a1[4 * q + 2] = fmaf(x1, z.z, a1[4 * q + 2]);
+        a1[4 * q + 3] = fmaf(x1, z.w, a1[4 * q + 3]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      const int col = cg * CW + c;
+      if (col < l) {
+        T[lane * TS + col] = a0[c];
+        T[(lane + 32) * TS + col] = a1[c];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < kRitzRows * l; e += 256) {
+      int r, c;
+      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+      const int64_t o = offw[r];
+      if (o >= 0) W[o + P * c] = T[r * TS + c];
+    }
+  }
+}
+
+static size_t ritz_part_bytes(int l) { return align256((size_t)kRitzBlocks * l * l * sizeof(double)); }
+static size_t ritz_g_bytes(int l) { return align256((size_t)l * l * sizeof(double)); }
+
+size_t ritz_scratch(int l) {
+  return ritz_part_bytes(l) + ritz_g_bytes(l) + align256((size_t)l * l * sizeof(float));
+}
+
+cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* scratch,
+                               int* status, cudaStream_t st) {
+  if (l < 1 || l > TK_MAX_L || cols < 1 || P < 1) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    const int eig_max = (2 * TK_MAX_L * TK_MAX_L + TK_MAX_L) * (int)sizeof(float);
+    const int app_max = (TK_MAX_L * 128 + kRitzRows * (TK_MAX_L | 1)) * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         eig_max);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ritz_apply<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               app_max);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  unsigned char* sb = (unsigned char*)scratch;
+  double* part = (double*)sb;
+  double* G = (double*)(sb + ritz_part_bytes(l));
+  float* Z = (float*)(sb + ritz_part_bytes(l) + ritz_g_bytes(l));
+  int64_t R = (cols + kRitzBlocks - 1) / kRitzBlocks;
+  R = (R + kRitzRows - 1) / kRitzRows * kRitzRows;
+  const int nb = (int)((cols + R - 1) / R);
+  const int nbk = (l + 63) / 64;
+  k_ritz_gram<<<dim3(nb, nbk * nbk), 256, kRitzRows * 64 * nbk * sizeof(float), st>>>(W, cols, P,
+                                                                                      l, R, part);
+  count_kernels(1);
+  k_ritz_sum<<<(l * l + 255) / 256, 256, 0, st>>>(part, nb, l * l, G);
+  count_kernels(1);
+  k_ritz_eig<<<1, 256, (2 * l * l + l) * sizeof(float), st>>>(G, l, Z, status);
+  count_kernels(1);
+  const int64_t ntile = (cols + kRitzRows - 1) / kRitzRows;
+  const int grid = (int)std::min<int64_t>(ntile, 152 * 8);
+  if (l <= 64)
+    k_ritz_apply<8><<<grid, 256, (l * 64 + kRitzRows * (l | 1)) * sizeof(float), st>>>(
+        W, cols, P, l, Z);
+  else
+    k_ritz_apply<16><<<grid, 256, (l * 128 + kRitzRows * (l | 1)) * sizeof(float), st>>>(
+        W, cols, P, l, Z);
+  count_kernels(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,
                              double* Q, double* sigma, void* scratch, int shift_rule,
                              bool update_shift, double* alpha, double* alpha_hist,

@@ -127,6 +127,15 @@ size_t polish_scratch(int64_t n, int r);
 cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* status,
                           cudaStream_t st);
 
+// Rayleigh-Ritz rotation of W = X^T Q in place (precision form, before its
+// FP32 step Y = X W): G = W^T W, Z = eigenvectors of G by descending
+// eigenvalue, W <- W Z.  W holds cols x l FP32 entries in the (P, l, S)
+// layout the products use (entry (j, c) at j % P + P (c + l (j / P))).
+// scratch: ritz_scratch(l) bytes.
+size_t ritz_scratch(int l);
+cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* scratch,
+                               int* status, cudaStream_t st);
+
 // ---- misc (k_misc.cu) -----------------------------------------------------
 cudaError_t launch_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed, uint32_t tag,
                          float* out, cudaStream_t st);

@@ -93,7 +93,6 @@ struct HosvdPlan {
   // sizes (bytes)
   size_t gbuf = 0, shadow = 0, wbuf = 0, part = 0, ymat = 0, small = 0, qd = 0;
   std::vector<SmallPlan> sp;
-  std::vector<SmallPlan> sp64;   // precision form: FP64 svd after the FP32 step
   std::vector<std::vector<int64_t>> dims_at;  // tensor dims seen by each step
 };
 

@@ -112,7 +112,6 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
   const size_t es = xsize(p.xt), ta = asize(p.xt);
   p.l.assign(p.d, 0);
   p.sp.assign(p.d, SmallPlan{});
-  p.sp64.assign(p.d, SmallPlan{});
   p.dims_at.assign(p.d, {});
   std::vector<int64_t> cur = p.n;
   for (int step = 0; step < p.d; ++step) {
@@ -128,16 +127,12 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     p.sp[k] = small_plan(v.n, (int)lk, p.xt == X_F64);
     if (p.sp[k].Pb <= 0) return TK_ENOTIMPL;
     p.small = std::max(p.small, p.sp[k].scratch_bytes);
-    if (p.bf16 && p.q >= 2) {
-      p.sp64[k] = small_plan(v.n, (int)lk, true);
-      if (p.sp64[k].Pb <= 0) return TK_ENOTIMPL;
-      p.small = std::max(p.small, p.sp64[k].scratch_bytes);
-    }
     if (p.xt != X_F64) p.small = std::max(p.small, polish_scratch(v.n, p.r[k]));
     const int lc = xb_lc((int)lk);
     const int splits = xb_splits(p.xt, v, (int)lk);
     // the precision form's FP32 step keeps (hi, lo) partial pairs
     p.part = std::max(p.part, (size_t)splits * v.n * lc * ta * (p.bf16 && p.q >= 2 ? 2 : 1));
+    if (p.bf16 && p.q >= 2) p.part = std::max(p.part, ritz_scratch((int)lk));
     if (xtb32_ok(p.xt, v, (const void*)1)) {   // row-split scratch of W = X^T Q and the TTM
       p.part = std::max(p.part, xtb32_scratch(v, (int)lk));
       p.part = std::max(p.part, xtb32_scratch(v, p.r[k]));
@@ -226,12 +221,14 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
   }
   for (int t = 1; t <= p.q; ++t) {
     const bool low = p.bf16 && t < p.q;
+    // precision form: the FP32 step after the bfloat16 ones
+    const bool last32 = p.bf16 && p.q >= 2 && t == p.q;
     const void* Xp = low ? w.shadow : X;
     const XType xp = low ? X_BF16 : xt;
     // precision form: the shift sequence restarts when the step switches
     // from the bfloat16 copy to the FP32 tensor (the bfloat16 Sigma(l,l)
     // sits on the copy's rounding floor, far above sigma_l(X X^T)/2)
-    if (p.bf16 && p.q >= 2 && t == p.q) TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
+    if (last32) TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
     if (low && power_tc_supported(v, l, Xp)) {
       // one fused tensor-core pass over the bfloat16 copy
       const int groups = power_tc_groups(v, l);
@@ -250,13 +247,22 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
         ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
         TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st, 0, w.part));
       }
-      // precision form, FP32 step after the bfloat16 ones: the subspace
-      // handed over by the copy carries large components along the leading
-      // directions in its weak columns, so FP32 rounding of the running sums
-      // of Y = X W would bury the weak directions; Y's sums are compensated
-      // (hi/lo partials) there.
+      // The precision form's FP32 step has to resolve the weak directions
+      // the bfloat16 steps left inexact, to the FP32 path's accuracy:
+      //  * Q's weak columns carry components along the leading directions at
+      //    the copy's rounding level; in Y = X W these dominate the weak
+      //    columns and FP32 rounding of them buries the weak directions, so W
+      //    is first rotated to the Ritz vectors (Y Z = X (W Z) spans the same
+      //    subspace, alpha = 0 at this step);
+      //  * the sums of Y = X W over the unfolding's columns are compensated
+      //    (slab sums folded into (hi, lo) pairs).
+      if (last32) {
+        const double cw = (double)v.cols() * l;
+        ProfScope ps(TK_K_RITZ, 3.0 * cw * 4.0, 4.0 * cw * l, st);
+        TK_TRY(launch_ritz_rotate((float*)w.w, v.cols(), v.P, l, w.part, w.status, st));
+      }
       void* plo = nullptr;
-      if (p.bf16 && p.q >= 2 && t == p.q && xtb32_ok(xp, v, Xp))
+      if (last32 && xtb32_ok(xp, v, Xp))
         plo = (unsigned char*)w.part + (size_t)splits * v.n * lc * asize(xp);
       {
         ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
@@ -268,13 +274,9 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
       }
     }
     {
-      // the precision form's FP32 step: Y's weak directions sit far below
-      // FP32 rounding of its (large) entries, so its svd runs in FP64
-      const bool wide = p.bf16 && p.q >= 2 && t == p.q;
       ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
-      TK_TRY(launch_small_svd(fp64 || wide, wide ? p.sp64[k] : p.sp[k], w.Y, v.n, w.Q, sig,
-                              w.small, (int)p.rule, true, w.alpha,
-                              w.ahist + (size_t)k * TK_MAX_Q + (t - 1),
+      TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, true,
+                              w.alpha, w.ahist + (size_t)k * TK_MAX_Q + (t - 1),
                               w.shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, st));
     }
   }
