@@ -765,6 +765,498 @@ cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* statu
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident FP32 path: 512 threads (16 warps); warp w keeps columns
+// c = w + 16 s (s < 4) of an m x l matrix (m <= 512, l <= 64) in registers,
+// lane holding rows 4 (lane + 32 k) + e (k < 4, e < 4).  A Householder step
+// streams only the reflector through shared memory and takes one barrier;
+// applying the reflectors backward (Q = H_0 ... H_{l-1} B) needs none.  The
+// l x l problem uses one-sided Jacobi with one warp per pair and column norms
+// kept incrementally (a' = a - t g, b' = b + t g; refreshed every sweep).
+// Same arithmetic as the shared-memory routines, in a different order.
+// ---------------------------------------------------------------------------
+constexpr int kRegThreads = 512;
+constexpr int kRegRK = 4;                    // float4 chunks per lane per column
+constexpr int kRegCPW = 4;                   // columns per warp
+constexpr int kRegRows = 4 * 32 * kRegRK;    // 512
+constexpr int kRegCols = 16 * kRegCPW;       // 64
+
+__host__ __device__ __forceinline__ int reg_ld(int64_t m) { return (int)((m + 3) / 4 * 4); }
+
+struct RegCols {
+  float y[kRegCPW][4 * kRegRK];
+  int lane, warp;
+  __device__ __forceinline__ RegCols() : lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {}
+  __device__ __forceinline__ int col(int s) const { return warp + 16 * s; }
+  __device__ __forceinline__ int row(int k, int e) const { return 4 * (lane + 32 * k) + e; }
+  __device__ __forceinline__ bool has(int k, int md) const { return 4 * (lane + 32 * k) < md; }
+
+  __device__ __forceinline__ void load_col(int s, const float* c, int md) {
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (has(k, md)) v = *reinterpret_cast<const float4*>(c + 4 * (lane + 32 * k));
+      y[s][4 * k] = v.x; y[s][4 * k + 1] = v.y; y[s][4 * k + 2] = v.z; y[s][4 * k + 3] = v.w;
+    }
+  }
+  __device__ __forceinline__ void store_col(int s, float* c, int md) const {
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k)
+      if (has(k, md))
+        *reinterpret_cast<float4*>(c + 4 * (lane + 32 * k)) =
+            make_float4(y[s][4 * k], y[s][4 * k + 1], y[s][4 * k + 2], y[s][4 * k + 3]);
+  }
+  // reflector j's entry at (k, e): 1 at row j, 0 above, stored value below
+  // (rows >= 128 lie below every j < l <= 64)
+  __device__ __forceinline__ float vsel(int k, int e, int j, float v) const {
+    if (k > 0) return v;
+    const int r = row(k, e);
+    return r > j ? v : (r == j ? 1.f : 0.f);
+  }
+  // y(:, c) <- (I - tj v v^T) y(:, c) for the owned columns lo < c < hi;
+  // v = reflector j in shared memory
+  __device__ __forceinline__ void apply(int j, const float* v, int md, float tj, int lo, int hi) {
+    bool act[kRegCPW];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s) {
+      act[s] = col(s) > lo && col(s) < hi;
+      any = any || act[s];
+    }
+    if (!any || tj == 0.f) return;
+    float d[kRegCPW];
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s) d[s] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k) {
+      if (!has(k, md)) continue;
+      const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
+      const float ve[4] = {vsel(k, 0, j, v4.x), vsel(k, 1, j, v4.y), vsel(k, 2, j, v4.z),
+                           vsel(k, 3, j, v4.w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int s = 0; s < kRegCPW; ++s)
+          if (act[s]) d[s] = fmaf(ve[e], y[s][4 * k + e], d[s]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int s = 0; s < kRegCPW; ++s) d[s] += __shfl_xor_sync(0xffffffffu, d[s], o);
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s) d[s] *= -tj;
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k) {
+      if (!has(k, md)) continue;
+      const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
+      const float ve[4] = {vsel(k, 0, j, v4.x), vsel(k, 1, j, v4.y), vsel(k, 2, j, v4.z),
+                           vsel(k, 3, j, v4.w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int s = 0; s < kRegCPW; ++s)
+          if (act[s]) y[s][4 * k + e] = fmaf(d[s], ve[e], y[s][4 * k + e]);
+    }
+  }
+  // reflector of column c (held in y[s]) as make_reflector builds it; stores
+  // the column (R part and reflector) and tau[c]
+  __device__ __forceinline__ void build(int s, int c, float* cp, int md, float* tau) {
+    float s0 = 0.f, s1 = 0.f, mine = 0.f;
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = row(k, e);
+        const float t = r > c ? y[s][4 * k + e] : 0.f;
+        if (e & 1) s1 = fmaf(t, t, s1); else s0 = fmaf(t, t, s0);
+        if (r == c) mine = y[s][4 * k + e];
+      }
+    const float ssq = warp_sum(s0 + s1);
+    const float alpha = __shfl_sync(0xffffffffu, mine, (c >> 2) & 31);
+    const float xnorm = sqrtf(ssq);
+    float beta = alpha, tj = 0.f, scal = 1.f;
+    if (xnorm > 0.f) {
+      const float mx = fmaxf(fabsf(alpha), xnorm);
+      const float a1 = alpha / mx, x1 = xnorm / mx;
+      beta = -copysignf(mx * sqrtf(a1 * a1 + x1 * x1), alpha);
+      tj = (beta - alpha) / beta;
+      scal = 1.f / (alpha - beta);
+    }
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = row(k, e);
+        if (r > c) y[s][4 * k + e] *= scal;
+        else if (r == c) y[s][4 * k + e] = beta;
+      }
+    store_col(s, cp, md);
+    if (lane == 0) tau[c] = tj;
+  }
+  // Householder QR of A (md x l in shared memory, ld md, rows past m zero)
+  // with the columns in registers; A ends as householder_qr leaves it.
+  __device__ void qr(float* A, int md, int l, float* tau) {
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s)
+      if (col(s) < l) load_col(s, A + (int64_t)md * col(s), md);
+    if (warp == 0) build(0, 0, A, md, tau);
+    __syncthreads();
+    for (int j = 0; j < l; ++j) {
+      const float tj = tau[j];
+      const float* v = A + (int64_t)md * j;
+      // the owner of column j+1 updates and factors it first (look-ahead)
+#pragma unroll
+      for (int s = 0; s < kRegCPW; ++s)
+        if (col(s) == j + 1 && j + 1 < l) {
+          apply(j, v, md, tj, j, j + 2);
+          build(s, j + 1, A + (int64_t)md * (j + 1), md, tau);
+        }
+      apply(j, v, md, tj, j + 1, l);
+      __syncthreads();
+    }
+  }
+  // y(:, c) <- H_0 H_1 ... H_{l-1} y(:, c) for the owned columns c < nb
+  // (reflectors and tau of qr() in shared memory, read only)
+  __device__ void apply_back(const float* A, int md, int l, const float* tau, int nb) {
+    for (int j = l - 1; j >= 0; --j) apply(j, A + (int64_t)md * j, md, tau[j], -1, nb);
+  }
+  // y(:, c) = B(r, c) for r < l (B(r, c) = src[r + ld c'] with c' = perm[c]
+  // when perm is given), 0 below
+  __device__ __forceinline__ void init_top(const float* src, int ld, const int* perm, int l,
+                                           int nb) {
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s) {
+      const int c = col(s);
+      const int cs = c < nb ? (perm ? perm[c] : c) : 0;
+#pragma unroll
+      for (int k = 0; k < kRegRK; ++k)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = row(k, e);
+          y[s][4 * k + e] = (c < nb && r < l) ? src[r + (int64_t)ld * cs] : 0.f;
+        }
+    }
+  }
+  // column c's entry of largest magnitude (lowest row on ties, rows < m):
+  // its value, broadcast to the warp
+  __device__ __forceinline__ float col_extreme(int s, int m, int* brow) const {
+    float best = -1.f, bval = 0.f;
+    int bi = 0;
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = row(k, e);
+        const float av = fabsf(y[s][4 * k + e]);
+        if (r < m && av > best) { best = av; bi = r; bval = y[s][4 * k + e]; }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const float ov = __shfl_xor_sync(0xffffffffu, bval, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bval = ov; }
+    }
+    if (brow) *brow = bi;
+    return bval;
+  }
+  // out[r + ldo c] = sgn y(r, c) for r < m (c < nb)
+  template <typename O>
+  __device__ __forceinline__ void store_out(int s, O* out, int64_t ldo, int m, float sgn) const {
+#pragma unroll
+    for (int k = 0; k < kRegRK; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = row(k, e);
+        if (r < m) out[r + ldo * col(s)] = (O)(sgn * y[s][4 * k + e]);
+      }
+  }
+};
+
+// One-sided Jacobi on the l columns of J (l x l, l <= 128), accumulating the
+// rotations in Vp; one warp per column pair of a round-robin round, column
+// norms in nrm (l) kept incrementally; all threads of the block take part.
+__device__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m2 = l + (l & 1), npairs = m2 / 2;
+  __shared__ int jflag[2];
+  if (threadIdx.x == 0) jflag[0] = jflag[1] = 0;
+  const float tol = jacobi_tol<float>(l);
+  const float tol2 = tol * tol;
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    for (int c = warp; c < l; c += nw) {
+      const float* x = J + l * c;
+      float a = 0.f;
+      for (int i = lane; i < l; i += 32) a = fmaf(x[i], x[i], a);
+      a = warp_sum(a);
+      if (lane == 0) nrm[c] = a;
+    }
+    __syncthreads();
+    const int fb = sweep & 1;
+    int rotated = 0;
+    for (int rd = 0; rd < m2 - 1; ++rd) {
+      for (int pr = warp; pr < npairs; pr += nw) {
+        int p, q;
+        if (pr == 0) {
+          p = rd;
+          q = m2 - 1;
+        } else {
+          p = rd + pr;
+          if (p >= m2 - 1) p -= m2 - 1;
+          q = rd - pr;
+          if (q < 0) q += m2 - 1;
+        }
+        if (p >= l || q >= l) continue;
+        float* xp = J + l * p;
+        float* xq = J + l * q;
+        float u[4], w[4], g = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = lane + 32 * k;
+          u[k] = i < l ? xp[i] : 0.f;
+          w[k] = i < l ? xq[i] : 0.f;
+          g = fmaf(u[k], w[k], g);
+        }
+        g = warp_sum(g);
+        const float a = nrm[p], b = nrm[q];
+        if (g != 0.f && g * g > tol2 * a * b) {
+          const float zeta = (b - a) / (g + g);
+          float t;
+          if (fabsf(zeta) > 1e15f) t = 0.5f / zeta;
+          else t = copysignf(1.f / (fabsf(zeta) + sqrtf(1.f + zeta * zeta)), zeta);
+          const float cs = rsqrtf(1.f + t * t);
+          const float sn = cs * t;
+          float* vp = Vp + l * p;
+          float* vq = Vp + l * q;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = lane + 32 * k;
+            if (i < l) {
+              xp[i] = cs * u[k] - sn * w[k];
+              xq[i] = sn * u[k] + cs * w[k];
+              const float a1 = vp[i], b1 = vq[i];
+              vp[i] = cs * a1 - sn * b1;
+              vq[i] = sn * a1 + cs * b1;
+            }
+          }
+          if (lane == 0) {
+            nrm[p] = a - t * g;
+            nrm[q] = b + t * g;
+          }
+          rotated = 1;
+        }
+      }
+      // the other sweep's flag is free once every thread has passed this
+      // sweep's first round
+      if (rd == 0 && threadIdx.x == 0) jflag[fb ^ 1] = 0;
+      __syncthreads();
+    }
+    if (rotated) jflag[fb] = 1;
+    __syncthreads();
+    if (!jflag[fb]) break;
+  }
+}
+
+// smem: A (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l), FP32
+__host__ __device__ __forceinline__ size_t reg_one_smem(int64_t n, int l) {
+  return ((size_t)reg_ld(n) * l + 2 * (size_t)l * l + 3 * (size_t)l) * sizeof(float);
+}
+
+// [Q, Sigma] = svd(Y) for n <= 512, l <= 64 (FP32 working precision), or
+// with basis_only an orthonormal basis of span(Y); as svd_one_body.
+__device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n, int l,
+                                             double* __restrict__ Q, double* __restrict__ sigma,
+                                             int shift_rule, int update_shift, int basis_only,
+                                             double* __restrict__ alpha,
+                                             double* __restrict__ alpha_hist,
+                                             double* __restrict__ sigl_hist,
+                                             int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int md = reg_ld(n);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* J = A + (int64_t)md * l;
+  float* Vp = J + l * l;
+  float* sg = Vp + l * l;
+  float* ts = sg + l;
+  float* nrm = ts + l;
+  __shared__ int perm[TK_MAX_L];
+  __shared__ double wmax[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // scale Y to max |entry| = 1 (sums of squares cannot under/overflow)
+  float mx = 0.f;
+  for (int64_t e = tid; e < (int64_t)md * l; e += blockDim.x) {
+    const int i = (int)(e % md), c = (int)(e / md);
+    const float v = i < n ? (float)Y[i + (int64_t)n * c] : 0.f;
+    A[e] = v;
+    mx = fmaxf(mx, fabsf(v));
+  }
+  mx = warp_max(mx);
+  if (lane == 0) wmax[warp] = (double)mx;
+  __syncthreads();
+  double gmax = 0.0;
+  for (int w = 0; w < nw; ++w) gmax = fmax(gmax, wmax[w]);
+  const double scale = (gmax > 0.0 && isfinite(gmax)) ? 1.0 / gmax : 1.0;
+  const float sc = (float)scale;
+  for (int64_t e = tid; e < (int64_t)md * l; e += blockDim.x) A[e] *= sc;
+  __syncthreads();
+  RegCols R;
+  R.qr(A, md, l, ts);
+  if (basis_only) {
+    // only span(Y) is needed: Q = Q_h
+    for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
+    __syncthreads();
+    R.init_top(Vp, l, nullptr, l, l);
+    R.apply_back(A, md, l, ts, l);
+#pragma unroll
+    for (int s = 0; s < kRegCPW; ++s)
+      if (R.col(s) < l) R.store_out(s, Q, n, n, 1.f);
+    return;
+  }
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    J[e] = (c <= i) ? A[c + (int64_t)md * i] : 0.f;   // J = R^T
+    Vp[e] = (i == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_pairs(J, Vp, l, nrm);
+  sigma_perm(J, l, sg, perm, Vp);
+  // Q = H_0 ... H_{l-1} [U_R; 0], U_R = Vp in perm order; sign convention
+  // (entry of largest magnitude positive, lowest row on ties)
+  R.init_top(Vp, l, perm, l, l);
+  R.apply_back(A, md, l, ts, l);
+#pragma unroll
+  for (int s = 0; s < kRegCPW; ++s)
+    if (R.col(s) < l) {
+      const float bv = R.col_extreme(s, n, nullptr);
+      R.store_out(s, Q, n, n, bv < 0.f ? -1.f : 1.f);
+    }
+  if (tid < l) {
+    const double sv = (double)sg[perm[tid]] / scale;
+    sigma[tid] = sv;
+    if (!isfinite(sv)) atomicExch(status, (int)TK_EBREAKDOWN);
+  }
+  if (tid == 0 && update_shift)
+    shift_update((double)sg[perm[l - 1]] / scale, shift_rule, alpha, alpha_hist, sigl_hist);
+}
+
+__global__ void __launch_bounds__(kRegThreads)
+k_svd_reg(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
+          double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
+          double* __restrict__ alpha, double* __restrict__ alpha_hist,
+          double* __restrict__ sigl_hist, int* __restrict__ status) {
+  svd_reg_body(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha, alpha_hist,
+               sigl_hist, status);
+}
+
+// TSQR leaf (MB <= 512 rows, a multiple of 32): reflectors to V (ld MB), tau,
+// R into the stack Rst (Pb l x l, ld Pb l)
+__global__ void __launch_bounds__(kRegThreads)
+k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
+              float* __restrict__ V, float* __restrict__ tau, float* __restrict__ Rst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* ts = A + (int64_t)MB * l;
+  const int b = blockIdx.x;
+  const int64_t r0 = (int64_t)b * MB;
+  const int64_t rows = min((int64_t)MB, n - r0);
+  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) {
+    const int64_t i = e % MB, c = e / MB;
+    A[e] = i < rows ? (float)Y[(r0 + i) + n * c] : 0.f;
+  }
+  __syncthreads();
+  RegCols R;
+  R.qr(A, MB, l, ts);
+  float* Vb = V + (int64_t)b * MB * l;
+  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) Vb[e] = A[e];
+  const int64_t ldr = (int64_t)Pb * l;
+  for (int64_t e = threadIdx.x; e < (int64_t)l * l; e += blockDim.x) {
+    const int i = (int)(e % l), c = (int)(e / l);
+    Rst[((int64_t)b * l + i) + ldr * c] = (i <= c && i < MB) ? A[i + (int64_t)MB * c] : 0.f;
+  }
+  for (int j = threadIdx.x; j < l; j += blockDim.x) tau[(int64_t)b * l + j] = ts[j];
+}
+
+// TSQR root (m = Pb l <= 512): QR of the stacked R's, svd of the root R, and
+// Mout = Q_root U_R (m x l, ld m); sigma and the shift update.
+// smem: S (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l)
+__global__ void __launch_bounds__(kRegThreads)
+k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mout,
+           double* __restrict__ sigma, int shift_rule, int update_shift,
+           double* __restrict__ alpha, double* __restrict__ alpha_hist,
+           double* __restrict__ sigl_hist, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = Pb * l, md = reg_ld(m);
+  float* S = reinterpret_cast<float*>(smem_raw);
+  float* J = S + (int64_t)md * l;
+  float* Vp = J + l * l;
+  float* sg = Vp + l * l;
+  float* ts = sg + l;
+  float* nrm = ts + l;
+  __shared__ int perm[TK_MAX_L];
+  const int tid = threadIdx.x;
+  for (int64_t e = tid; e < (int64_t)md * l; e += blockDim.x) {
+    const int i = (int)(e % md), c = (int)(e / md);
+    S[e] = i < m ? Rst[i + (int64_t)m * c] : 0.f;
+  }
+  __syncthreads();
+  RegCols R;
+  R.qr(S, md, l, ts);
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    J[e] = (c <= i) ? S[c + (int64_t)md * i] : 0.f;
+    Vp[e] = (i == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_pairs(J, Vp, l, nrm);
+  sigma_perm(J, l, sg, perm, Vp);
+  R.init_top(Vp, l, perm, l, l);
+  R.apply_back(S, md, l, ts, l);
+#pragma unroll
+  for (int s = 0; s < kRegCPW; ++s)
+    if (R.col(s) < l) R.store_out(s, Mout, m, m, 1.f);
+  if (tid < l) {
+    const double sv = (double)sg[perm[tid]];
+    sigma[tid] = sv;
+    if (!isfinite(sv)) atomicExch(status, (int)TK_EBREAKDOWN);
+  }
+  if (tid == 0 && update_shift)
+    shift_update((double)sg[perm[l - 1]], shift_rule, alpha, alpha_hist, sigl_hist);
+}
+
+// TSQR leaf Q: rows r0.. of Q = Q_leaf [M_b; 0] (M_b = rows b l.. of Mout),
+// written in FP64, with each column's entry of largest magnitude (and its
+// global row) for the sign pass.  smem: B (MB*l reflectors) | tau (l)
+__global__ void __launch_bounds__(kRegThreads)
+k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
+             const float* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
+             double* __restrict__ Q, double* __restrict__ colmax, int* __restrict__ colidx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* B = reinterpret_cast<float*>(smem_raw);
+  float* ts = B + (int64_t)MB * l;
+  const int b = blockIdx.x;
+  const int m = Pb * l;
+  const int64_t r0 = (int64_t)b * MB;
+  const int rows = (int)min((int64_t)MB, n - r0);
+  const float* Vb = V + (int64_t)b * MB * l;
+  for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) B[e] = Vb[e];
+  for (int j = threadIdx.x; j < l; j += blockDim.x) ts[j] = tau[(int64_t)b * l + j];
+  __syncthreads();
+  RegCols R;
+  R.init_top(Mout + (int64_t)b * l, m, nullptr, l, l);
+  R.apply_back(B, MB, l, ts, l);
+#pragma unroll
+  for (int s = 0; s < kRegCPW; ++s)
+    if (R.col(s) < l) {
+      int bi = 0;
+      const float bv = R.col_extreme(s, rows, &bi);
+      R.store_out(s, Q + r0, n, rows, 1.f);
+      if (R.lane == 0) {
+        colmax[(int64_t)b * l + R.col(s)] = fabs((double)bv);
+        colidx[(int64_t)b * l + R.col(s)] = (int)(r0 + bi);
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
 static const size_t kSmemBudget = kSvdSmemBudget;
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -780,26 +1272,60 @@ static size_t leafq_smem(int MB, int l, size_t es) {
   return ((size_t)MB * l + (size_t)l * l + (size_t)l) * es;
 }
 
-// Pb == 1 selects the single-CTA path (MB = n).
+// Pb == 1 selects the single-CTA path (MB = n).  FP32 problems with n <= 512
+// and l <= 64 take the register-resident single-CTA kernel; above the
+// single-CTA shared-memory budget, FP32 TSQR takes the register-resident
+// kernels when the leaves (<= 512 rows) and the root (Pb l <= 512 rows) fit.
+// (The work-list svd follows the same single-CTA choice, so batched and
+// single calls run the same kernels.)
+bool svd_reg_fits(int64_t n, int l, bool fp64) {
+  return !fp64 && l >= 1 && l <= kRegCols && n >= l && n <= kRegRows &&
+         reg_one_smem(n, l) <= kSmemBudget;
+}
+
 SmallPlan small_plan(int64_t n, int l, bool fp64) {
-  SmallPlan p{l, 0, 0, 0};
+  SmallPlan p{l, 0, 0, 0, 0};
   const size_t es = fp64 ? 8 : 4;
   if (l <= 0 || l > TK_MAX_L || n < l) return p;
+  if (svd_reg_fits(n, l, fp64)) {
+    p.MB = (int)n;
+    p.Pb = 1;
+    p.reg = 1;
+    p.scratch_bytes = 256;
+    return p;
+  }
   if (one_smem(n, l, es) <= kSmemBudget) {
     p.MB = (int)n;
     p.Pb = 1;
     p.scratch_bytes = 256;
     return p;
   }
-  for (int Pb = 2; Pb <= 64; ++Pb) {
-    int MB = (int)((n + Pb - 1) / Pb);
-    MB = std::max(MB, l);
-    MB = (MB + 31) / 32 * 32;
-    const int Pbe = (int)((n + MB - 1) / MB);
-    if (leafq_smem(MB, l, es) <= kSmemBudget && root_smem(Pbe, l, es) <= kSmemBudget) {
-      p.MB = MB;
-      p.Pb = Pbe;
+  if (!fp64 && l <= kRegCols) {
+    for (int Pb = 2; Pb * l <= kRegRows; ++Pb) {
+      int MB = (int)((n + Pb - 1) / Pb);
+      MB = std::max(MB, l);
+      MB = (MB + 31) / 32 * 32;
+      if (MB > kRegRows) continue;
+      const int Pbe = (int)((n + MB - 1) / MB);
+      if (Pbe * l <= kRegRows && reg_one_smem((int64_t)Pbe * l, l) <= kSmemBudget) {
+        p.MB = MB;
+        p.Pb = Pbe;
+        p.reg = 1;
+      }
       break;
+    }
+  }
+  if (p.Pb <= 0) {
+    for (int Pb = 2; Pb <= 64; ++Pb) {
+      int MB = (int)((n + Pb - 1) / Pb);
+      MB = std::max(MB, l);
+      MB = (MB + 31) / 32 * 32;
+      const int Pbe = (int)((n + MB - 1) / MB);
+      if (leafq_smem(MB, l, es) <= kSmemBudget && root_smem(Pbe, l, es) <= kSmemBudget) {
+        p.MB = MB;
+        p.Pb = Pbe;
+        break;
+      }
     }
   }
   if (p.Pb <= 0) return p;
@@ -823,7 +1349,37 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
     cudaFuncSetAttribute(k_leaf_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_leaf_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_svd_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_qr_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_root_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_q_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     attr_set = true;
+  }
+  if (pl.reg && sizeof(T) == 4) {
+    if (Pb == 1) {
+      count_kernels(1);
+      k_svd_reg<<<1, kRegThreads, reg_one_smem(n, l), st>>>(
+          Y, (int)n, l, Q, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
+          alpha_hist, sigl_hist, status);
+      return cudaGetLastError();
+    }
+    unsigned char* w = (unsigned char*)scratch;
+    float* V = (float*)w;        w += align256((size_t)Pb * MB * l * 4);
+    float* tau = (float*)w;      w += align256((size_t)Pb * l * 4);
+    float* Rst = (float*)w;      w += align256((size_t)Pb * l * l * 4);
+    float* Mout = (float*)w;     w += align256((size_t)Pb * l * l * 4);
+    double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
+    int* colidx = (int*)w;
+    const size_t leaf_smem = ((size_t)MB * l + l) * sizeof(float);
+    count_kernels(4);
+    k_leaf_qr_reg<<<Pb, kRegThreads, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
+    k_root_reg<<<1, kRegThreads, reg_one_smem((int64_t)Pb * l, l), st>>>(
+        Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, alpha, alpha_hist, sigl_hist,
+        status);
+    k_leaf_q_reg<<<Pb, kRegThreads, leaf_smem, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
+                                                      colidx);
+    k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
+    return cudaGetLastError();
   }
   if (Pb == 1) {
     const int threads = (int64_t)n * l >= 4096 ? 1024 : 256;
@@ -866,6 +1422,17 @@ __global__ void k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __r
   }
 }
 
+__global__ void __launch_bounds__(kRegThreads)
+k_svd_batch_reg(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+                uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const SvdJob J = jobs[batch_job(start, njobs, b)];
+    svd_reg_body(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
+                 J.alpha, J.ahist, J.shist, J.status);
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k_gram_batch(const GramJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
              uint32_t total) {
@@ -888,8 +1455,13 @@ k_polish_batch(const PolishJob* __restrict__ jobs, const uint32_t* __restrict__ 
   }
 }
 
-int svd_threads(int64_t n, int l) { return (int64_t)n * l >= 4096 ? 1024 : 256; }
-size_t svd_smem(int64_t n, int l, bool fp64) { return one_smem(n, l, fp64 ? 8 : 4); }
+int svd_threads(int64_t n, int l, bool fp64) {
+  if (svd_reg_fits(n, l, fp64)) return kRegThreads;
+  return (int64_t)n * l >= 4096 ? 1024 : 256;
+}
+size_t svd_smem(int64_t n, int l, bool fp64) {
+  return svd_reg_fits(n, l, fp64) ? reg_one_smem(n, l) : one_smem(n, l, fp64 ? 8 : 4);
+}
 int polish_blocks(int64_t n) { return (int)((n + kPolishRows - 1) / kPolishRows); }
 size_t gram_smem(int r) { return (size_t)kPolishRows * r * sizeof(double); }
 size_t polish_smem(int r) { return ((size_t)r * r + (size_t)kPolishRows * r) * sizeof(double); }
@@ -902,6 +1474,7 @@ void batch_kernels_init() {
   const int mx = (int)kSmemBudget + 4096;
   cudaFuncSetAttribute(k_svd_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_svd_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_svd_batch_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_gram_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_polish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   attr = true;
@@ -912,6 +1485,9 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
   switch (b.kind) {
     case BK_SVD:
       if (b.xt == X_F64) return run_batch(k_svd_batch<double>, b, b.tile, st);
+      // jobs of one launch share a thread count: the register-resident ones
+      // run 512 threads, no other svd does
+      if (b.tile == kRegThreads) return run_batch(k_svd_batch_reg, b, kRegThreads, st);
       return run_batch(k_svd_batch<float>, b, b.tile, st);
     case BK_GRAM:
       return run_batch(k_gram_batch, b, 256, st);

@@ -113,6 +113,7 @@ cudaError_t launch_power_tc(const void* X, View v, const double* Q, int l, void*
 struct SmallPlan {
   int l, MB, Pb;
   size_t scratch_bytes;
+  int reg;   // register-resident FP32 kernels
 };
 SmallPlan small_plan(int64_t n, int l, bool fp64);
 cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, int64_t n,

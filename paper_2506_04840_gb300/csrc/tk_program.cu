@@ -194,7 +194,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     const XType acc = fp64 ? X_F64 : X_F32;
     double* sig = stt->sig + (size_t)k * TK_MAX_L;
     double* alpha = stt->alpha + k;
-    const int sthreads = svd_threads(v.n, l);
+    const int sthreads = svd_threads(v.n, l, fp64);
     const size_t ssmem = svd_smem(v.n, l, fp64);
 
     // ---- sketch phase
