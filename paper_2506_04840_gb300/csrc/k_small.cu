@@ -35,6 +35,15 @@ template <typename T> __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// Division and square root for the small solvers' scalar steps: in FP32 the
+// fast intrinsics (a few ulp; the correctly rounded forms have ~5x their
+// latency, which sits on every Householder step's and Jacobi rotation's
+// critical path), in FP64 the correctly rounded operations.
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float ssqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double ssqrt(double x) { return sqrt(x); }
+
 // Householder reflector for column j of A (ld m) given ssq = sum of squares of
 // its entries below the diagonal; run by one warp.  LAPACK-style generation
 // (beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta)).
@@ -43,14 +52,15 @@ __device__ __forceinline__ void make_reflector(T* A, int m, int j, T ssq, T* tau
   const int lane = threadIdx.x & 31;
   T* x = A + (int64_t)m * j;
   const T alpha = x[j];
-  const T xnorm = sqrt(ssq);
+  const T xnorm = ssqrt(ssq);
   T beta = alpha, tj = (T)0;
   if (xnorm > (T)0) {
     const T mx = max((T)fabs(alpha), xnorm);
-    const T a1 = alpha / mx, x1 = xnorm / mx;
-    beta = -copysign(mx * sqrt(a1 * a1 + x1 * x1), alpha);
-    tj = (beta - alpha) / beta;
-    const T scal = (T)1 / (alpha - beta);
+    const T rmx = sdiv((T)1, mx);
+    const T a1 = alpha * rmx, x1 = xnorm * rmx;
+    beta = -copysign(mx * ssqrt(a1 * a1 + x1 * x1), alpha);
+    tj = sdiv(beta - alpha, beta);
+    const T scal = sdiv((T)1, alpha - beta);
     for (int i = j + 1 + lane; i < m; i += 32) x[i] *= scal;
   }
   __syncwarp();
@@ -116,22 +126,23 @@ __device__ void householder_qr(T* A, int m, int l, T* tau) {
       amax = warp_max(amax);
       T ssq = (T)0;
       if (amax > (T)0) {
-        const T inv = (T)1 / amax;
+        const T inv = sdiv((T)1, amax);
         for (int i = j + 1 + lane; i < m; i += 32) {
           const T t = x[i] * inv;
           ssq += t * t;
         }
       }
       ssq = warp_sum(ssq);
-      const T xnorm = amax * sqrt(ssq);
+      const T xnorm = amax * ssqrt(ssq);
       const T alpha = x[j];
       T beta = alpha, tj = (T)0;
       if (xnorm > (T)0) {
         const T mx = max((T)fabs(alpha), xnorm);
-        const T a1 = alpha / mx, x1 = xnorm / mx;
-        beta = -copysign(mx * sqrt(a1 * a1 + x1 * x1), alpha);
-        tj = (beta - alpha) / beta;
-        const T scal = (T)1 / (alpha - beta);
+        const T rmx = sdiv((T)1, mx);
+        const T a1 = alpha * rmx, x1 = xnorm * rmx;
+        beta = -copysign(mx * ssqrt(a1 * a1 + x1 * x1), alpha);
+        tj = sdiv(beta - alpha, beta);
+        const T scal = sdiv((T)1, alpha - beta);
         for (int i = j + 1 + lane; i < m; i += 32) x[i] *= scal;
       }
       __syncwarp();
@@ -249,10 +260,10 @@ __device__ void jacobi_warp(T* J, T* Vp, int l) {
           gm += __shfl_xor_sync(0xffffffffu, gm, o);
         }
         if (act && gm != (T)0 && gm * gm > tol2 * a * bb) {
-          const T zeta = (bb - a) / (gm + gm);
+          const T zeta = sdiv(bb - a, gm + gm);
           T t;
-          if (fabs(zeta) > (T)1e15) t = (T)0.5 / zeta;
-          else t = copysign((T)1 / (fabs(zeta) + sqrt((T)1 + zeta * zeta)), zeta);
+          if (fabs(zeta) > (T)1e15) t = sdiv((T)0.5, zeta);
+          else t = copysign(sdiv((T)1, fabs(zeta) + ssqrt((T)1 + zeta * zeta)), zeta);
           const T cs = rsqrt((T)1 + t * t);
           const T sn = cs * t;
           for (int i = sub; i < l; i += g) {
@@ -805,16 +816,9 @@ struct RegCols {
         *reinterpret_cast<float4*>(c + 4 * (lane + 32 * k)) =
             make_float4(y[s][4 * k], y[s][4 * k + 1], y[s][4 * k + 2], y[s][4 * k + 3]);
   }
-  // reflector j's entry at (k, e): 1 at row j, 0 above, stored value below
-  // (rows >= 128 lie below every j < l <= 64)
-  __device__ __forceinline__ float vsel(int k, int e, int j, float v) const {
-    if (k > 0) return v;
-    const int r = row(k, e);
-    return r > j ? v : (r == j ? 1.f : 0.f);
-  }
   // y(:, c) <- (I - tj v v^T) y(:, c) for the owned columns lo < c < hi;
-  // v = reflector j in shared memory
-  __device__ __forceinline__ void apply(int j, const float* v, int md, float tj, int lo, int hi) {
+  // v = reflector j in shared memory, stored in full (0 above row j, 1 at j)
+  __device__ __forceinline__ void apply(const float* v, int md, float tj, int lo, int hi) {
     bool act[kRegCPW];
     bool any = false;
 #pragma unroll
@@ -830,8 +834,7 @@ struct RegCols {
     for (int k = 0; k < kRegRK; ++k) {
       if (!has(k, md)) continue;
       const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
-      const float ve[4] = {vsel(k, 0, j, v4.x), vsel(k, 1, j, v4.y), vsel(k, 2, j, v4.z),
-                           vsel(k, 3, j, v4.w)};
+      const float ve[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
@@ -848,8 +851,7 @@ struct RegCols {
     for (int k = 0; k < kRegRK; ++k) {
       if (!has(k, md)) continue;
       const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
-      const float ve[4] = {vsel(k, 0, j, v4.x), vsel(k, 1, j, v4.y), vsel(k, 2, j, v4.z),
-                           vsel(k, 3, j, v4.w)};
+      const float ve[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
@@ -857,9 +859,11 @@ struct RegCols {
           if (act[s]) y[s][4 * k + e] = fmaf(d[s], ve[e], y[s][4 * k + e]);
     }
   }
-  // reflector of column c (held in y[s]) as make_reflector builds it; stores
-  // the column (R part and reflector) and tau[c]
-  __device__ __forceinline__ void build(int s, int c, float* cp, int md, float* tau) {
+  // reflector of column c (held in y[s]) as make_reflector builds it: R(r, c)
+  // (r <= c) goes to rs[r * rr + c * rc] (when rs is given), the column is
+  // stored as the full reflector (0 above row c, 1 at c, v below), tau[c]
+  __device__ __forceinline__ void build(int s, int c, float* cp, int md, float* tau, float* rs,
+                                        int rr, int rc) {
     float s0 = 0.f, s1 = 0.f, mine = 0.f;
 #pragma unroll
     for (int k = 0; k < kRegRK; ++k)
@@ -872,33 +876,41 @@ struct RegCols {
       }
     const float ssq = warp_sum(s0 + s1);
     const float alpha = __shfl_sync(0xffffffffu, mine, (c >> 2) & 31);
-    const float xnorm = sqrtf(ssq);
+    // the fast reciprocal square root and division intrinsics (a few ulp;
+    // the correctly rounded forms cost ~5x their latency on the step's
+    // critical path) -- the reflector stays orthogonal to FP32 rounding
+    const float xnorm = ssq > 0.f ? ssq * rsqrtf(ssq) : 0.f;
     float beta = alpha, tj = 0.f, scal = 1.f;
     if (xnorm > 0.f) {
       const float mx = fmaxf(fabsf(alpha), xnorm);
-      const float a1 = alpha / mx, x1 = xnorm / mx;
-      beta = -copysignf(mx * sqrtf(a1 * a1 + x1 * x1), alpha);
-      tj = (beta - alpha) / beta;
-      scal = 1.f / (alpha - beta);
+      const float rmx = __fdividef(1.f, mx);
+      const float a1 = alpha * rmx, x1 = xnorm * rmx;
+      const float h = a1 * a1 + x1 * x1;   // in [1, 2]
+      beta = -copysignf(mx * (h * rsqrtf(h)), alpha);
+      tj = __fdividef(beta - alpha, beta);
+      scal = __fdividef(1.f, alpha - beta);
     }
 #pragma unroll
     for (int k = 0; k < kRegRK; ++k)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = row(k, e);
-        if (r > c) y[s][4 * k + e] *= scal;
-        else if (r == c) y[s][4 * k + e] = beta;
+        float& x = y[s][4 * k + e];
+        if (rs != nullptr && r <= c) rs[r * rr + c * rc] = r == c ? beta : x;
+        x = r > c ? x * scal : (r == c ? 1.f : 0.f);
       }
     store_col(s, cp, md);
     if (lane == 0) tau[c] = tj;
   }
   // Householder QR of A (md x l in shared memory, ld md, rows past m zero)
-  // with the columns in registers; A ends as householder_qr leaves it.
-  __device__ void qr(float* A, int md, int l, float* tau) {
+  // with the columns in registers.  A ends holding the full reflectors
+  // (column j: 0 above row j, 1 at j, v_j below), tau the factors, and R
+  // (upper triangle) goes to rs[r * rr + c * rc] when rs is given.
+  __device__ void qr(float* A, int md, int l, float* tau, float* rs, int rr, int rc) {
 #pragma unroll
     for (int s = 0; s < kRegCPW; ++s)
       if (col(s) < l) load_col(s, A + (int64_t)md * col(s), md);
-    if (warp == 0) build(0, 0, A, md, tau);
+    if (warp == 0) build(0, 0, A, md, tau, rs, rr, rc);
     __syncthreads();
     for (int j = 0; j < l; ++j) {
       const float tj = tau[j];
@@ -907,17 +919,17 @@ struct RegCols {
 #pragma unroll
       for (int s = 0; s < kRegCPW; ++s)
         if (col(s) == j + 1 && j + 1 < l) {
-          apply(j, v, md, tj, j, j + 2);
-          build(s, j + 1, A + (int64_t)md * (j + 1), md, tau);
+          apply(v, md, tj, j, j + 2);
+          build(s, j + 1, A + (int64_t)md * (j + 1), md, tau, rs, rr, rc);
         }
-      apply(j, v, md, tj, j + 1, l);
+      apply(v, md, tj, j + 1, l);
       __syncthreads();
     }
   }
   // y(:, c) <- H_0 H_1 ... H_{l-1} y(:, c) for the owned columns c < nb
-  // (reflectors and tau of qr() in shared memory, read only)
+  // (full reflectors and tau of qr() in shared memory, read only)
   __device__ void apply_back(const float* A, int md, int l, const float* tau, int nb) {
-    for (int j = l - 1; j >= 0; --j) apply(j, A + (int64_t)md * j, md, tau[j], -1, nb);
+    for (int j = l - 1; j >= 0; --j) apply(A + (int64_t)md * j, md, tau[j], -1, nb);
   }
   // y(:, c) = B(r, c) for r < l (B(r, c) = src[r + ld c'] with c' = perm[c]
   // when perm is given), 0 below
@@ -973,10 +985,15 @@ struct RegCols {
 };
 
 // One-sided Jacobi on the l columns of J (l x l, l <= 128), accumulating the
-// rotations in Vp; one warp per column pair of a round-robin round, column
-// norms in nrm (l) kept incrementally; all threads of the block take part.
-__device__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
+// rotations in Vp; G lanes per column pair of a round-robin round (G = 16:
+// two pairs per warp, l <= 64; G = 32: l <= 128), each lane holding 4
+// entries of the pair's columns; column norms in nrm (l) kept incrementally;
+// all threads of the block take part.
+template <int G>
+__device__ void jacobi_pairs_g(float* J, float* Vp, int l, float* nrm) {
+  constexpr int PPW = 32 / G;   // pairs per warp and pass
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int hw = lane / G, sub = lane % G;
   const int m2 = l + (l & 1), npairs = m2 / 2;
   __shared__ int jflag[2];
   if (threadIdx.x == 0) jflag[0] = jflag[1] = 0;
@@ -994,42 +1011,54 @@ __device__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
     const int fb = sweep & 1;
     int rotated = 0;
     for (int rd = 0; rd < m2 - 1; ++rd) {
-      for (int pr = warp; pr < npairs; pr += nw) {
-        int p, q;
-        if (pr == 0) {
-          p = rd;
-          q = m2 - 1;
-        } else {
-          p = rd + pr;
-          if (p >= m2 - 1) p -= m2 - 1;
-          q = rd - pr;
-          if (q < 0) q += m2 - 1;
+      // uniform per warp: both halves iterate together (the shuffles need
+      // every lane)
+      for (int pr0 = PPW * warp; pr0 < npairs; pr0 += PPW * nw) {
+        const int pr = pr0 + hw;
+        int p = 0, q = 0;
+        if (pr < npairs) {
+          if (pr == 0) {
+            p = rd;
+            q = m2 - 1;
+          } else {
+            p = rd + pr;
+            if (p >= m2 - 1) p -= m2 - 1;
+            q = rd - pr;
+            if (q < 0) q += m2 - 1;
+          }
         }
-        if (p >= l || q >= l) continue;
+        const bool act = pr < npairs && p < l && q < l;
         float* xp = J + l * p;
         float* xq = J + l * q;
         float u[4], w[4], g = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int i = lane + 32 * k;
-          u[k] = i < l ? xp[i] : 0.f;
-          w[k] = i < l ? xq[i] : 0.f;
+          const int i = sub + G * k;
+          u[k] = (act && i < l) ? xp[i] : 0.f;
+          w[k] = (act && i < l) ? xq[i] : 0.f;
           g = fmaf(u[k], w[k], g);
         }
-        g = warp_sum(g);
-        const float a = nrm[p], b = nrm[q];
-        if (g != 0.f && g * g > tol2 * a * b) {
-          const float zeta = (b - a) / (g + g);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        const float a = act ? nrm[p] : 0.f, b = act ? nrm[q] : 0.f;
+        if (act && g != 0.f && g * g > tol2 * a * b) {
+          // rotation parameters with the fast intrinsics: any angle close to
+          // the Jacobi angle is an exact plane rotation (cs, sn from t)
+          const float zeta = __fdividef(b - a, g + g);
           float t;
-          if (fabsf(zeta) > 1e15f) t = 0.5f / zeta;
-          else t = copysignf(1.f / (fabsf(zeta) + sqrtf(1.f + zeta * zeta)), zeta);
+          if (fabsf(zeta) > 1e15f) {
+            t = __fdividef(0.5f, zeta);
+          } else {
+            const float h = 1.f + zeta * zeta;
+            t = copysignf(__fdividef(1.f, fabsf(zeta) + h * rsqrtf(h)), zeta);
+          }
           const float cs = rsqrtf(1.f + t * t);
           const float sn = cs * t;
           float* vp = Vp + l * p;
           float* vq = Vp + l * q;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int i = lane + 32 * k;
+            const int i = sub + G * k;
             if (i < l) {
               xp[i] = cs * u[k] - sn * w[k];
               xq[i] = sn * u[k] + cs * w[k];
@@ -1038,7 +1067,7 @@ __device__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
               vq[i] = sn * a1 + cs * b1;
             }
           }
-          if (lane == 0) {
+          if (sub == 0) {
             nrm[p] = a - t * g;
             nrm[q] = b + t * g;
           }
@@ -1054,6 +1083,11 @@ __device__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
     __syncthreads();
     if (!jflag[fb]) break;
   }
+}
+
+__device__ __forceinline__ void jacobi_pairs(float* J, float* Vp, int l, float* nrm) {
+  if (l <= 64) jacobi_pairs_g<16>(J, Vp, l, nrm);
+  else jacobi_pairs_g<32>(J, Vp, l, nrm);
 }
 
 // smem: A (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l), FP32
@@ -1098,8 +1132,11 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
   const float sc = (float)scale;
   for (int64_t e = tid; e < (int64_t)md * l; e += blockDim.x) A[e] *= sc;
   __syncthreads();
+  if (!basis_only)
+    for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
+  __syncthreads();
   RegCols R;
-  R.qr(A, md, l, ts);
+  R.qr(A, md, l, ts, basis_only ? nullptr : J, l, 1);   // J = R^T
   if (basis_only) {
     // only span(Y) is needed: Q = Q_h
     for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
@@ -1111,11 +1148,7 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
       if (R.col(s) < l) R.store_out(s, Q, n, n, 1.f);
     return;
   }
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e % l, c = e / l;
-    J[e] = (c <= i) ? A[c + (int64_t)md * i] : 0.f;   // J = R^T
-    Vp[e] = (i == c) ? 1.f : 0.f;
-  }
+  for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
   __syncthreads();
   jacobi_pairs(J, Vp, l, nrm);
   sigma_perm(J, l, sg, perm, Vp);
@@ -1163,15 +1196,17 @@ k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
     A[e] = i < rows ? (float)Y[(r0 + i) + n * c] : 0.f;
   }
   __syncthreads();
+  const int ldr = Pb * l;
+  float* Rb = Rst + (int64_t)b * l;
+  // the strictly lower part of this leaf's R block; qr() writes the rest
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    if (i > c) Rb[i + (int64_t)ldr * c] = 0.f;
+  }
   RegCols R;
-  R.qr(A, MB, l, ts);
+  R.qr(A, MB, l, ts, Rb, 1, ldr);
   float* Vb = V + (int64_t)b * MB * l;
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) Vb[e] = A[e];
-  const int64_t ldr = (int64_t)Pb * l;
-  for (int64_t e = threadIdx.x; e < (int64_t)l * l; e += blockDim.x) {
-    const int i = (int)(e % l), c = (int)(e / l);
-    Rst[((int64_t)b * l + i) + ldr * c] = (i <= c && i < MB) ? A[i + (int64_t)MB * c] : 0.f;
-  }
   for (int j = threadIdx.x; j < l; j += blockDim.x) tau[(int64_t)b * l + j] = ts[j];
 }
 
@@ -1197,14 +1232,11 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
     const int i = (int)(e % md), c = (int)(e / md);
     S[e] = i < m ? Rst[i + (int64_t)m * c] : 0.f;
   }
+  for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
   __syncthreads();
   RegCols R;
-  R.qr(S, md, l, ts);
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e % l, c = e / l;
-    J[e] = (c <= i) ? S[c + (int64_t)md * i] : 0.f;
-    Vp[e] = (i == c) ? 1.f : 0.f;
-  }
+  R.qr(S, md, l, ts, J, l, 1);   // J = R^T
+  for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
   __syncthreads();
   jacobi_pairs(J, Vp, l, nrm);
   sigma_perm(J, l, sg, perm, Vp);
@@ -1596,13 +1628,14 @@ __global__ void __launch_bounds__(256) k_ritz_sum(const double* __restrict__ par
 }
 
 // Z (l x l, column c = eigenvector of the c-th largest eigenvalue of G).
-// smem: J (l*l) | Vp (l*l) | sg (l), FP32.
+// smem: J (l*l) | Vp (l*l) | sg (l) | nrm (l), FP32.
 __global__ void __launch_bounds__(256) k_ritz_eig(const double* __restrict__ G, int l,
                                                   float* __restrict__ Z, int* __restrict__ status) {
   extern __shared__ __align__(16) float sre[];
   float* J = sre;
   float* Vp = J + l * l;
   float* sg = Vp + l * l;
+  float* nrm = sg + l;
   __shared__ int perm[TK_MAX_L];
   __shared__ double dmax;
   const int tid = threadIdx.x;
@@ -1622,7 +1655,7 @@ __global__ void __launch_bounds__(256) k_ritz_eig(const double* __restrict__ G, 
     Vp[e] = (e % l == e / l) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_warp(J, Vp, l);
+  jacobi_pairs(J, Vp, l, nrm);
   __syncthreads();
   sigma_perm(J, l, sg, perm, Vp);
   for (int e = tid; e < l * l; e += blockDim.x) {
@@ -1716,7 +1749,7 @@ cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* s
   if (l < 1 || l > TK_MAX_L || cols < 1 || P < 1) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    const int eig_max = (2 * TK_MAX_L * TK_MAX_L + TK_MAX_L) * (int)sizeof(float);
+    const int eig_max = (2 * TK_MAX_L * TK_MAX_L + 2 * TK_MAX_L) * (int)sizeof(float);
     const int app_max = (TK_MAX_L * 128 + kRitzRows * (TK_MAX_L | 1)) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          eig_max);
@@ -1739,7 +1772,7 @@ cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* s
   count_kernels(1);
   k_ritz_sum<<<(l * l + 255) / 256, 256, 0, st>>>(part, nb, l * l, G);
   count_kernels(1);
-  k_ritz_eig<<<1, 256, (2 * l * l + l) * sizeof(float), st>>>(G, l, Z, status);
+  k_ritz_eig<<<1, 256, (2 * l * l + 2 * l) * sizeof(float), st>>>(G, l, Z, status);
   count_kernels(1);
   const int64_t ntile = (cols + kRitzRows - 1) / kRitzRows;
   const int grid = (int)std::min<int64_t>(ntile, 152 * 8);
