@@ -578,9 +578,10 @@ static cudaError_t xtb_lc_go(const void* X, View v, const double* B, int64_t b_r
 
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
                        int64_t b_cm, int m, void* out, cudaStream_t st, int tout,
-                       void* scratch) {
+                       void* scratch, const float* B32) {
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
-  if (xtb32_ok(xt, v, X)) return launch_xtb32(X, v, B, b_ri, b_cm, m, out, st, tout, scratch);
+  if (xtb32_ok(xt, v, X))
+    return launch_xtb32(X, v, B, b_ri, b_cm, m, out, st, tout, scratch, B32);
   if (tout) return cudaErrorInvalidValue;
   switch (xt) {
     case X_F64: return xtb_lc_go<double, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);
@@ -598,10 +599,10 @@ int xtb_error_blocks(XType xt, View v, int m) {
 
 cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
                              int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
-                             cudaStream_t st) {
+                             cudaStream_t st, const float* B32) {
   *blocks = xtb_error_blocks(xt, v, m);
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
-  if (err32_ok(xt, v)) return launch_err32(T, v, B, b_ri, b_cm, m, A, err_part, st);
+  if (err32_ok(xt, v)) return launch_err32(T, v, B, b_ri, b_cm, m, A, err_part, st, B32);
   if (xt == X_F64) return xtb_lc_go<double, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
   return xtb_lc_go<float, 1>(T, v, B, b_ri, b_cm, m, nullptr, A, err_part, st);
 }

@@ -31,15 +31,17 @@ constexpr int KS = 16;   // contraction rows staged per slab
 // out is written in the (1, m, cols) layout out[c + m j], or with tout in
 // the (cols, m) layout out[j + cols c] (the mode just contracted moves last).
 // ---------------------------------------------------------------------------
-template <int WJ, int WC>
+template <int WJ, int WC, typename BT>
 __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
-                                           const double* __restrict__ B, int64_t b_ri,
+                                           const BT* __restrict__ B, int64_t b_ri,
                                            int64_t b_cm, int m, float* __restrict__ out,
                                            int tout, int64_t ib, int64_t ie, unsigned bx,
                                            unsigned by) {
   constexpr int MJ = 64 * WJ, MC = 16 * WC, T = 32 * WJ * WC;
   constexpr int XPT = KS * MJ / T;          // X elements each thread stages per slab
   constexpr int BPT = (KS * MC + T - 1) / T;
+  // slabs in flight in registers: two where the staging registers allow
+  constexpr int PF = XPT <= 8 ? 2 : 1;
   __shared__ __align__(16) float Xs[2][KS][MJ + 4];
   __shared__ __align__(16) float Bs[2][KS][MC];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -56,14 +58,16 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
 
-  float xr[XPT], br[BPT];
-  auto load = [&](int64_t i0) {
+  // slab t (rows ib + t KS ..) travels in register set t % PF, then shared
+  // buffer t & 1
+  float xr[PF][XPT], br[PF][BPT];
+  auto load = [&](int p, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < XPT; ++r) {
       const int e = tid + r * T;
       const int ii = e % KS, jj = e / KS;
       const int64_t i = i0 + ii, j = j0 + jj;
-      xr[r] = (i < ie && j < cols) ? __ldg(X + j * n + i) : 0.f;
+      xr[p][r] = (i < ie && j < cols) ? __ldg(X + j * n + i) : 0.f;
     }
 #pragma unroll
     for (int r = 0; r < BPT; ++r) {
@@ -74,31 +78,35 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
         const int64_t i = i0 + ii;
         if (i < ie && c0 + c < m) v = (float)B[i * b_ri + (int64_t)(c0 + c) * b_cm];
       }
-      br[r] = v;
+      br[p][r] = v;
     }
   };
-  auto store = [&](int buf) {
+  auto store = [&](int p, int buf) {
 #pragma unroll
     for (int r = 0; r < XPT; ++r) {
       const int e = tid + r * T;
-      Xs[buf][e % KS][e / KS] = xr[r];
+      Xs[buf][e % KS][e / KS] = xr[p][r];
     }
 #pragma unroll
     for (int r = 0; r < BPT; ++r) {
       const int e = tid + r * T;
-      if (e < KS * MC) Bs[buf][e / MC][e % MC] = br[r];
+      if (e < KS * MC) Bs[buf][e / MC][e % MC] = br[p][r];
     }
   };
 
   const int nsl = ie > ib ? (int)((ie - ib + KS - 1) / KS) : 0;
   if (nsl > 0) {
-    load(ib);
-    store(0);
+    load(0, ib);
+    store(0, 0);
+  }
+  if (PF == 2) {
+    if (1 < nsl) load(1, ib + KS);
+    if (2 < nsl) load(0, ib + 2 * KS);
   }
   __syncthreads();
   for (int s = 0; s < nsl; ++s) {
     const int buf = s & 1;
-    if (s + 1 < nsl) load(ib + (int64_t)(s + 1) * KS);
+    if (PF == 1 && s + 1 < nsl) load(0, ib + (int64_t)(s + 1) * KS);
 #pragma unroll
     for (int ii = 0; ii < KS; ++ii) {
       const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][ii][ja]);
@@ -111,7 +119,19 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
     }
-    if (s + 1 < nsl) store(buf ^ 1);
+    if (PF == 1) {
+      if (s + 1 < nsl) store(0, (s + 1) & 1);
+    } else if (s + 1 < nsl) {
+      // slab s+1 to shared memory; its register set takes slab s+3
+      const int64_t nxt = ib + (int64_t)(s + 3) * KS;
+      if (((s + 1) & 1) == 0) {
+        store(0, (s + 1) & 1);
+        if (s + 3 < nsl) load(0, nxt);
+      } else {
+        store(PF - 1, (s + 1) & 1);
+        if (s + 3 < nsl) load(PF - 1, nxt);
+      }
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -307,16 +327,16 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
   }
 }
 
-template <int WJ, int WC>
+template <int WJ, int WC, typename BT>
 __global__ void __launch_bounds__(32 * WJ * WC)
-k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const double* __restrict__ B,
+k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const BT* __restrict__ B,
         int64_t b_ri, int64_t b_cm, int m, float* __restrict__ out, int tout, int64_t kps,
         float* __restrict__ part) {
   // split z of the rows writes its partial sums to part (layout c + m j)
   const int64_t ib = (int64_t)blockIdx.z * kps, ie = min(n, ib + kps);
   float* o = part ? part + (int64_t)blockIdx.z * cols * m : out;
-  xtb32_body<WJ, WC>(X, n, cols, B, b_ri, b_cm, m, o, part ? 0 : tout, ib, ie, blockIdx.x,
-                     blockIdx.y);
+  xtb32_body<WJ, WC, BT>(X, n, cols, B, b_ri, b_cm, m, o, part ? 0 : tout, ib, ie, blockIdx.x,
+                         blockIdx.y);
 }
 
 // out = sum over the ks row splits of the partials, in a fixed order.
@@ -368,7 +388,7 @@ k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy, z = lb / gxy, r = lb % gxy;
     const int64_t ib = (int64_t)z * J.kps, ie = min(J.n, ib + J.kps);
     float* o = J.part ? (float*)J.part + (int64_t)z * J.cols * J.m : (float*)J.out;
-    xtb32_body<WJ, WC>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
+    xtb32_body<WJ, WC, double>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
                        J.part ? 0 : J.tout, ib, ie, r % (uint32_t)J.gx, r / (uint32_t)J.gx);
     __syncthreads();
   }
@@ -398,8 +418,9 @@ k_xb32_batch(const Xb32Job* __restrict__ jobs, const uint32_t* __restrict__ star
 // 128 x 64 tile (p, c) and writes the two sums to err[2 blk], blk = by gx + bx.
 // a_hat is never stored.  Thread tile 8 p x 4 c (lanes 8 x 4, warps 2 x 4).
 // ---------------------------------------------------------------------------
+template <typename BT>
 __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t P, int K,
-                                           const double* __restrict__ Bm, int64_t b_ri,
+                                           const BT* __restrict__ Bm, int64_t b_ri,
                                            int64_t b_cm, int m, const float* __restrict__ A,
                                            double* __restrict__ err, unsigned bx, unsigned by,
                                            unsigned gx) {
@@ -514,11 +535,12 @@ __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t
   __syncthreads();
 }
 
+template <typename BT>
 __global__ void __launch_bounds__(256)
-k_err32(const float* __restrict__ Tt, int64_t P, int K, const double* __restrict__ Bm,
+k_err32(const float* __restrict__ Tt, int64_t P, int K, const BT* __restrict__ Bm,
         int64_t b_ri, int64_t b_cm, int m, const float* __restrict__ A,
         double* __restrict__ err) {
-  err32_body(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.x, blockIdx.y, gridDim.x);
+  err32_body<BT>(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256)
@@ -528,7 +550,8 @@ k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const int j = batch_job(start, njobs, b);
     const Err32Job J = jobs[j];
     const uint32_t lb = b - __ldg(start + j);
-    err32_body((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A, J.err,
+    err32_body<double>((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A,
+                       J.err,
                lb % (uint32_t)J.gx, lb / (uint32_t)J.gx, (uint32_t)J.gx);
   }
 }
@@ -571,9 +594,14 @@ Xtb32Shape xtb32_shape(View v, int m, bool allow_split) {
   return s;
 }
 
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// scratch: the row-split partials (when the rows are split), then B in FP32
+// (n x m): converting B once here instead of per element in every CTA
 size_t xtb32_scratch(View v, int m) {
   const Xtb32Shape s = xtb32_shape(v, m, true);
-  return s.ks > 1 ? (size_t)s.ks * v.cols() * m * sizeof(float) : 0;
+  const size_t part = s.ks > 1 ? al256((size_t)s.ks * v.cols() * m * sizeof(float)) : 0;
+  return part + al256((size_t)v.n * m * sizeof(float));
 }
 
 Xb32Shape xb32_shape(View v, int l, int splits_req) {
@@ -601,25 +629,60 @@ Xb32Shape xb32_shape(View v, int l, int splits_req) {
   return s;
 }
 
-template <int WJ, int WC>
-static void xtb32_go(const float* X, View v, const double* B, int64_t b_ri, int64_t b_cm, int m,
+template <int WJ, int WC, typename BT>
+static void xtb32_go(const float* X, View v, const BT* B, int64_t b_ri, int64_t b_cm, int m,
                      float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
-  c32::k_xtb32<WJ, WC><<<dim3(s.gx, s.gy, s.ks), 32 * WJ * WC, 0, st>>>(
+  c32::k_xtb32<WJ, WC, BT><<<dim3(s.gx, s.gy, s.ks), 32 * WJ * WC, 0, st>>>(
       X, v.n, v.cols(), B, b_ri, b_cm, m, out, tout, s.kps, s.ks > 1 ? part : nullptr);
 }
 
+template <typename BT>
+static void xtb32_wc(const float* X, View v, const BT* B, int64_t b_ri, int64_t b_cm, int m,
+                     float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
+  switch (s.wc) {
+    case 1: xtb32_go<4, 1>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+    case 2: xtb32_go<4, 2>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+    default: xtb32_go<2, 4>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+  }
+}
+
+namespace c32 {
+// out[i + n c] = (float) B[i b_ri + c b_cm]
+__global__ void __launch_bounds__(256) k_b_to_f32(const double* __restrict__ B, int64_t b_ri,
+                                                  int64_t b_cm, int64_t n, int m,
+                                                  float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (e >= n * m) return;
+  const int64_t i = e % n, c = e / n;
+  out[e] = (float)B[i * b_ri + c * b_cm];
+}
+}  // namespace c32
+
+// With scratch (sized by xtb32_scratch), B is first rounded to FP32 once;
+// without, every CTA rounds the entries it stages.  The products are the
+// same either way (each FMA sees (float)B).
 cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
-                         int m, void* out, cudaStream_t st, int tout, void* scratch) {
+                         int m, void* out, cudaStream_t st, int tout, void* scratch,
+                         const float* B32) {
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
   const Xtb32Shape s = xtb32_shape(v, m, scratch != nullptr);
-  float* part = (float*)scratch;
-  count_kernels(s.ks > 1 ? 2 : 1);
   const float* x = (const float*)X;
   float* o = (float*)out;
-  switch (s.wc) {
-    case 1: xtb32_go<4, 1>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
-    case 2: xtb32_go<4, 2>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
-    default: xtb32_go<2, 4>(x, v, B, b_ri, b_cm, m, o, tout, part, s, st); break;
+  float* part = (float*)scratch;
+  if (B32 != nullptr) {
+    count_kernels(s.ks > 1 ? 2 : 1);
+    xtb32_wc(x, v, B32, b_ri, b_cm, m, o, tout, part, s, st);
+  } else if (scratch == nullptr) {
+    count_kernels(1);
+    xtb32_wc(x, v, B, b_ri, b_cm, m, o, tout, (float*)nullptr, s, st);
+    return cudaGetLastError();
+  } else {
+    float* b32 = (float*)((unsigned char*)scratch +
+                          (s.ks > 1 ? al256((size_t)s.ks * v.cols() * m * sizeof(float)) : 0));
+    count_kernels(s.ks > 1 ? 3 : 2);
+    const int64_t nb = v.n * m;
+    c32::k_b_to_f32<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B, b_ri, b_cm, v.n, m, b32);
+    xtb32_wc(x, v, (const float*)b32, 1, v.n, m, o, tout, part, s, st);
   }
   if (s.ks > 1) {
     const int64_t tot = v.cols() * m;
@@ -687,12 +750,17 @@ int err32_blocks(View v, int m) {
 }
 
 cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
-                         int m, const void* A, double* err_part, cudaStream_t st) {
+                         int m, const void* A, double* err_part, cudaStream_t st,
+                         const float* B32) {
   if (v.P <= 0 || m <= 0) return cudaSuccess;
   const dim3 grid((unsigned)((v.P + 127) / 128), (unsigned)((m + 63) / 64));
   count_kernels(1);
-  c32::k_err32<<<grid, 256, 0, st>>>((const float*)T, v.P, (int)v.n, B, b_ri, b_cm, m,
-                                     (const float*)A, err_part);
+  if (B32 != nullptr)
+    c32::k_err32<float><<<grid, 256, 0, st>>>((const float*)T, v.P, (int)v.n, B32, b_ri, b_cm, m,
+                                              (const float*)A, err_part);
+  else
+    c32::k_err32<double><<<grid, 256, 0, st>>>((const float*)T, v.P, (int)v.n, B, b_ri, b_cm, m,
+                                               (const float*)A, err_part);
   return cudaGetLastError();
 }
 

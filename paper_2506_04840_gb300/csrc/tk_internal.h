@@ -48,17 +48,20 @@ bool xtb32_ok(XType xt, View v, const void* X);
 // out[c + m*j].  ka, kb: Omega's row for layout column j is j/ka + kb*(j%ka)
 // (ka = 0: the natural layout, row j).
 // scratch (may be NULL): xtb32_scratch bytes; lets few-column products split
-// their rows over more CTAs.
+// their rows over more CTAs and holds B rounded to FP32 once.
+// B32 (may be NULL): B already in FP32 with the same strides (then B is
+// not read).
 cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, void* out, cudaStream_t st, int tout = 0,
-                         void* scratch = nullptr);
+                         void* scratch = nullptr, const float* B32 = nullptr);
 size_t xtb32_scratch(View v, int m);
 // FP32 last-mode expansion fused with the error sums (S == 1): err_part gets
 // err32_blocks(v, m) (e^2, a^2) pairs.
 bool err32_ok(XType xt, View v);
 int err32_blocks(View v, int m);
 cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
-                         int m, const void* A, double* err_part, cudaStream_t st);
+                         int m, const void* A, double* err_part, cudaStream_t st,
+                         const float* B32 = nullptr);
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka = 0,
                         int64_t kb = 1, void* part_lo = nullptr);
@@ -79,15 +82,17 @@ cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int
 // X (or `out_bf16` when non-null: BF16 output is not supported here).
 // tout = 1 (FP32 mode-major views only): out[j + cols*c] instead of the
 // (P, m, S) layout.
+// B32 (may be NULL): B in FP32 with the same strides, used by the FP32
+// mode-major kernels.
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
                        int64_t b_cm, int m, void* out, cudaStream_t st, int tout = 0,
-                       void* scratch = nullptr);
+                       void* scratch = nullptr, const float* B32 = nullptr);
 // Fused last-mode expansion and error sums: for S == 1, a_hat(p, c) =
 // sum_i T(p, i) B(i, c); accumulates (A - a_hat)^2 and A^2 per block into
 // err_part[2*block].  Returns the number of blocks via *blocks.
 cudaError_t launch_xtb_error(XType xt, const void* T, View v, const double* B, int64_t b_ri,
                              int64_t b_cm, int m, const void* A, double* err_part, int* blocks,
-                             cudaStream_t st);
+                             cudaStream_t st, const float* B32 = nullptr);
 int xtb_error_blocks(XType xt, View v, int m);
 cudaError_t launch_error_final(const double* err_part, int blocks, double* rel_err,
                                cudaStream_t st);

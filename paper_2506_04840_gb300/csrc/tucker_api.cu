@@ -285,11 +285,14 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
 
 // TTM shrink G <- G x_k U_k^T with U_k = Q(:, 1:r_k) (Algorithm 2/3, last
 // step of each k), instrumented.
+// U32: the same factor in FP32 (the returned U_k of an FP32 tensor), or NULL.
 static cudaError_t ttm(XType xt, const void* X, View v, const double* U, int r, void* out,
-                       cudaStream_t st, int tout = 0, void* scratch = nullptr) {
+                       cudaStream_t st, int tout = 0, void* scratch = nullptr,
+                       const void* U32 = nullptr) {
   const double N = (double)v.P * (double)v.n * (double)v.S;
   ProfScope ps(TK_K_TTM, (N + N / v.n * r) * xsize(xt), 2.0 * N * r, st);
-  return launch_xtb(xt, X, v, U, 1, v.n, r, out, st, tout, scratch);
+  return launch_xtb(xt, X, v, U, 1, v.n, r, out, st, tout, scratch,
+                    xt == X_F32 ? (const float*)U32 : nullptr);
 }
 
 static cudaError_t polish(double* Q, int64_t n, int r, void* scratch, int* status,
@@ -337,7 +340,7 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
         if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
         TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
         void* out = (step == p.d - 1) ? core : w.g[pp];
-        TK_TRY(ttm(p.xt, X, v, w.Q, p.r[k], out, st, p.rot ? 1 : 0, w.part));
+        TK_TRY(ttm(p.xt, X, v, w.Q, p.r[k], out, st, p.rot ? 1 : 0, w.part, U[k]));
         X = out;
         pp ^= 1;
         cur[k] = p.r[k];
@@ -361,7 +364,7 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
       for (int k = 0; k < p.d; ++k) {
         const View v = view_of(cur, k);
         void* out = (k == p.d - 1) ? core : w.g[k & 1];
-        TK_TRY(ttm(p.xt, X, v, qd[k], p.r[k], out, st));
+        TK_TRY(ttm(p.xt, X, v, qd[k], p.r[k], out, st, 0, nullptr, U[k]));
         X = out;
         cur[k] = p.r[k];
       }
@@ -583,7 +586,8 @@ tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const
       const double cin = (double)v.P * v.n * v.S;
       ProfScope ps(TK_K_ERROR, (cin + cin / v.n * A->n[k]) * es, 2.0 * cin / v.n * A->n[k] * v.n,
                    st);
-      e = launch_xtb(xt, X, v, Ud[k], A->n[k], 1, (int)A->n[k], tb[k & 1], st);
+      e = launch_xtb(xt, X, v, Ud[k], A->n[k], 1, (int)A->n[k], tb[k & 1], st, 0, nullptr,
+                     xt == X_F32 ? (const float*)U[k] : nullptr);
       X = tb[k & 1];
       dims[k] = A->n[k];
     }
@@ -592,7 +596,8 @@ tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const
     ProfScope ps(TK_K_ERROR, Nf * es + (double)vl.P * vl.n * es, 2.0 * Nf * vl.n, st);
     if (e == cudaSuccess)
       e = launch_xtb_error(xt, X, vl, Ud[d - 1], A->n[d - 1], 1, (int)A->n[d - 1], A->data,
-                           (double*)(base + ep), &nb, st);
+                           (double*)(base + ep), &nb, st,
+                           xt == X_F32 ? (const float*)U[d - 1] : nullptr);
     if (e == cudaSuccess) e = launch_error_final((double*)(base + ep), nb, rel_err, st);
     return e;
   };
