@@ -388,7 +388,7 @@ k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy, z = lb / gxy, r = lb % gxy;
     const int64_t ib = (int64_t)z * J.kps, ie = min(J.n, ib + J.kps);
     float* o = J.part ? (float*)J.part + (int64_t)z * J.cols * J.m : (float*)J.out;
-    xtb32_body<WJ, WC, double>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
+    xtb32_body<WJ, WC, float>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
                        J.part ? 0 : J.tout, ib, ie, r % (uint32_t)J.gx, r / (uint32_t)J.gx);
     __syncthreads();
   }
@@ -550,7 +550,7 @@ k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const int j = batch_job(start, njobs, b);
     const Err32Job J = jobs[j];
     const uint32_t lb = b - __ldg(start + j);
-    err32_body<double>((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A,
+    err32_body<float>((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A,
                        J.err,
                lb % (uint32_t)J.gx, lb / (uint32_t)J.gx, (uint32_t)J.gx);
   }
@@ -598,10 +598,12 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // scratch: the row-split partials (when the rows are split), then B in FP32
 // (n x m): converting B once here instead of per element in every CTA
-size_t xtb32_scratch(View v, int m) {
+size_t xtb32_b32_offset(View v, int m) {
   const Xtb32Shape s = xtb32_shape(v, m, true);
-  const size_t part = s.ks > 1 ? al256((size_t)s.ks * v.cols() * m * sizeof(float)) : 0;
-  return part + al256((size_t)v.n * m * sizeof(float));
+  return s.ks > 1 ? al256((size_t)s.ks * v.cols() * m * sizeof(float)) : 0;
+}
+size_t xtb32_scratch(View v, int m) {
+  return xtb32_b32_offset(v, m) + al256((size_t)v.n * m * sizeof(float));
 }
 
 Xb32Shape xb32_shape(View v, int l, int splits_req) {
@@ -677,8 +679,7 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
     xtb32_wc(x, v, B, b_ri, b_cm, m, o, tout, (float*)nullptr, s, st);
     return cudaGetLastError();
   } else {
-    float* b32 = (float*)((unsigned char*)scratch +
-                          (s.ks > 1 ? al256((size_t)s.ks * v.cols() * m * sizeof(float)) : 0));
+    float* b32 = (float*)((unsigned char*)scratch + xtb32_b32_offset(v, m));
     count_kernels(s.ks > 1 ? 3 : 2);
     const int64_t nb = v.n * m;
     c32::k_b_to_f32<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B, b_ri, b_cm, v.n, m, b32);

@@ -1629,7 +1629,7 @@ __global__ void __launch_bounds__(256) k_ritz_sum(const double* __restrict__ par
 
 // Z (l x l, column c = eigenvector of the c-th largest eigenvalue of G).
 // smem: J (l*l) | Vp (l*l) | sg (l) | nrm (l), FP32.
-__global__ void __launch_bounds__(256) k_ritz_eig(const double* __restrict__ G, int l,
+__global__ void __launch_bounds__(512) k_ritz_eig(const double* __restrict__ G, int l,
                                                   float* __restrict__ Z, int* __restrict__ status) {
   extern __shared__ __align__(16) float sre[];
   float* J = sre;
@@ -1772,7 +1772,7 @@ cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* s
   count_kernels(1);
   k_ritz_sum<<<(l * l + 255) / 256, 256, 0, st>>>(part, nb, l * l, G);
   count_kernels(1);
-  k_ritz_eig<<<1, 256, (2 * l * l + 2 * l) * sizeof(float), st>>>(G, l, Z, status);
+  k_ritz_eig<<<1, 512, (2 * l * l + 2 * l) * sizeof(float), st>>>(G, l, Z, status);
   count_kernels(1);
   const int64_t ntile = (cols + kRitzRows - 1) / kRitzRows;
   const int grid = (int)std::min<int64_t>(ntile, 152 * 8);

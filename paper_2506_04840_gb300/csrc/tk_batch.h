@@ -94,7 +94,7 @@ struct ErrFinalJob {
 struct Xtb32Job {
   const void* X;
   int64_t n, cols;
-  const double* B;
+  const float* B;       // B rounded to FP32 (as the single-problem path rounds it)
   int64_t b_ri, b_cm;
   void* out;
   void* part;           // non-null: row splits write partials here (ks > 1)
@@ -105,7 +105,7 @@ struct Xtb32Job {
 struct Err32Job {
   const void* T;
   int64_t P;
-  const double* B;
+  const float* B;       // the returned FP32 factor
   int64_t b_ri, b_cm;
   const void* A;
   double* err;

@@ -55,6 +55,8 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
                          int m, void* out, cudaStream_t st, int tout = 0,
                          void* scratch = nullptr, const float* B32 = nullptr);
 size_t xtb32_scratch(View v, int m);
+// offset of the FP32 copy of B inside that scratch
+size_t xtb32_b32_offset(View v, int m);
 // FP32 last-mode expansion fused with the error sums (S == 1): err_part gets
 // err32_blocks(v, m) (e^2, a^2) pairs.
 bool err32_ok(XType xt, View v);

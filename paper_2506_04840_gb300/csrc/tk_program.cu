@@ -51,13 +51,25 @@ uint32_t cdiv(int64_t a, int64_t b) { return (uint32_t)((a + b - 1) / b); }
 // out = X x_k B^T (EPI 0) as the single-problem launch_xtb runs it (with the
 // same scratch): the FP32 mode-major kernel where it applies (+ the sum of its
 // row splits at position pos + 1), else the generic one.
+// The FP32 kernel reads B in FP32: B32 (same strides) when given, else B is
+// first rounded into the scratch (at position pos - 1; scratch required).
 void xtb_ops(Phase& ph, int pos, int prof, XType xt, const void* X, View v, const double* B,
              int64_t b_ri, int64_t b_cm, int m, void* out, double bytes, double flops,
-             int tout = 0, void* scratch = nullptr) {
+             int tout = 0, void* scratch = nullptr, const float* B32 = nullptr) {
   if (xtb32_ok(xt, v, X)) {
     const Xtb32Shape sh = xtb32_shape(v, m, scratch != nullptr);
     void* part = sh.ks > 1 ? scratch : nullptr;
-    Xtb32Job j{X, v.n, v.cols(), B, b_ri, b_cm, out, part, sh.kps, m, sh.gx, sh.gy, tout};
+    if (B32 == nullptr) {
+      // B is a column-major n x m FP64 factor here (b_ri = 1, b_cm = n)
+      float* b32 = (float*)((unsigned char*)scratch + xtb32_b32_offset(v, m));
+      CopyJob cj{B, b32, b_cm, v.n, v.n, m};
+      ph.push_back(make_op(pos - 1, TK_K_CONVERT, BK_COPY, X_F32, 0, 0, 0, cdiv(v.n * m, 256),
+                           (double)v.n * m * 12.0, 0.0, cj));
+      B32 = b32;
+      b_ri = 1;
+      b_cm = v.n;
+    }
+    Xtb32Job j{X, v.n, v.cols(), B32, b_ri, b_cm, out, part, sh.kps, m, sh.gx, sh.gy, tout};
     ph.push_back(make_op(pos, prof, BK_XTB32, xt, sh.wc, sh.wj << 1, 0,
                          (uint32_t)sh.gx * sh.gy * sh.ks, bytes, flops, j));
     if (part) {
@@ -215,16 +227,16 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     // ---- power phases
     for (int t = 1; t <= p.q; ++t) {
       Phase ph;
-      xtb_ops(ph, 0, TK_K_POWER_W, xt, X, v, w.Q, 1, v.n, l, w.w, N * es, 2.0 * N * l, 0, w.part);
-      ph.push_back(xb_op(2, TK_K_POWER_Y, xt, X, v, w.w, l, it.seed, it.tag, k, w.part, splits,
+      xtb_ops(ph, 1, TK_K_POWER_W, xt, X, v, w.Q, 1, v.n, l, w.w, N * es, 2.0 * N * l, 0, w.part);
+      ph.push_back(xb_op(3, TK_K_POWER_Y, xt, X, v, w.w, l, it.seed, it.tag, k, w.part, splits,
                          N * es, 2.0 * N * l));
       ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc};
-      ph.push_back(make_op(3, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
+      ph.push_back(make_op(4, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
                 stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,
                 (int)p.rule, 1, 0};
-      ph.push_back(make_op(4, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+      ph.push_back(make_op(5, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
                            2.0 * nl * 8.0, svd_flops, sv));
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + t);
@@ -252,8 +264,9 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
                              cdiv(v.n * r, 256), (double)v.n * r * 16.0, 0.0, cq));
       }
       void* out = (step == d - 1) ? it.core : w.g[pp];
+      // the TTM reads the returned factor (FP32 for an FP32 tensor)
       xtb_ops(ph, 3, TK_K_TTM, xt, X, v, w.Q, 1, v.n, r, out, (N + N / v.n * r) * es,
-              2.0 * N * r, p.rot ? 1 : 0, w.part);
+              2.0 * N * r, p.rot ? 1 : 0, w.part, fp64 ? nullptr : (const float*)it.U[k]);
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + TK_MAX_Q + 1);
       X = out;
@@ -272,7 +285,8 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       const int m = (int)p.n[k];
       const double cin = (double)v.P * v.n * v.S;
       xtb_ops(ph, k, TK_K_ERROR, xt, Xe, v, qd[k], p.n[k], 1, m, tb[k & 1],
-              (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n);
+              (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n, 0, nullptr,
+              fp64 ? nullptr : (const float*)it.U[k]);
       Xe = tb[k & 1];
       dims[k] = p.n[k];
     }
@@ -284,7 +298,8 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     double* ep = (double*)(base + ex.ep);
     if (err32_ok(xt, vl)) {
       const int gx = (int)cdiv(vl.P, 128);
-      Err32Job ej{Xe, vl.P, qd[d - 1], p.n[d - 1], 1, it.A.data, ep, (int)vl.n, m, gx};
+      Err32Job ej{Xe, vl.P, (const float*)it.U[d - 1], p.n[d - 1], 1, it.A.data, ep, (int)vl.n,
+                  m, gx};
       ph.push_back(make_op(d - 1, TK_K_ERROR, BK_ERR32, xt, 0, 0, 0,
                            (uint32_t)gx * cdiv(m, 64), Nf * es + (double)vl.P * vl.n * es,
                            2.0 * Nf * vl.n, ej));
