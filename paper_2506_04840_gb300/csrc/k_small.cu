@@ -793,8 +793,9 @@ constexpr int kRegCols = 16 * kRegCPW;       // 64
 
 __host__ __device__ __forceinline__ int reg_ld(int64_t m) { return (int)((m + 3) / 4 * 4); }
 
+template <int CPW>
 struct RegCols {
-  float y[kRegCPW][4 * kRegRK];
+  float y[CPW][4 * kRegRK];
   int lane, warp;
   __device__ __forceinline__ RegCols() : lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {}
   __device__ __forceinline__ int col(int s) const { return warp + 16 * s; }
@@ -819,17 +820,17 @@ struct RegCols {
   // y(:, c) <- (I - tj v v^T) y(:, c) for the owned columns lo < c < hi;
   // v = reflector j in shared memory, stored in full (0 above row j, 1 at j)
   __device__ __forceinline__ void apply(const float* v, int md, float tj, int lo, int hi) {
-    bool act[kRegCPW];
+    bool act[CPW];
     bool any = false;
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s) {
+    for (int s = 0; s < CPW; ++s) {
       act[s] = col(s) > lo && col(s) < hi;
       any = any || act[s];
     }
     if (!any || tj == 0.f) return;
-    float d[kRegCPW];
+    float d[CPW];
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s) d[s] = 0.f;
+    for (int s = 0; s < CPW; ++s) d[s] = 0.f;
 #pragma unroll
     for (int k = 0; k < kRegRK; ++k) {
       if (!has(k, md)) continue;
@@ -838,15 +839,15 @@ struct RegCols {
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int s = 0; s < kRegCPW; ++s)
+        for (int s = 0; s < CPW; ++s)
           if (act[s]) d[s] = fmaf(ve[e], y[s][4 * k + e], d[s]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int s = 0; s < kRegCPW; ++s) d[s] += __shfl_xor_sync(0xffffffffu, d[s], o);
+      for (int s = 0; s < CPW; ++s) d[s] += __shfl_xor_sync(0xffffffffu, d[s], o);
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s) d[s] *= -tj;
+    for (int s = 0; s < CPW; ++s) d[s] *= -tj;
 #pragma unroll
     for (int k = 0; k < kRegRK; ++k) {
       if (!has(k, md)) continue;
@@ -855,7 +856,7 @@ struct RegCols {
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int s = 0; s < kRegCPW; ++s)
+        for (int s = 0; s < CPW; ++s)
           if (act[s]) y[s][4 * k + e] = fmaf(d[s], ve[e], y[s][4 * k + e]);
     }
   }
@@ -908,7 +909,7 @@ struct RegCols {
   // (upper triangle) goes to rs[r * rr + c * rc] when rs is given.
   __device__ void qr(float* A, int md, int l, float* tau, float* rs, int rr, int rc) {
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s)
+    for (int s = 0; s < CPW; ++s)
       if (col(s) < l) load_col(s, A + (int64_t)md * col(s), md);
     if (warp == 0) build(0, 0, A, md, tau, rs, rr, rc);
     __syncthreads();
@@ -917,7 +918,7 @@ struct RegCols {
       const float* v = A + (int64_t)md * j;
       // the owner of column j+1 updates and factors it first (look-ahead)
 #pragma unroll
-      for (int s = 0; s < kRegCPW; ++s)
+      for (int s = 0; s < CPW; ++s)
         if (col(s) == j + 1 && j + 1 < l) {
           apply(v, md, tj, j, j + 2);
           build(s, j + 1, A + (int64_t)md * (j + 1), md, tau, rs, rr, rc);
@@ -936,7 +937,7 @@ struct RegCols {
   __device__ __forceinline__ void init_top(const float* src, int ld, const int* perm, int l,
                                            int nb) {
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s) {
+    for (int s = 0; s < CPW; ++s) {
       const int c = col(s);
       const int cs = c < nb ? (perm ? perm[c] : c) : 0;
 #pragma unroll
@@ -1097,6 +1098,7 @@ __host__ __device__ __forceinline__ size_t reg_one_smem(int64_t n, int l) {
 
 // [Q, Sigma] = svd(Y) for n <= 512, l <= 64 (FP32 working precision), or
 // with basis_only an orthonormal basis of span(Y); as svd_one_body.
+template <int CPW>
 __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n, int l,
                                              double* __restrict__ Q, double* __restrict__ sigma,
                                              int shift_rule, int update_shift, int basis_only,
@@ -1135,7 +1137,7 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
   if (!basis_only)
     for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
   __syncthreads();
-  RegCols R;
+  RegCols<CPW> R;
   R.qr(A, md, l, ts, basis_only ? nullptr : J, l, 1);   // J = R^T
   if (basis_only) {
     // only span(Y) is needed: Q = Q_h
@@ -1144,7 +1146,7 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
     R.init_top(Vp, l, nullptr, l, l);
     R.apply_back(A, md, l, ts, l);
 #pragma unroll
-    for (int s = 0; s < kRegCPW; ++s)
+    for (int s = 0; s < CPW; ++s)
       if (R.col(s) < l) R.store_out(s, Q, n, n, 1.f);
     return;
   }
@@ -1157,7 +1159,7 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
   R.init_top(Vp, l, perm, l, l);
   R.apply_back(A, md, l, ts, l);
 #pragma unroll
-  for (int s = 0; s < kRegCPW; ++s)
+  for (int s = 0; s < CPW; ++s)
     if (R.col(s) < l) {
       const float bv = R.col_extreme(s, n, nullptr);
       R.store_out(s, Q, n, n, bv < 0.f ? -1.f : 1.f);
@@ -1171,17 +1173,19 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
     shift_update((double)sg[perm[l - 1]] / scale, shift_rule, alpha, alpha_hist, sigl_hist);
 }
 
+template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_svd_reg(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
           double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
           double* __restrict__ alpha, double* __restrict__ alpha_hist,
           double* __restrict__ sigl_hist, int* __restrict__ status) {
-  svd_reg_body(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha, alpha_hist,
-               sigl_hist, status);
+  svd_reg_body<CPW>(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha, alpha_hist,
+                    sigl_hist, status);
 }
 
 // TSQR leaf (MB <= 512 rows, a multiple of 32): reflectors to V (ld MB), tau,
 // R into the stack Rst (Pb l x l, ld Pb l)
+template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
               float* __restrict__ V, float* __restrict__ tau, float* __restrict__ Rst) {
@@ -1203,7 +1207,7 @@ k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
     const int i = e % l, c = e / l;
     if (i > c) Rb[i + (int64_t)ldr * c] = 0.f;
   }
-  RegCols R;
+  RegCols<CPW> R;
   R.qr(A, MB, l, ts, Rb, 1, ldr);
   float* Vb = V + (int64_t)b * MB * l;
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) Vb[e] = A[e];
@@ -1213,6 +1217,7 @@ k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
 // TSQR root (m = Pb l <= 512): QR of the stacked R's, svd of the root R, and
 // Mout = Q_root U_R (m x l, ld m); sigma and the shift update.
 // smem: S (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l)
+template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mout,
            double* __restrict__ sigma, int shift_rule, int update_shift,
@@ -1234,7 +1239,7 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
   }
   for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
   __syncthreads();
-  RegCols R;
+  RegCols<CPW> R;
   R.qr(S, md, l, ts, J, l, 1);   // J = R^T
   for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
   __syncthreads();
@@ -1243,7 +1248,7 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
   R.init_top(Vp, l, perm, l, l);
   R.apply_back(S, md, l, ts, l);
 #pragma unroll
-  for (int s = 0; s < kRegCPW; ++s)
+  for (int s = 0; s < CPW; ++s)
     if (R.col(s) < l) R.store_out(s, Mout, m, m, 1.f);
   if (tid < l) {
     const double sv = (double)sg[perm[tid]];
@@ -1257,6 +1262,7 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
 // TSQR leaf Q: rows r0.. of Q = Q_leaf [M_b; 0] (M_b = rows b l.. of Mout),
 // written in FP64, with each column's entry of largest magnitude (and its
 // global row) for the sign pass.  smem: B (MB*l reflectors) | tau (l)
+template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
              const float* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
@@ -1272,11 +1278,11 @@ k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) B[e] = Vb[e];
   for (int j = threadIdx.x; j < l; j += blockDim.x) ts[j] = tau[(int64_t)b * l + j];
   __syncthreads();
-  RegCols R;
+  RegCols<CPW> R;
   R.init_top(Mout + (int64_t)b * l, m, nullptr, l, l);
   R.apply_back(B, MB, l, ts, l);
 #pragma unroll
-  for (int s = 0; s < kRegCPW; ++s)
+  for (int s = 0; s < CPW; ++s)
     if (R.col(s) < l) {
       int bi = 0;
       const float bv = R.col_extreme(s, rows, &bi);
@@ -1367,6 +1373,40 @@ SmallPlan small_plan(int64_t n, int l, bool fp64) {
   return p;
 }
 
+// Register-resident kernels with CPW columns per warp (16 warps hold l <= 16 CPW
+// columns; CPW = 2 for l <= 32 keeps no idle column slots).
+template <int CPW>
+static cudaError_t reg_go(const SmallPlan& pl, const double* Y, int64_t n, double* Q,
+                          double* sigma, void* scratch, int shift_rule, bool update_shift,
+                          bool basis_only, double* alpha, double* alpha_hist, double* sigl_hist,
+                          int* status, cudaStream_t st) {
+  const int l = pl.l, MB = pl.MB, Pb = pl.Pb;
+  if (Pb == 1) {
+    count_kernels(1);
+    k_svd_reg<CPW><<<1, kRegThreads, reg_one_smem(n, l), st>>>(
+        Y, (int)n, l, Q, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
+        alpha_hist, sigl_hist, status);
+    return cudaGetLastError();
+  }
+  unsigned char* w = (unsigned char*)scratch;
+  float* V = (float*)w;        w += align256((size_t)Pb * MB * l * 4);
+  float* tau = (float*)w;      w += align256((size_t)Pb * l * 4);
+  float* Rst = (float*)w;      w += align256((size_t)Pb * l * l * 4);
+  float* Mout = (float*)w;     w += align256((size_t)Pb * l * l * 4);
+  double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
+  int* colidx = (int*)w;
+  const size_t leaf_smem = ((size_t)MB * l + l) * sizeof(float);
+  count_kernels(4);
+  k_leaf_qr_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
+  k_root_reg<CPW><<<1, kRegThreads, reg_one_smem((int64_t)Pb * l, l), st>>>(
+      Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, alpha, alpha_hist, sigl_hist,
+      status);
+  k_leaf_q_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
+                                                         colidx);
+  k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, double* Q,
                             double* sigma, void* scratch, int shift_rule, bool update_shift,
@@ -1381,37 +1421,22 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
     cudaFuncSetAttribute(k_leaf_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_root<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_leaf_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_svd_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_leaf_qr_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_root_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_leaf_q_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_svd_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_svd_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_qr_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_qr_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_root_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_root_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_q_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_leaf_q_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     attr_set = true;
   }
   if (pl.reg && sizeof(T) == 4) {
-    if (Pb == 1) {
-      count_kernels(1);
-      k_svd_reg<<<1, kRegThreads, reg_one_smem(n, l), st>>>(
-          Y, (int)n, l, Q, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
-          alpha_hist, sigl_hist, status);
-      return cudaGetLastError();
-    }
-    unsigned char* w = (unsigned char*)scratch;
-    float* V = (float*)w;        w += align256((size_t)Pb * MB * l * 4);
-    float* tau = (float*)w;      w += align256((size_t)Pb * l * 4);
-    float* Rst = (float*)w;      w += align256((size_t)Pb * l * l * 4);
-    float* Mout = (float*)w;     w += align256((size_t)Pb * l * l * 4);
-    double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
-    int* colidx = (int*)w;
-    const size_t leaf_smem = ((size_t)MB * l + l) * sizeof(float);
-    count_kernels(4);
-    k_leaf_qr_reg<<<Pb, kRegThreads, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
-    k_root_reg<<<1, kRegThreads, reg_one_smem((int64_t)Pb * l, l), st>>>(
-        Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, alpha, alpha_hist, sigl_hist,
-        status);
-    k_leaf_q_reg<<<Pb, kRegThreads, leaf_smem, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
-                                                      colidx);
-    k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
-    return cudaGetLastError();
+    if (l <= 32)
+      return reg_go<2>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, basis_only, alpha,
+                       alpha_hist, sigl_hist, status, st);
+    return reg_go<4>(pl, Y, n, Q, sigma, scratch, shift_rule, update_shift, basis_only, alpha,
+                     alpha_hist, sigl_hist, status, st);
   }
   if (Pb == 1) {
     const int threads = (int64_t)n * l >= 4096 ? 1024 : 256;
@@ -1454,12 +1479,13 @@ __global__ void k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __r
   }
 }
 
+template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_svd_batch_reg(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
                 uint32_t total) {
   for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
     const SvdJob J = jobs[batch_job(start, njobs, b)];
-    svd_reg_body(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
+    svd_reg_body<CPW>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
                  J.alpha, J.ahist, J.shist, J.status);
     __syncthreads();
   }
@@ -1487,6 +1513,10 @@ k_polish_batch(const PolishJob* __restrict__ jobs, const uint32_t* __restrict__ 
   }
 }
 
+int svd_variant(int64_t n, int l, bool fp64) {
+  if (!svd_reg_fits(n, l, fp64)) return 0;
+  return l <= 32 ? 2 : 4;
+}
 int svd_threads(int64_t n, int l, bool fp64) {
   if (svd_reg_fits(n, l, fp64)) return kRegThreads;
   return (int64_t)n * l >= 4096 ? 1024 : 256;
@@ -1506,7 +1536,8 @@ void batch_kernels_init() {
   const int mx = (int)kSmemBudget + 4096;
   cudaFuncSetAttribute(k_svd_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_svd_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_svd_batch_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_svd_batch_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_svd_batch_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_gram_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_polish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   attr = true;
@@ -1519,7 +1550,10 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
       if (b.xt == X_F64) return run_batch(k_svd_batch<double>, b, b.tile, st);
       // jobs of one launch share a thread count: the register-resident ones
       // run 512 threads, no other svd does
-      if (b.tile == kRegThreads) return run_batch(k_svd_batch_reg, b, kRegThreads, st);
+      if (b.tile == kRegThreads) {
+        if (b.flag == 2) return run_batch(k_svd_batch_reg<2>, b, kRegThreads, st);
+        return run_batch(k_svd_batch_reg<4>, b, kRegThreads, st);
+      }
       return run_batch(k_svd_batch<float>, b, b.tile, st);
     case BK_GRAM:
       return run_batch(k_gram_batch, b, 256, st);

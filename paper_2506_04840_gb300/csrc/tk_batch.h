@@ -175,6 +175,8 @@ int xb_grid_x(View v, int l);
 int64_t xb_cols_per_split(XType xt, View v, int splits);
 int xtb_tile(int m);
 int svd_threads(int64_t n, int l, bool fp64);
+// 0: shared-memory svd; 2 or 4: register-resident svd with that many columns per warp
+int svd_variant(int64_t n, int l, bool fp64);
 size_t svd_smem(int64_t n, int l, bool fp64);
 int polish_blocks(int64_t n);
 size_t gram_smem(int r);

@@ -207,6 +207,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     double* sig = stt->sig + (size_t)k * TK_MAX_L;
     double* alpha = stt->alpha + k;
     const int sthreads = svd_threads(v.n, l, fp64);
+    const int svar = svd_variant(v.n, l, fp64);
     const size_t ssmem = svd_smem(v.n, l, fp64);
 
     // ---- sketch phase
@@ -219,7 +220,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,
                 0, p.q >= 1 ? 1 : 0};
-      ph.push_back(make_op(2, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+      ph.push_back(make_op(2, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, svar, ssmem, 1,
                            2.0 * nl * 8.0, svd_flops, sv));
       prog.push_back(ph);
       pr->slot.push_back(step * per_step);
@@ -236,7 +237,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
                 stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,
                 (int)p.rule, 1, 0};
-      ph.push_back(make_op(5, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, 0, ssmem, 1,
+      ph.push_back(make_op(5, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, svar, ssmem, 1,
                            2.0 * nl * 8.0, svd_flops, sv));
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + t);
