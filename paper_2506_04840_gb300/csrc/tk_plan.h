@@ -137,6 +137,9 @@ struct HosvdWs {
 
 tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st, HosvdPlan& p);
 // Lays the workspace out from `base` (nullptr: only measures); returns bytes.
+// ws (when given) receives workspace_copies(p) entries (one per concurrently
+// factored mode; they share the tensor buffers, histories and status).
+int workspace_copies(const HosvdPlan& p);
 size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws);
 
 }  // namespace tk

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <deque>
 #include <vector>
 
 #include "tk_common.cuh"
@@ -163,6 +164,12 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
   return TK_OK;
 }
 
+// T-HOSVD factors its modes concurrently (one stream each), so every mode
+// gets its own W, partials, Y, Q, small-solver scratch and shift; ST-HOSVD
+// (sequential by definition) lays out one set.  ws (when given) receives
+// workspace_copies(p) entries.
+int workspace_copies(const HosvdPlan& p) { return p.st ? 1 : p.d; }
+
 size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
   Arena a;
   a.base = base;
@@ -170,26 +177,32 @@ size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
   w.g[0] = a.take(p.gbuf);
   w.g[1] = a.take(p.gbuf);
   w.shadow = a.take(p.shadow);
-  w.w = a.take(p.wbuf);
-  w.part = a.take(p.part);
-  w.Y = (double*)a.take(p.ymat);
-  w.Q = (double*)a.take(p.ymat);
-  w.small = a.take(p.small);
   w.qd = (double*)a.take(p.qd);
-  w.alpha = (double*)a.take(sizeof(double));
   w.ahist = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_Q);
   w.shist = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_Q);
   w.sig = (double*)a.take(sizeof(double) * TK_MAX_D * TK_MAX_L);
   w.status = (int*)a.take(sizeof(int));
-  if (ws) *ws = w;
+  const int copies = workspace_copies(p);
+  for (int c = 0; c < copies; ++c) {
+    HosvdWs m = w;
+    m.w = a.take(p.wbuf);
+    m.part = a.take(p.part);
+    m.Y = (double*)a.take(p.ymat);
+    m.Q = (double*)a.take(p.ymat);
+    m.small = a.take(p.small);
+    m.alpha = (double*)a.take(sizeof(double));
+    if (ws) ws[c] = m;
+  }
   return al(a.off) + 256;
 }
 
 // Sketch, q shifted power steps and the final svd for mode k of X
 // (Algorithm 2/3 steps for one k).  Leaves Q (n x l) and Sigma in ws.
+// shadow_ready: the bfloat16 copy of X is already in w.shadow (T-HOSVD
+// converts A once for all modes).
 static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt, View v,
                              int64_t ka, int64_t kb, uint64_t seed, uint32_t tag,
-                             const HosvdWs& w, cudaStream_t st) {
+                             const HosvdWs& w, cudaStream_t st, bool shadow_ready = false) {
   const int l = p.l[k];
   const int lc = xb_lc(l);
   const int splits = xb_splits(xt, v, l);
@@ -215,7 +228,7 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false,
                             w.alpha, nullptr, nullptr, w.status, st, p.q >= 1));
   }
-  if (p.bf16 && p.q >= 2) {
+  if (p.bf16 && p.q >= 2 && !shadow_ready) {
     ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
     TK_TRY(launch_to_bf16((const float*)X, v.P * v.n * v.S, (uint16_t*)w.shadow, st));
   }
@@ -301,6 +314,33 @@ static cudaError_t polish(double* Q, int64_t n, int r, void* scratch, int* statu
   return launch_polish(Q, n, r, scratch, status, st);
 }
 
+// Per-host-thread, per-device side streams and fork/join events for the
+// concurrent T-HOSVD modes (created on first use, kept for the process).
+struct SideStreams {
+  int dev = -1;
+  cudaStream_t s[TK_MAX_D] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[TK_MAX_D] = {};
+};
+
+static SideStreams& side_streams(int d) {
+  thread_local std::deque<SideStreams> pool;   // stable addresses
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (auto& e : pool)
+    if (e.dev == dev) return e;
+  pool.emplace_back();
+  SideStreams& e = pool.back();
+  e.dev = dev;
+  cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming);
+  for (int k = 1; k < TK_MAX_D; ++k) {
+    cudaStreamCreateWithFlags(&e.s[k], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&e.join[k], cudaEventDisableTiming);
+  }
+  (void)d;
+  return e;
+}
+
 static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
                            void* const* U, tk_stats* stats, cudaStream_t st, bool sequential) {
   HosvdPlan p;
@@ -318,8 +358,9 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
   } else if (o->workspace_bytes < need) {
     return TK_EWORKSPACE;
   }
-  HosvdWs w;
-  carve(p, (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255), &w);
+  HosvdWs wm[TK_MAX_D];
+  carve(p, (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255), wm);
+  const HosvdWs& w = wm[0];
   tk_status rs = TK_OK;
   auto run = [&]() -> tk_status {
     TK_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), st));
@@ -346,18 +387,39 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
         cur[k] = p.r[k];
       }
     } else {
+      // Algorithm 2's modes are independent: each factors on its own stream
+      // (forked from and joined back to the call's stream by events)
       size_t off = 0;
       std::vector<double*> qd(p.d);
+      if (p.bf16 && p.q >= 2) {
+        const double N = (double)prod(p.n);
+        ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
+        TK_TRY(launch_to_bf16((const float*)A->data, prod(p.n), (uint16_t*)w.shadow, st));
+      }
+      SideStreams& ss = side_streams(p.d);
+      TK_TRY(cudaEventRecord(ss.fork, st));
+      tk_status first = TK_OK;
       for (int k = 0; k < p.d; ++k) {
         qd[k] = (double*)((unsigned char*)w.qd + off);
         off += al((size_t)p.n[k] * p.r[k] * sizeof(double));
         const View v = view_of(p.n, k);
-        tk_status e = factor_mode(p, k, A->data, p.xt, v, 0, 1, o->seed, o->tag, w, st);
-        if (e != TK_OK) return e;
-        if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
-        TK_TRY(launch_copy_matrix(w.Q, v.n, qd[k], v.n, v.n, p.r[k], X_F64, st));
-        TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
+        const HosvdWs& wk = wm[k];
+        cudaStream_t sk = k == 0 ? st : ss.s[k];
+        if (k > 0) TK_TRY(cudaStreamWaitEvent(sk, ss.fork, 0));
+        tk_status e = factor_mode(p, k, A->data, p.xt, v, 0, 1, o->seed, o->tag, wk, sk, true);
+        if (e == TK_OK && p.xt != X_F64) e = from_cuda(polish(wk.Q, v.n, p.r[k], wk.small, wk.status, sk));
+        if (e == TK_OK) e = from_cuda(launch_copy_matrix(wk.Q, v.n, qd[k], v.n, v.n, p.r[k], X_F64, sk));
+        if (e == TK_OK) e = from_cuda(launch_copy_matrix(wk.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, sk));
+        if (k > 0) {
+          // join even after an error, so no side-stream work outlives the call
+          cudaError_t j = cudaEventRecord(ss.join[k], sk);
+          if (j == cudaSuccess) j = cudaStreamWaitEvent(st, ss.join[k], 0);
+          if (e == TK_OK && j != cudaSuccess) e = from_cuda(j);
+        }
+        if (first == TK_OK) first = e;
+        if (e != TK_OK) break;
       }
+      if (first != TK_OK) return first;
       // core G = A x_1 U_1^T ... x_d U_d^T (Algorithm 2, last step of each k)
       const void* X = A->data;
       std::vector<int64_t> cur = p.n;
