@@ -235,6 +235,21 @@ def test_workspace_and_determinism(lib):
         assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def test_thosvd_concurrent_modes_workspace_and_determinism(lib):
+    """Algorithm 2 factors its modes concurrently (one stream each, one
+    workspace set each): a caller workspace of tucker_workspace_size bytes
+    and the internal allocation give bitwise the same results, run after
+    run, and the precision form too."""
+    A = I.tucker_plus_noise([70, 50, 40], [6, 6, 6], 33, noise=1e-3, dtype=np.float32)
+    for prec in (api.TK_PREC_PLAIN, api.TK_PREC_BF16_POWER):
+        G1, U1, _ = run_hosvd(A, [5, 5, 5], 5, 3, st=False, prec=prec)
+        G2, U2, _ = run_hosvd(A, [5, 5, 5], 5, 3, st=False, prec=prec, workspace=True)
+        G3, U3, _ = run_hosvd(A, [5, 5, 5], 5, 3, st=False, prec=prec, stats=False)
+        assert np.array_equal(G1, G2) and np.array_equal(G1, G3)
+        for a, b, c in zip(U1, U2, U3):
+            assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
 def test_rank_exceeding_columns_is_rejected(lib):
     # mode 1 has 2*2 = 4 columns: l_1 = min(5 + 1, 6, 4) = 4 < r_1 = 5
     A = np.asfortranarray(np.ones((6, 2, 2), dtype=np.float32))
