@@ -1609,19 +1609,50 @@ __global__ void __launch_bounds__(256) k_ritz_gram(const float* __restrict__ W, 
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f, accd[i][j] = 0.0;
   const int64_t jb = (int64_t)blockIdx.x * R;
   const int64_t je = min(cols, jb + R);
+  // mode-major W with l a multiple of 4: a tile is 64 l contiguous floats,
+  // staged as float4 and the next tile prefetched into registers
+  const bool vec = P == 1 && (l & 3) == 0 && l <= kRegCols;
+  constexpr int NV = kRitzRows * kRegCols / 4 / 256;   // float4 per thread (l <= 64)
+  float4 pre[NV];
+  auto vload = [&](int64_t t0) {
+    const int64_t nel = (min(je, t0 + kRitzRows) - t0) * l;
+    const float4* src = reinterpret_cast<const float4*>(W + t0 * l);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e4 = tid + q * 256;
+      pre[q] = 4 * (int64_t)e4 < nel ? __ldg(src + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (vec && jb < je) vload(jb);
   int tiles = 0;
   for (int64_t j0 = jb; j0 < je; j0 += kRitzRows) {
     __syncthreads();
-    if (tid < kRitzRows) {
-      const int64_t j = j0 + tid;
-      offw[tid] = j < je ? ritz_off(j, P, l) : -1;
-    }
-    __syncthreads();
-    for (int e = tid; e < kRitzRows * l; e += 256) {
-      int r, c;
-      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
-      const int64_t o = offw[r];
-      sgw[r * S + c] = o >= 0 ? __ldg(W + o + P * c) : 0.f;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int e4 = tid + q * 256;
+        if (4 * e4 < kRitzRows * l) {
+          const float v[4] = {pre[q].x, pre[q].y, pre[q].z, pre[q].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int e = 4 * e4 + k, r = e / l;
+            sgw[r * S + (e - r * l)] = v[k];
+          }
+        }
+      }
+      if (j0 + kRitzRows < je) vload(j0 + kRitzRows);
+    } else {
+      if (tid < kRitzRows) {
+        const int64_t j = j0 + tid;
+        offw[tid] = j < je ? ritz_off(j, P, l) : -1;
+      }
+      __syncthreads();
+      for (int e = tid; e < kRitzRows * l; e += 256) {
+        int r, c;
+        if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+        const int64_t o = offw[r];
+        sgw[r * S + c] = o >= 0 ? __ldg(W + o + P * c) : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll 4
