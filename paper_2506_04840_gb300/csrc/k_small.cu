@@ -647,10 +647,13 @@ __global__ void k_sign(double* __restrict__ Q, int64_t n, int l, int Pb,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 re-orthonormalisation of a factor computed in FP32 arithmetic:
-// U <- U R^{-1} with R^T R = U^T U (one CholeskyQR step).  U is already
-// orthonormal to FP32 rounding, so the Gram matrix is within ~1e-5 of the
-// identity and the Cholesky factorisation is perfectly conditioned.
+// Re-orthonormalisation of a factor computed in FP32 arithmetic (FP64
+// storage): one CholeskyQR step U <- U R^{-1}, R^T R = G = U^T U, taken to
+// first order.  U is orthonormal to FP32 rounding, so G = I + E with
+// |E| ~ 1e-6; R = I + F + O(|E|^2) with F the upper triangle of E (diagonal
+// halved) and R^{-1} = I - F + O(|E|^2).  The O(1e-12) remainder is far
+// below the FP32 rounding of the returned factor, and the correction U F
+// (itself ~1e-6 |U|) needs only FP32 arithmetic; G and the update are FP64.
 // ---------------------------------------------------------------------------
 constexpr int kPolishRows = 64;
 
@@ -680,71 +683,44 @@ __global__ void k_gram_part(const double* __restrict__ U, int64_t n, int r,
   gram_part_body(U, n, r, part, blockIdx.x);
 }
 
-// smem: R (r*r) | block rows (kPolishRows*r)
+// smem: F (r*r, FP32) | block rows (kPolishRows*r, FP64)
 __device__ __forceinline__ void polish_body(double* __restrict__ U, int64_t n, int r, int nblk,
                                             const double* __restrict__ part,
                                             int* __restrict__ status, unsigned bx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* R = reinterpret_cast<double*>(smem_raw);
-  double* Ub = R + (int64_t)r * r;
+  float* F = reinterpret_cast<float*>(smem_raw);
+  double* Ub = reinterpret_cast<double*>(smem_raw + (((size_t)r * r * sizeof(float) + 15) & ~(size_t)15));
   __shared__ int bad;
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)bx * kPolishRows;
   const int rows = (int)min((int64_t)kPolishRows, n - r0);
   if (tid == 0) bad = 0;
+  __syncthreads();
   for (int e = tid; e < r * r; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * r * r + e];
-    R[e] = s;
+    double g = 0.0;
+    for (int b = 0; b < nblk; ++b) g += part[(int64_t)b * r * r + e];
+    const int i = e % r, c = e / r;
+    const double dev = g - (i == c ? 1.0 : 0.0);
+    // a factor this far from orthonormal is not a rounding-level correction
+    if (!(fabs(dev) <= 0.25)) bad = 1;
+    F[e] = i < c ? (float)dev : (i == c ? (float)(0.5 * dev) : 0.f);
   }
   for (int e = tid; e < kPolishRows * r; e += blockDim.x) {
     const int i = e % kPolishRows, c = e / kPolishRows;
     Ub[e] = i < rows ? U[(r0 + i) + n * c] : 0.0;
   }
-  __shared__ double rinv[TK_MAX_L];
   __syncthreads();
-  // Cholesky, upper factor in place: R(i, j) for i <= j, R^T R = G.  FP64
-  // division and square root are slow on this GPU, so each diagonal entry is
-  // inverted once (by the warp that forms it) and rows are scaled by it.
-  const int lane = tid & 31;
-  for (int j = 0; j < r; ++j) {
-    if (tid < 32) {
-      double d = 0.0;
-      for (int k = lane; k < j; k += 32) d += R[k + r * j] * R[k + r * j];
-      d = warp_sum(d);
-      if (lane == 0) {
-        double g = R[j + r * j] - d;
-        if (!(g > 0.0)) { bad = 1; g = 1.0; }
-        const double rj = sqrt(g);
-        R[j + r * j] = rj;
-        rinv[j] = 1.0 / rj;
-      }
-    }
-    __syncthreads();
-    const double ij = rinv[j];
-    for (int c = j + 1 + tid; c < r; c += blockDim.x) {
-      double s = R[j + r * c];
-      for (int k = 0; k < j; ++k) s -= R[k + r * j] * R[k + r * c];
-      R[j + r * c] = s * ij;
-    }
-    __syncthreads();
-  }
   if (bad) {
     if (tid == 0 && bx == 0) atomicExch(status, (int)TK_EBREAKDOWN);
     return;
   }
-  // rows of this block: u <- u R^{-1} (forward substitution on R^T), in smem
-  for (int i = tid; i < rows; i += blockDim.x) {
-    for (int c = 0; c < r; ++c) {
-      double s = Ub[i + kPolishRows * c];
-      for (int k = 0; k < c; ++k) s -= Ub[i + kPolishRows * k] * R[k + r * c];
-      Ub[i + kPolishRows * c] = s * rinv[c];
-    }
-  }
-  __syncthreads();
+  // u(c) <- u(c) - sum_{k <= c} u(k) F(k, c)
   for (int e = tid; e < kPolishRows * r; e += blockDim.x) {
     const int i = e % kPolishRows, c = e / kPolishRows;
-    if (i < rows) U[(r0 + i) + n * c] = Ub[e];
+    if (i >= rows) continue;
+    float s = 0.f;
+    for (int k = 0; k <= c; ++k) s = fmaf((float)Ub[i + kPolishRows * k], F[k + r * c], s);
+    U[(r0 + i) + n * c] = Ub[e] - (double)s;
   }
 }
 
@@ -770,7 +746,7 @@ cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* statu
   count_kernels(2);
   k_gram_part<<<nblk, 256, (size_t)kPolishRows * r * sizeof(double), st>>>(U, n, r,
                                                                            (double*)scratch);
-  k_polish<<<nblk, 64, ((size_t)r * r + (size_t)kPolishRows * r) * sizeof(double), st>>>(
+  k_polish<<<nblk, 256, polish_smem(r), st>>>(
       U, n, r, nblk, (const double*)scratch, status);
   return cudaGetLastError();
 }
@@ -1502,7 +1478,7 @@ k_gram_batch(const GramJob* __restrict__ jobs, const uint32_t* __restrict__ star
   }
 }
 
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(256)
 k_polish_batch(const PolishJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
                uint32_t total) {
   for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
@@ -1526,7 +1502,9 @@ size_t svd_smem(int64_t n, int l, bool fp64) {
 }
 int polish_blocks(int64_t n) { return (int)((n + kPolishRows - 1) / kPolishRows); }
 size_t gram_smem(int r) { return (size_t)kPolishRows * r * sizeof(double); }
-size_t polish_smem(int r) { return ((size_t)r * r + (size_t)kPolishRows * r) * sizeof(double); }
+size_t polish_smem(int r) {
+  return (((size_t)r * r * sizeof(float) + 15) & ~(size_t)15) + (size_t)kPolishRows * r * sizeof(double);
+}
 
 // Raises the dynamic shared-memory limit of the work-list kernels (once per
 // process; call before capturing launches into a graph).
@@ -1558,7 +1536,7 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
     case BK_GRAM:
       return run_batch(k_gram_batch, b, 256, st);
     case BK_POLISH:
-      return run_batch(k_polish_batch, b, 64, st);
+      return run_batch(k_polish_batch, b, 256, st);
     default:
       return cudaErrorInvalidValue;
   }
