@@ -129,8 +129,9 @@ cudaError_t launch_small_svd(bool fp64, const SmallPlan& pl, const double* Y, in
                              double* sigl_hist, int* status, cudaStream_t st,
                              bool basis_only = false);
 
-// One FP64 CholeskyQR step on an n x r factor computed in FP32 arithmetic
-// (U <- U R^{-1}, R^T R = U^T U); scratch: polish_scratch(n, r) bytes.
+// One CholeskyQR step (U <- U R^{-1}, R^T R = U^T U) to first order on an
+// n x r FP64 factor computed in FP32 arithmetic; scratch: polish_scratch(n, r)
+// bytes.
 size_t polish_scratch(int64_t n, int r);
 cudaError_t launch_polish(double* U, int64_t n, int r, void* scratch, int* status,
                           cudaStream_t st);
