@@ -55,6 +55,13 @@ WORKLOADS = {
                                            "p=10, q=3, precision form (a small profiling case)",
                                       shape=[512, 512, 512], r=[50, 50, 50], s=10, q=3, st=True,
                                       dtype="f32", prec=1),
+    "superdiag600slow_fp32_st_pve": dict(desc="600^3 FP32 tensor C of Section 5.1 (superdiagonal "
+                                              "core v_i = 1/i^2, Haar factors); Algorithm 4: "
+                                              "ST-HOSVD with per-mode power counts chosen by "
+                                              "the PVE test, tol=0.5, q_max=10, r=(20,20,20), "
+                                              "p=10",
+                                         shape=[600, 600, 600], r=[20, 20, 20], s=10, q=10,
+                                         st=True, dtype="f32", prec=0, pve=0.5),
     "hilbert100_fp64_t": dict(desc="100^3 FP64 Hilbert-type 1/(i+j+k-2); randomized T-HOSVD, "
                                    "r=(10,10,10), p=5, q=1", shape=[100, 100, 100],
                               r=[10, 10, 10], s=5, q=1, st=False, dtype="f64", prec=0),
@@ -95,6 +102,8 @@ def make_input(name, rank=0):
                                    decay=0.8, dtype=np.float32)
     if name.startswith("invradius"):
         return I.inverse_radius(w["shape"][0], seed=3 + 1000 * rank, noise=1e-6)
+    if name.startswith("superdiag600slow"):
+        return I.superdiagonal(w["shape"][0], "slow", seed=11 + 1000 * rank, dtype=np.float32)
     if name.startswith("hilbert100"):
         return I.hilbert(w["shape"])
     raise KeyError(name)
@@ -158,6 +167,9 @@ class Clocks:
 
 def oracle_step(A, w):
     from oracle import tucker as T
+    if w.get("pve") is not None:
+        G, Us, _, _ = T.rsthosvd_pve(A, w["r"], w["s"], w["q"], w["pve"])
+        return T.rel_error(A, G, Us)
     f = T.rsthosvd if w["st"] else T.rthosvd
     G, Us, _ = f(A, w["r"], w["s"], w["q"], bf16_power=bool(w["prec"])) if w["st"] else \
         f(A, w["r"], w["s"], w["q"])
@@ -584,8 +596,14 @@ def main():
     fn = api.tucker_rsthosvd if w["st"] else api.tucker_rthosvd
     stream = torch.cuda.current_stream()
 
+    q_chosen = []
+
     def step(X):
-        fn(X, dims, r, opts, core, U, stats=False, stream=stream)
+        if w.get("pve") is not None:
+            qs, _ = api.tucker_rsthosvd_pve(X, dims, r, opts, w["pve"], core, U, stream=stream)
+            q_chosen[:] = qs
+        else:
+            fn(X, dims, r, opts, core, U, stats=False, stream=stream)
         api.tucker_error(X, dims, core, r, U, rel, stream=stream)
 
     for _ in range(args.warmup):
@@ -738,6 +756,8 @@ def main():
                     "overlap": "step k+1's host->device copy overlaps step k's compute "
                                "(two device input buffers)"},
             "clocks": clk, "gpu_launches": prof["kernels"]}
+    if q_chosen:
+        line["config"]["pve"] = {"tol": w["pve"], "q_max": w["q"], "q_per_mode": list(q_chosen)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, w)
     print(json.dumps(line), flush=True)

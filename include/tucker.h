@@ -172,6 +172,22 @@ tk_status tucker_rthosvd(const tk_tensor* A, const int* r, const tk_opts* o, voi
 tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
                           void* const* U, tk_stats* st, void* stream);
 
+/* Algorithm 4: Algorithm 3 with the power count q_k of each mode chosen by
+ * the PVE accuracy test (Section 3.3).  After the sketch, steps
+ * t = 1..q_max (q_max = o->q, 1 <= q_max <= TK_MAX_Q) run until
+ *   max_{i <= r_k} |sigma_t(i) - sigma_{t-1}(i)| <= tol * sigma_t(r_k + 1),
+ * where sigma_t = diag(Sigma) + alpha_{t-1} after step t's svd, sigma_0 = 0,
+ * and sigma_t(r_k + 1) is the l_k-th entry when l_k = r_k; q_k = that t
+ * (q_max when the test never holds).  The shift update of Algorithm 3
+ * follows a step that does not stop.  tol >= 0 (host).  The test is taken
+ * on the host after each step, so the call synchronises `stream` once per
+ * power step.  q_out: host array of d ints, the chosen q_k (NULL = not
+ * returned).  o->prec must be TK_PREC_PLAIN.  Other arguments as
+ * tucker_rsthosvd; in st, q is q_max and the per-step entries past q_k are 0. */
+tk_status tucker_rsthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o, double tol,
+                              void* core, void* const* U, int* q_out, tk_stats* st,
+                              void* stream);
+
 /* Relative error RE = ||A - G x_1 U_1 ... x_d U_d|| / ||A|| (Section 5,
  * definition of RE).  core, U as returned by tucker_r(s)thosvd (A's dtype);
  * r: host ranks.  rel_err: one FP64 (device).  The reconstruction is never

@@ -170,6 +170,59 @@ def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power
     return G, Us, stats
 
 
+def pve_threshold_index(r_k, l):
+    """0-based index of the estimate the Algorithm 4 test scales tol by: the
+    (r_k+1)-th (the first one past the kept rank), or the last one when the
+    sketch has no column past r_k (l_k = r_k)."""
+    return min(r_k, l - 1)
+
+
+def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=None):
+    """Algorithm 4: Algorithm 3 with the power count of each mode chosen by
+    the PVE test.  Returns (G, [U_k], [q_k], stats).
+
+    Per mode k, after the sketch's svd (alpha_0 = 0, sigma_hat = 0), step
+    t = 1..q_max: q_k = t; [Q, Sigma] = svd(X_(k)(X_(k)^T Q) - alpha_{t-1} Q);
+    sigma_t = diag(Sigma) + alpha_{t-1}; stop when
+    max_{i <= r_k} |sigma_t(i) - sigma_hat(i)| <= tol * sigma_t(r_k + 1);
+    otherwise the shift update of Algorithm 3 and sigma_hat = sigma_t.
+    The stats record sigma_t per step ('sigma_hist'), the shifts and q_k.
+    """
+    G = np.asarray(A, dtype=np.float64)
+    d = G.ndim
+    s = [s] * d if np.isscalar(s) else list(s)
+    order = list(range(d)) if order is None else list(order)
+    Us, qs, stats = [None] * d, [0] * d, [None] * d
+    for k in order:
+        cols = int(np.prod([G.shape[m] for m in range(d) if m != k]))
+        l = clamp_l(r[k], s[k], G.shape[k], cols)
+        if l < r[k]:
+            raise ValueError("mode %d: only %d columns for rank %d" % (k, l, r[k]))
+        Xk = unfold(G, k)
+        Q, _ = svd_econ(sketch(G, k, l, seed, tag))
+        alpha = 0.0
+        sig_hat = np.zeros(l)
+        hist, a_hist = [], []
+        ridx = pve_threshold_index(r[k], l)
+        qk = 0
+        for t in range(1, q_max + 1):
+            qk = t
+            a_used = 0.0 if rule == SHIFT_NONE else alpha
+            Q, S = svd_econ(Xk @ (Xk.T @ Q) - a_used * Q)
+            sig_t = S + a_used
+            hist.append(sig_t)
+            if np.max(np.abs(sig_t[:r[k]] - sig_hat[:r[k]])) <= tol * sig_t[ridx]:
+                break
+            alpha = shift_update(S[-1], alpha, rule)
+            a_hist.append(alpha)
+            sig_hat = sig_t
+        Us[k] = Q[:, :r[k]]
+        qs[k] = qk
+        stats[k] = dict(l=l, q=qk, sigma_hist=hist, alpha=a_hist)
+        G = mode_product(G, Us[k].T, k)
+    return G, Us, qs, stats
+
+
 def hosvd(A, r, sequential):
     """Algorithm 1: deterministic T-HOSVD (sequential=False) or ST-HOSVD."""
     A = np.asarray(A, dtype=np.float64)

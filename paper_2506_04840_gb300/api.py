@@ -96,6 +96,10 @@ SIGNATURES = {
     "tucker_rsthosvd": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
                                 ctypes.POINTER(tk_opts), c_void_p, ctypes.POINTER(c_void_p),
                                 ctypes.POINTER(tk_stats), c_void_p]),
+    "tucker_rsthosvd_pve": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                    ctypes.POINTER(tk_opts), c_double, c_void_p,
+                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_int),
+                                    ctypes.POINTER(tk_stats), c_void_p]),
     "tucker_error": (c_int, [ctypes.POINTER(tk_tensor), c_void_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
     "tucker_to_bf16": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
@@ -266,6 +270,18 @@ def tucker_rthosvd(A, dims, r, opts, core, U, stats=False, stream=None):
 
 def tucker_rsthosvd(A, dims, r, opts, core, U, stats=False, stream=None):
     return _hosvd("tucker_rsthosvd", A, dims, r, opts, core, U, stats, stream)
+
+
+def tucker_rsthosvd_pve(A, dims, r, opts, tol, core, U, stats=False, stream=None):
+    """Algorithm 4 (opts.q = q_max).  Returns (q_k list, stats dict or None)."""
+    desc = tensor_desc(A, dims)
+    st = tk_stats() if stats else None
+    qs = (c_int * len(dims))()
+    _check(load().tucker_rsthosvd_pve(ctypes.byref(desc), _ranks(r), ctypes.byref(opts),
+                                      float(tol), _ptr(core), _ptr_array(U), qs,
+                                      ctypes.byref(st) if st is not None else None,
+                                      _stream(stream)), "tucker_rsthosvd_pve")
+    return [int(x) for x in qs], (_stats_dict(st) if st is not None else None)
 
 
 def tucker_error(A, dims, core, r, U, rel_err, stream=None):

@@ -3,6 +3,7 @@
 // only for launches: the shift alpha, Q, Sigma and Y live on the device and
 // no device-to-host copy happens inside the mode loop.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -200,9 +201,16 @@ size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
 // (Algorithm 2/3 steps for one k).  Leaves Q (n x l) and Sigma in ws.
 // shadow_ready: the bfloat16 copy of X is already in w.shadow (T-HOSVD
 // converts A once for all modes).
+// PVE control (Algorithm 4): stop the power steps when the estimates settle.
+struct PveCtl {
+  double tol = -1.0;   // < 0: run all p.q steps (Algorithms 2, 3)
+  int q_used = 0;      // out: steps run
+};
+
 static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt, View v,
                              int64_t ka, int64_t kb, uint64_t seed, uint32_t tag,
-                             const HosvdWs& w, cudaStream_t st, bool shadow_ready = false) {
+                             const HosvdWs& w, cudaStream_t st, bool shadow_ready = false,
+                             PveCtl* pve = nullptr) {
   const int l = p.l[k];
   const int lc = xb_lc(l);
   const int splits = xb_splits(xt, v, l);
@@ -232,6 +240,9 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
     TK_TRY(launch_to_bf16((const float*)X, v.P * v.n * v.S, (uint16_t*)w.shadow, st));
   }
+  std::vector<double> sig_hat(pve ? l : 0, 0.0), sig_h(pve ? l : 0);
+  double alpha_prev = 0.0;
+  if (pve) pve->q_used = p.q;
   for (int t = 1; t <= p.q; ++t) {
     const bool low = p.bf16 && t < p.q;
     // precision form: the FP32 step after the bfloat16 ones
@@ -292,6 +303,27 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
                               w.alpha, w.ahist + (size_t)k * TK_MAX_Q + (t - 1),
                               w.shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, st));
     }
+    if (pve) {
+      // Algorithm 4's test on sigma_t = diag(Sigma) + alpha_{t-1}; the svd
+      // has already applied the shift update, which only matters if the
+      // loop goes on
+      double alpha_new = 0.0;
+      TK_TRY(cudaMemcpyAsync(sig_h.data(), sig, (size_t)l * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(&alpha_new, w.alpha, sizeof(double), cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaStreamSynchronize(st));
+      const int r = p.r[k];
+      double dmax = 0.0;
+      for (int i = 0; i < l; ++i) sig_h[i] += alpha_prev;
+      for (int i = 0; i < r; ++i) dmax = std::max(dmax, std::fabs(sig_h[i] - sig_hat[i]));
+      const double thr = pve->tol * sig_h[std::min(r, l - 1)];
+      if (dmax <= thr) {
+        pve->q_used = t;
+        break;
+      }
+      alpha_prev = alpha_new;
+      sig_hat = sig_h;
+    }
   }
   return TK_OK;
 }
@@ -342,7 +374,8 @@ static SideStreams& side_streams(int d) {
 }
 
 static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
-                           void* const* U, tk_stats* stats, cudaStream_t st, bool sequential) {
+                           void* const* U, tk_stats* stats, cudaStream_t st, bool sequential,
+                           double pve_tol = -1.0, int* q_out = nullptr) {
   HosvdPlan p;
   tk_status s = make_plan(A, r, o, sequential, p);
   if (s != TK_OK) return s;
@@ -376,8 +409,12 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
         const int k = p.order[step];
         int64_t ka, kb;
         const View v = step_view(p, cur, k, &ka, &kb);
-        tk_status e = factor_mode(p, k, X, p.xt, v, ka, kb, o->seed, o->tag, w, st);
+        PveCtl pve;
+        pve.tol = pve_tol;
+        tk_status e = factor_mode(p, k, X, p.xt, v, ka, kb, o->seed, o->tag, w, st, false,
+                                  pve_tol >= 0.0 ? &pve : nullptr);
         if (e != TK_OK) return e;
+        if (q_out) q_out[k] = pve_tol >= 0.0 ? pve.q_used : p.q;
         if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, p.r[k], w.small, w.status, st));
         TK_TRY(launch_copy_matrix(w.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, st));
         void* out = (step == p.d - 1) ? core : w.g[pp];
@@ -599,6 +636,13 @@ tk_status tucker_rthosvd(const tk_tensor* A, const int* r, const tk_opts* o, voi
 tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
                           void* const* U, tk_stats* st, void* stream) {
   return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, true);
+}
+
+tk_status tucker_rsthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o, double tol,
+                              void* core, void* const* U, int* q_out, tk_stats* st,
+                              void* stream) {
+  if (!o || !(tol >= 0.0) || o->q < 1 || o->prec != TK_PREC_PLAIN) return TK_EINVAL;
+  return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, true, tol, q_out);
 }
 
 tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const void* const* U,

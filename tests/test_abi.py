@@ -115,6 +115,12 @@ def test_argument_validation_before_launch():
     assert lib.tucker_debug_omega(0, -1, 4, 4, 0, 0, ctypes.c_void_p(0x3000),
                                   None) == api.TK_EINVAL
     assert lib.tucker_to_bf16(None, 5, None, None) == api.TK_EINVAL
+    # Algorithm 4: tol >= 0, q_max >= 1, plain precision only
+    for tol, oo in ((-1.0, api.make_opts(3, 2, 5)), (0.5, api.make_opts(3, 0, 5)),
+                    (0.5, api.make_opts(3, 2, 5, prec=api.TK_PREC_BF16_POWER))):
+        assert lib.tucker_rsthosvd_pve(ctypes.byref(A), rr, ctypes.byref(oo), tol,
+                                       ctypes.c_void_p(0x3000), U, None, None,
+                                       None) == api.TK_EINVAL
     bad = _fake_tensor([10, 0, 10])
     assert lib.tucker_error(ctypes.byref(bad), ctypes.c_void_p(0x3000), rr, U,
                             ctypes.c_void_p(0x3000), None) == api.TK_EINVAL

@@ -251,3 +251,70 @@ def test_processing_order_is_respected():
     assert s1[2]["l"] == 7
     assert G1.shape == (4, 4, 4)
     assert T.rel_error(A, G1, U1) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4 (PVE-controlled power count)
+# ---------------------------------------------------------------------------
+def _pve_tensor():
+    return I.tucker_plus_noise([30, 26, 22], [5, 4, 4], 11, noise=1e-3, noise_mode="relative")
+
+
+def test_pve_limits_reduce_to_algorithm3():
+    """tol -> infinity stops after the first power step and tol = 0 never
+    stops early: Algorithm 4 is then Algorithm 3 with q = 1 and q = q_max,
+    result for result."""
+    A = _pve_tensor()
+    r, s, qmax = [4, 3, 3], 3, 4
+    for tol, q in ((1e300, 1), (0.0, qmax)):
+        G, Us, qs, _ = T.rsthosvd_pve(A, r, s, qmax, tol)
+        Gr, Ur, _ = T.rsthosvd(A, r, s, q)
+        assert qs == [q] * 3
+        assert np.array_equal(G, Gr)
+        for a, b in zip(Us, Ur):
+            assert np.array_equal(a, b)
+
+
+def test_pve_first_step_never_stops_below_unit_tol():
+    """With sigma_0 = 0 the first test compares sigma_1(1) >= sigma_1(r+1)
+    with tol * sigma_1(r+1): for tol < 1 it cannot hold, so every q_k >= 2
+    (the paper's Table of q tuples has no 1)."""
+    A = _pve_tensor()
+    for tol in (0.5, 0.1, 0.01):
+        _, _, qs, _ = T.rsthosvd_pve(A, [4, 3, 3], 3, 10, tol)
+        assert min(qs) >= 2, (tol, qs)
+
+
+def test_pve_count_grows_as_tol_shrinks_and_error_follows_algorithm3():
+    """A smaller tol never stops earlier on this tensor, and the result is
+    Algorithm 3's with the chosen per-mode counts (run mode by mode)."""
+    A = _pve_tensor()
+    r, s = [4, 3, 3], 3
+    prev = None
+    for tol in (0.5, 0.05, 0.005):
+        G, Us, qs, st = T.rsthosvd_pve(A, r, s, 12, tol)
+        if prev is not None:
+            assert all(a >= b for a, b in zip(qs, prev)), (qs, prev)
+        prev = qs
+        # same factors as Algorithm 3 applied with q_k on each mode
+        Gm = np.asarray(A, dtype=np.float64)
+        for k in range(3):
+            Gk, Uk, _ = T.rsthosvd(Gm, r, s, qs[k], order=[k, (k + 1) % 3, (k + 2) % 3])
+            assert np.array_equal(Uk[k], Us[k]), (tol, k)
+            Gm = T.mode_product(Gm, Us[k].T, k)
+        assert np.array_equal(Gm, G)
+
+
+@pytest.mark.parametrize("decay,r", [("slow", 10), ("fast", 10), ("sshape", 32)])
+def test_pve_half_tol_reaches_the_tensor_C_optimum(decay, r):
+    """Section 5.6: tol = 0.5 is enough for a quasi-optimal result.  On tensor
+    C the optimum has the closed form sqrt(sum_{i>r} v_i^2 / sum v_i^2); the
+    PVE-controlled counts land within 1% of it and each take at least two
+    steps (the first test cannot pass for tol < 1)."""
+    n = 60
+    A = I.superdiagonal(n, decay, seed=14)
+    opt = _closed_form(I.superdiagonal_values(n, decay), r)
+    G, Us, qs, _ = T.rsthosvd_pve(A, [r] * 3, 10, 10, 0.5)
+    re = T.rel_error(A, G, Us)
+    assert opt * (1 - 1e-9) <= re <= opt * 1.01, (re, opt, qs)
+    assert all(2 <= q <= 10 for q in qs), qs
