@@ -25,6 +25,22 @@ numpy) and the CUDA kernels implement it independently:
   ln, cos and sin are evaluated in FP32 by the fixed sequences of correctly
   rounded +, -, *, /, sqrt below (Taylor series of atanh, sin and cos with
   exact octant reduction), so that both implementations agree bit for bit.
+
+Structured test matrices (Section 5.5 compares them with the Gaussian one;
+the remark after Algorithm 3 names the Khatri-Rao products):
+
+* Uniform: entries i.i.d. on [-1, 1].  Entry (j, c) takes word c mod 4 of
+  the same counter as the Gaussian entry and maps it to
+  u = (2*(w >> 8) + 1 - 2^24) * 2^-24, an odd multiple of 2^-24 in (-1, 1)
+  (exact in FP32).
+* Khatri-Rao (KR-Gaussian, KR-uniform): Omega_k is the Khatri-Rao product
+  (column-wise Kronecker product) of one factor per mode m != k, each
+  n_m x l with n_m the current size of mode m, ordered so that the row
+  index of Omega_k is the unfolding's column index (lowest mode fastest):
+  Omega_k(j, c) = prod_{m != k} F_m(i_m(j), c).  Entry (i, c) of F_m comes
+  from the counter (i, 2^31 | m, c >> 2, (k & 0xff) | (tag << 8)) -- the
+  second word keeps these draws apart from the dense ones -- then
+  Box-Muller as above (KR-Gaussian) or the uniform map (KR-uniform).
 """
 import numpy as np
 
@@ -179,3 +195,79 @@ def omega_rows(k, row0, rows, l, seed=0, tag=0):
         out[:, 4 * g + 2] = zc
         out[:, 4 * g + 3] = zd
     return out[:, :l]
+
+
+OMEGA_GAUSS = "gauss"
+OMEGA_UNIFORM = "uniform"
+OMEGA_KR_GAUSS = "kr_gauss"
+OMEGA_KR_UNIFORM = "kr_uniform"
+OMEGA_KINDS = (OMEGA_GAUSS, OMEGA_UNIFORM, OMEGA_KR_GAUSS, OMEGA_KR_UNIFORM)
+
+
+def uniform_from_word(w):
+    """u = (2*(w >> 8) + 1 - 2^24) * 2^-24 in (-1, 1), FP32 (exact)."""
+    m = (np.asarray(w, dtype=np.uint32) >> np.uint32(8)).astype(np.int64)
+    return ((2 * m + 1 - (1 << 24)).astype(np.float64) * 2.0 ** -24).astype(np.float32)
+
+
+def uniform_rows(k, row0, rows, l, seed=0, tag=0):
+    """Rows [row0, row0+rows) of the dense uniform Omega_k, shape (rows, l), FP32."""
+    if rows <= 0 or l <= 0:
+        return np.zeros((max(rows, 0), max(l, 0)), dtype=np.float32)
+    j = np.arange(row0, row0 + rows, dtype=np.uint64)
+    groups = (l + 3) // 4
+    out = np.empty((rows, groups * 4), dtype=np.float32)
+    c3 = np.uint64((int(k) & 0xFF) | (int(tag) << 8))
+    for g in range(groups):
+        ws = philox4x32_10(j & _MASK32, j >> np.uint64(32), np.uint64(g), c3, seed)
+        for e in range(4):
+            out[:, 4 * g + e] = uniform_from_word(ws[e])
+    return out[:, :l]
+
+
+def kr_factor(k, m, n_m, l, gaussian, seed=0, tag=0):
+    """Factor F_m (n_m x l, FP32) of mode k's Khatri-Rao test matrix."""
+    if n_m <= 0 or l <= 0:
+        return np.zeros((max(n_m, 0), max(l, 0)), dtype=np.float32)
+    i = np.arange(n_m, dtype=np.uint64)
+    groups = (l + 3) // 4
+    out = np.empty((n_m, groups * 4), dtype=np.float32)
+    c1 = np.uint64((1 << 31) | int(m))
+    c3 = np.uint64((int(k) & 0xFF) | (int(tag) << 8))
+    for g in range(groups):
+        w0, w1, w2, w3 = philox4x32_10(i, c1, np.uint64(g), c3, seed)
+        if gaussian:
+            out[:, 4 * g + 0], out[:, 4 * g + 1] = box_muller(w0, w1)
+            out[:, 4 * g + 2], out[:, 4 * g + 3] = box_muller(w2, w3)
+        else:
+            for e, w in enumerate((w0, w1, w2, w3)):
+                out[:, 4 * g + e] = uniform_from_word(w)
+    return out[:, :l]
+
+
+def omega_matrix(kind, shape, k, l, seed=0, tag=0):
+    """Omega_k (prod_{m != k} shape[m] x l) of the given kind, in FP64.
+
+    The Khatri-Rao kinds are formed by the definition: scipy's khatri_rao
+    (column-wise Kronecker product, the second operand's row index fastest)
+    applied to the factors from the highest mode down to the lowest.
+    """
+    d = len(shape)
+    cols = int(np.prod([shape[m] for m in range(d) if m != k]))
+    if kind == OMEGA_GAUSS:
+        return omega_rows(k, 0, cols, l, seed=seed, tag=tag).astype(np.float64)
+    if kind == OMEGA_UNIFORM:
+        return uniform_rows(k, 0, cols, l, seed=seed, tag=tag).astype(np.float64)
+    if kind not in (OMEGA_KR_GAUSS, OMEGA_KR_UNIFORM):
+        raise ValueError(kind)
+    from scipy.linalg import khatri_rao
+    gaussian = kind == OMEGA_KR_GAUSS
+    Om = None
+    for m in range(d):
+        if m == k:
+            continue
+        F = kr_factor(k, m, int(shape[m]), l, gaussian, seed=seed, tag=tag).astype(np.float64)
+        Om = F if Om is None else khatri_rao(F, Om)
+    if Om is None:      # order-1 tensor: one column index
+        Om = np.ones((1, l))
+    return Om

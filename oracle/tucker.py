@@ -18,7 +18,7 @@ Conventions (the paper is silent on them; the library uses the same ones):
 """
 import numpy as np
 
-from .omega import omega_rows
+from .omega import OMEGA_GAUSS, omega_matrix
 
 SHIFT_PAPER = "paper"   # adaptive midpoint shift, Algorithms 2 and 3
 SHIFT_NONE = "none"     # alpha = 0 throughout: Algorithm A.1
@@ -63,15 +63,11 @@ def clamp_l(r_k, s_k, n_k, ncols):
     return int(min(r_k + s_k, n_k, ncols))
 
 
-def omega(k, ncols, l, seed, tag):
-    """Omega_k (ncols x l) promoted to FP64."""
-    return omega_rows(k, 0, ncols, l, seed=seed, tag=tag).astype(np.float64)
-
-
-def sketch(X, k, l, seed=0, tag=0):
-    """Y = X_(k) Omega_k (Algorithm 2/3, first svd argument)."""
-    Xk = unfold(np.asarray(X, dtype=np.float64), k)
-    return Xk @ omega(k, Xk.shape[1], l, seed, tag)
+def sketch(X, k, l, seed=0, tag=0, kind=OMEGA_GAUSS):
+    """Y = X_(k) Omega_k (Algorithm 2/3, first svd argument); Omega_k of the
+    given kind (Section 5.5) for the current sizes of X."""
+    X = np.asarray(X, dtype=np.float64)
+    return unfold(X, k) @ omega_matrix(kind, X.shape, k, l, seed, tag)
 
 
 def shift_update(sigma_l, alpha_prev, rule=SHIFT_PAPER):
@@ -106,13 +102,13 @@ def shifted_power(X, k, Q, alpha, q, rule=SHIFT_PAPER, X_for_step=None):
     return Q, S, alpha, a_hist, s_hist
 
 
-def _mode_factor(X, k, r_k, s_k, q, seed, tag, rule, X_for_step=None):
+def _mode_factor(X, k, r_k, s_k, q, seed, tag, rule, X_for_step=None, kind=OMEGA_GAUSS):
     """Steps of Algorithms 2/3 for one mode: sketch, q shifted powers, U_k."""
     Xk_cols = int(np.prod([X.shape[m] for m in range(X.ndim) if m != k]))
     l = clamp_l(r_k, s_k, X.shape[k], Xk_cols)
     if l < r_k:
         raise ValueError("mode %d: only %d columns for rank %d" % (k, l, r_k))
-    Y = sketch(X, k, l, seed, tag)
+    Y = sketch(X, k, l, seed, tag, kind)
     Q, S = svd_econ(Y)
     if X_for_step is None or q < 2:
         Q, S2, alpha, a_hist, s_hist = shifted_power(X, k, Q, 0.0, q, rule)
@@ -129,22 +125,24 @@ def _mode_factor(X, k, r_k, s_k, q, seed, tag, rule, X_for_step=None):
     return Q[:, :r_k], dict(l=l, alpha=a_hist, sigma_l=s_hist, sigma=S)
 
 
-def rthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER):
-    """Algorithm 2: shifted randomized T-HOSVD.  Returns (G, [U_k], stats)."""
+def rthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, omega=OMEGA_GAUSS):
+    """Algorithm 2: shifted randomized T-HOSVD.  Returns (G, [U_k], stats).
+    ``omega``: the test matrix kind (oracle.omega.OMEGA_KINDS)."""
     A = np.asarray(A, dtype=np.float64)
     d = A.ndim
     s = [s] * d if np.isscalar(s) else list(s)
     Us, stats = [], []
     G = A
     for k in range(d):
-        U, st = _mode_factor(A, k, r[k], s[k], q, seed, tag, rule)
+        U, st = _mode_factor(A, k, r[k], s[k], q, seed, tag, rule, kind=omega)
         Us.append(U)
         stats.append(st)
         G = mode_product(G, U.T, k)
     return G, Us, stats
 
 
-def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power=False):
+def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power=False,
+             omega=OMEGA_GAUSS):
     """Algorithm 3: shifted randomized ST-HOSVD.  Returns (G, [U_k], stats).
 
     ``order`` is a permutation of the modes (Section 2: any processing order).
@@ -163,7 +161,7 @@ def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power
         if bf16_power:
             Gb = round_bf16(G)
             X_for_step = (lambda t, Gb=Gb, Gf=G: Gb if t < q else Gf)
-        U, st = _mode_factor(G, k, r[k], s[k], q, seed, tag, rule, X_for_step)
+        U, st = _mode_factor(G, k, r[k], s[k], q, seed, tag, rule, X_for_step, kind=omega)
         Us[k] = U
         stats[k] = st
         G = mode_product(G, U.T, k)
@@ -177,7 +175,8 @@ def pve_threshold_index(r_k, l):
     return min(r_k, l - 1)
 
 
-def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=None):
+def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=None,
+                 omega=OMEGA_GAUSS):
     """Algorithm 4: Algorithm 3 with the power count of each mode chosen by
     the PVE test.  Returns (G, [U_k], [q_k], stats).
 
@@ -199,7 +198,7 @@ def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=Non
         if l < r[k]:
             raise ValueError("mode %d: only %d columns for rank %d" % (k, l, r[k]))
         Xk = unfold(G, k)
-        Q, _ = svd_econ(sketch(G, k, l, seed, tag))
+        Q, _ = svd_econ(sketch(G, k, l, seed, tag, omega))
         alpha = 0.0
         sig_hat = np.zeros(l)
         hist, a_hist = [], []

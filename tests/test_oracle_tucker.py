@@ -318,3 +318,22 @@ def test_pve_half_tol_reaches_the_tensor_C_optimum(decay, r):
     re = T.rel_error(A, G, Us)
     assert opt * (1 - 1e-9) <= re <= opt * 1.01, (re, opt, qs)
     assert all(2 <= q <= 10 for q in qs), qs
+
+
+@pytest.mark.parametrize("kind", ["uniform", "kr_gauss", "kr_uniform"])
+@pytest.mark.parametrize("st", [False, True])
+def test_structured_test_matrices_reach_the_tensor_C_optimum(kind, st):
+    """Section 5.5: with s = 10 and q = 1 the uniform and Khatri-Rao test
+    matrices give errors comparable to the Gaussian one.  On tensor C (slow
+    and fast decay) every kind lands within 2% of the closed-form optimum
+    and within 1.5% of the Gaussian sketch's error."""
+    n, r = 60, 10
+    f = T.rsthosvd if st else T.rthosvd
+    for decay in ("slow", "fast"):
+        A = I.superdiagonal(n, decay, seed=21)
+        opt = _closed_form(I.superdiagonal_values(n, decay), r)
+        re_g = T.rel_error(A, *f(A, [r] * 3, 10, 1)[:2])
+        G, Us, _ = f(A, [r] * 3, 10, 1, omega=kind)
+        re = T.rel_error(A, G, Us)
+        assert opt * (1 - 1e-9) <= re <= 1.02 * opt, (kind, decay, re, opt)
+        assert re <= 1.015 * re_g, (kind, decay, re, re_g)
