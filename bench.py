@@ -43,6 +43,10 @@ WORKLOADS = {
                                    "randomized ST-HOSVD, adaptive shifts, r=(20,20,20), p=10, q=2",
                               shape=[400, 400, 400], r=[20, 20, 20], s=10, q=2, st=True,
                               dtype="f32", prec=0),
+    "tucker400_fp32_st_krgauss": dict(desc="as tucker400_fp32_st with a Khatri-Rao product of "
+                                           "Gaussian factors as Omega_k (Section 5.5)",
+                                      shape=[400, 400, 400], r=[20, 20, 20], s=10, q=2,
+                                      st=True, dtype="f32", prec=0, omega=2),
     "invradius1000_fp32_st": dict(desc="1000^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise; randomized "
                                        "ST-HOSVD, r=(50,50,50), p=10, q=3, plain FP32",
                                   shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3, st=True,
@@ -170,9 +174,11 @@ def oracle_step(A, w):
     if w.get("pve") is not None:
         G, Us, _, _ = T.rsthosvd_pve(A, w["r"], w["s"], w["q"], w["pve"])
         return T.rel_error(A, G, Us)
+    from oracle import omega as om
+    kind = om.OMEGA_KINDS[w.get("omega", 0)]
     f = T.rsthosvd if w["st"] else T.rthosvd
-    G, Us, _ = f(A, w["r"], w["s"], w["q"], bf16_power=bool(w["prec"])) if w["st"] else \
-        f(A, w["r"], w["s"], w["q"])
+    G, Us, _ = f(A, w["r"], w["s"], w["q"], bf16_power=bool(w["prec"]), omega=kind) \
+        if w["st"] else f(A, w["r"], w["s"], w["q"], omega=kind)
     return T.rel_error(A, G, Us)
 
 
@@ -589,10 +595,11 @@ def main():
     core = torch.empty(int(np.prod(r)), dtype=tdt, device="cuda")
     U = [torch.empty(dims[k] * r[k], dtype=tdt, device="cuda") for k in range(d)]
     rel = torch.zeros(1, dtype=torch.float64, device="cuda")
-    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"])
+    kind = w.get("omega", api.TK_OMEGA_GAUSS)
+    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], omega=kind)
     nbytes = api.tucker_workspace_size(Ad, dims, r, opts, 1 if w["st"] else 0)
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], workspace=ws)
+    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], workspace=ws, omega=kind)
     fn = api.tucker_rsthosvd if w["st"] else api.tucker_rthosvd
     stream = torch.cuda.current_stream()
 

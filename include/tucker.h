@@ -73,6 +73,31 @@ typedef enum { TK_SHIFT_PAPER = 0, TK_SHIFT_NONE = 1 } tk_shift;
  * the sketch, power step q, the TTM shrink and the core read FP32. */
 typedef enum { TK_PREC_PLAIN = 0, TK_PREC_BF16_POWER = 1 } tk_precision;
 
+/* Test matrix Omega_k of the sketch (Section 5.5 compares these four; the
+ * remark after Algorithm 3 motivates the structured ones).
+ * TK_OMEGA_GAUSS: i.i.d. N(0,1), generated inside the sketch pass, never
+ *   stored (the draw defined above).
+ * TK_OMEGA_UNIFORM: i.i.d. uniform on [-1, 1]; entry (j, c) maps word
+ *   c mod 4 of the Gaussian entry's Philox counter to
+ *   u = (2*(w >> 8) + 1 - 2^24) * 2^-24 (exact in FP32).
+ * TK_OMEGA_KR_GAUSS, TK_OMEGA_KR_UNIFORM: the Khatri-Rao product of one
+ *   factor F_m (n_m x l, n_m the current size of mode m) per mode m != k,
+ *   Omega_k(j, c) = prod_{m != k} F_m(i_m(j), c) with (i_m) the unfolding's
+ *   column j (lowest mode fastest), multiplied in FP64 in ascending m and
+ *   rounded once to the sketch's accumulation type (FP32 or FP64).
+ *   F_m(i, c) comes from the counter (i, 2^31 | m, c >> 2,
+ *   (k & 0xff) | (tag << 8)), then Box-Muller (pairs of words, as above) or
+ *   the uniform map.
+ * The three structured kinds are written into the W buffer of the power
+ * steps (prod_{m != k} n_m x l_k in the accumulation type) and the sketch
+ * reads them there. */
+typedef enum {
+  TK_OMEGA_GAUSS = 0,
+  TK_OMEGA_UNIFORM = 1,
+  TK_OMEGA_KR_GAUSS = 2,
+  TK_OMEGA_KR_UNIFORM = 3
+} tk_omega;
+
 /* A dense tensor.  data: device pointer, column-major, dtype F64 or F32
  * (BF16 only where stated). */
 typedef struct {
@@ -96,6 +121,7 @@ typedef struct {
   void* workspace;         /* device workspace or NULL (then the call
                               allocates and frees it on `stream`) */
   size_t workspace_bytes;
+  tk_omega omega;          /* test matrix kind (0 = Gaussian) */
 } tk_opts;
 
 /* Per-call statistics (HOST memory; filling it synchronises the stream). */
@@ -121,6 +147,14 @@ size_t tucker_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o,
  * FP32 matrix `out` (device).  k: 0-based mode; tag < 2^24. */
 tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed,
                              uint32_t tag, float* out, void* stream);
+
+/* Omega_k of any kind (tk_omega) for a tensor of order d and sizes n, in the
+ * unfolding's own row order, written as a (prod_{m != k} n_m) x l
+ * column-major FP32 matrix `out` (device).  Returns TK_EINVAL for a bad
+ * kind, k, l (1..TK_MAX_L), sizes or tag; the Khatri-Rao kinds allocate
+ * their factor scratch on `stream`. */
+tk_status tucker_debug_omega_matrix(tk_omega kind, int d, const int64_t* n, int k, int l,
+                                    uint64_t seed, uint32_t tag, float* out, void* stream);
 
 /* Sketch Y = A_(k) Omega_k (Algorithm 2: svd argument before the power
  * loop; Algorithm 3 with the current tensor G).  A: F64, F32 or BF16.

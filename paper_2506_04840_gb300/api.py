@@ -22,6 +22,7 @@ TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_EBREAKDOWN, TK_ETIMEOUT, TK_ENOTIMPL, 
 TK_F64, TK_F32, TK_BF16 = 0, 1, 2
 TK_SHIFT_PAPER, TK_SHIFT_NONE = 0, 1
 TK_PREC_PLAIN, TK_PREC_BF16_POWER = 0, 1
+TK_OMEGA_GAUSS, TK_OMEGA_UNIFORM, TK_OMEGA_KR_GAUSS, TK_OMEGA_KR_UNIFORM = 0, 1, 2, 3
 
 c_int, c_int64, c_uint64, c_uint32, c_double = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                                  ctypes.c_uint32, ctypes.c_double)
@@ -35,7 +36,7 @@ class tk_tensor(ctypes.Structure):
 class tk_opts(ctypes.Structure):
     _fields_ = [("q", c_int), ("s", c_int * TK_MAX_D), ("seed", c_uint64), ("tag", c_uint32),
                 ("shift", c_int), ("prec", c_int), ("order", c_int * TK_MAX_D),
-                ("workspace", c_void_p), ("workspace_bytes", c_size_t)]
+                ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("omega", c_int)]
 
 
 class tk_stats(ctypes.Structure):
@@ -84,6 +85,8 @@ SIGNATURES = {
     "tucker_status_string": (ctypes.c_char_p, [c_int]),
     "tucker_workspace_size": (c_size_t, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
                                          ctypes.POINTER(tk_opts), c_int]),
+    "tucker_debug_omega_matrix": (c_int, [c_int, c_int, ctypes.POINTER(c_int64), c_int, c_int,
+                                          c_uint64, c_uint32, c_void_p, c_void_p]),
     "tucker_debug_omega": (c_int, [c_int, c_int64, c_int64, c_int, c_uint64, c_uint32, c_void_p,
                                    c_void_p]),
     "tucker_sketch": (c_int, [ctypes.POINTER(tk_tensor), c_int, c_int, c_uint64, c_uint32,
@@ -185,7 +188,7 @@ def tensor_desc(data, dims, dtype=None):
 
 
 def make_opts(d, q, s, seed=0, tag=0, shift=TK_SHIFT_PAPER, prec=TK_PREC_PLAIN, order=None,
-              workspace=None):
+              workspace=None, omega=TK_OMEGA_GAUSS):
     o = tk_opts()
     o.q = int(q)
     svals = [s] * d if np.isscalar(s) else list(s)
@@ -195,6 +198,7 @@ def make_opts(d, q, s, seed=0, tag=0, shift=TK_SHIFT_PAPER, prec=TK_PREC_PLAIN, 
     o.tag = int(tag)
     o.shift = int(shift)
     o.prec = int(prec)
+    o.omega = int(omega)
     if order is None:
         o.order[0] = -1
     else:
@@ -233,6 +237,12 @@ def tucker_workspace_size(A, dims, r, opts, st):
 def tucker_debug_omega(k, row0, rows, l, seed, tag, out, stream=None):
     _check(load().tucker_debug_omega(k, row0, rows, l, seed, tag, _ptr(out), _stream(stream)),
            "tucker_debug_omega")
+
+
+def tucker_debug_omega_matrix(kind, dims, k, l, seed, tag, out, stream=None):
+    n = (c_int64 * len(dims))(*[int(x) for x in dims])
+    _check(load().tucker_debug_omega_matrix(int(kind), len(dims), n, k, l, seed, tag, _ptr(out),
+                                            _stream(stream)), "tucker_debug_omega_matrix")
 
 
 def tucker_sketch(A, dims, k, l, seed, tag, Y, stream=None):

@@ -1,5 +1,7 @@
 // Small elementwise kernels: Omega tiles for inspection, the bfloat16
 // shadow of the precision form, factor/core copies with type conversion.
+#include <algorithm>
+
 #include "tk_common.cuh"
 #include "tk_batch.h"
 #include "tk_internal.h"
@@ -27,6 +29,166 @@ cudaError_t launch_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed
   if (tot <= 0) return cudaSuccess;
   count_kernels(1);
   k_omega<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k, row0, rows, l, seed, tag, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Structured test matrices (Section 5.5): dense uniform and Khatri-Rao
+// products, written out into the sketch's W buffer.
+// ---------------------------------------------------------------------------
+
+// u = (2 (w >> 8) + 1 - 2^24) 2^-24: an odd multiple of 2^-24 in (-1, 1); the
+// integer is below 2^24 in magnitude, so both conversions are exact.
+__device__ __forceinline__ float uniform_word(uint32_t w) {
+  const int32_t num = (int32_t)(2u * (w >> 8) + 1u) - (1 << 24);
+  return __int2float_rn(num) * 0x1p-24f;
+}
+
+__device__ __forceinline__ void uniform4(uint64_t j, int g, int k, uint32_t tag, uint64_t seed,
+                                         float out[4]) {
+  const uint4 ctr = make_uint4((uint32_t)j, (uint32_t)(j >> 32), (uint32_t)g,
+                               ((uint32_t)k & 0xFFu) | (tag << 8));
+  const uint4 w = philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+  out[0] = uniform_word(w.x);
+  out[1] = uniform_word(w.y);
+  out[2] = uniform_word(w.z);
+  out[3] = uniform_word(w.w);
+}
+
+// Khatri-Rao factors of mode k: factor f (mode geo.mode[f]) is written as
+// geo.size[f] rows of lp floats (row i at kr + geo.off[f] + i lp).
+__global__ void k_kr_factors(OmegaGeom geo, int k, int lp, bool gauss, uint64_t seed,
+                             uint32_t tag, float* __restrict__ kr) {
+  const int64_t tot = geo.off[geo.nf] / 4;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int f = 0;
+    while (f + 1 < geo.nf && 4 * idx >= geo.off[f + 1]) ++f;
+    const int64_t e = 4 * idx - geo.off[f];
+    const int64_t i = e / lp;
+    const int g = (int)((e % lp) / 4);
+    const uint4 ctr = make_uint4((uint32_t)i, 0x80000000u | (uint32_t)geo.mode[f], (uint32_t)g,
+                                 ((uint32_t)k & 0xFFu) | (tag << 8));
+    const uint4 w = philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+    float v[4];
+    if (gauss) {
+      box_muller(w.x, w.y, v[0], v[1]);
+      box_muller(w.z, w.w, v[2], v[3]);
+    } else {
+      v[0] = uniform_word(w.x);
+      v[1] = uniform_word(w.y);
+      v[2] = uniform_word(w.z);
+      v[3] = uniform_word(w.w);
+    }
+    *reinterpret_cast<float4*>(kr + 4 * idx) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// out(j, c) = Omega_k(jk, c) for the layout's column j, jk = j / ka + kb (j % ka)
+// its row of Omega_k; four columns per thread.  P >= 1: the W layout of the
+// products, (j, c) at j % P + P (c + l (j / P)); P = 0: column-major
+// (cols x l).  Threads run over the four-column groups first when P = 1 and
+// over j first otherwise, so that neighbouring threads write neighbouring
+// addresses.
+template <typename T>
+__global__ void k_omega_fill(int kind, int k, int64_t cols, int l, int64_t ka, int64_t kb,
+                             OmegaGeom geo, int lp, const float* __restrict__ kr,
+                             uint64_t seed, uint32_t tag, T* __restrict__ out, int64_t P) {
+  const int groups = (l + 3) / 4;
+  const int64_t tot = cols * groups;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = P == 1 ? idx / groups : idx % cols;
+    const int g = (int)(P == 1 ? idx % groups : idx / cols);
+    const uint64_t jk = (uint64_t)(j / ka + kb * (j % ka));
+    // the Khatri-Rao product is taken in FP64, factor by factor in ascending
+    // mode order, and rounded once to the output type (exact for two
+    // factors)
+    double v[4] = {1.0, 1.0, 1.0, 1.0};
+    if (kind == TK_OMEGA_UNIFORM || kind == TK_OMEGA_GAUSS) {
+      float u[4];
+      if (kind == TK_OMEGA_UNIFORM)
+        uniform4(jk, g, k, tag, seed, u);
+      else
+        omega4(jk, g, k, tag, seed, u);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (double)u[e];
+    } else {
+      uint64_t rest = jk;
+      for (int f = 0; f < geo.nf; ++f) {
+        const uint64_t sz = (uint64_t)geo.size[f];
+        const uint64_t i = rest % sz;
+        rest /= sz;
+        const float4 t = __ldg(reinterpret_cast<const float4*>(kr + geo.off[f] + i * lp) + g);
+        if (f == 0) {
+          v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+          v[0] = __dmul_rn(v[0], (double)t.x);
+          v[1] = __dmul_rn(v[1], (double)t.y);
+          v[2] = __dmul_rn(v[2], (double)t.z);
+          v[3] = __dmul_rn(v[3], (double)t.w);
+        }
+      }
+    }
+    const int64_t base = P == 0 ? j : (j % P) + P * l * (j / P);
+    const int64_t cs = P == 0 ? cols : P;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * g + e < l) out[base + (int64_t)(4 * g + e) * cs] = (T)v[e];
+  }
+}
+
+OmegaGeom omega_geom(const int64_t* dims, int d, int k, int l) {
+  OmegaGeom geo{};
+  const int lp = (l + 3) / 4 * 4;
+  geo.off[0] = 0;
+  for (int m = 0; m < d; ++m) {
+    if (m == k) continue;
+    geo.mode[geo.nf] = m;
+    geo.size[geo.nf] = dims[m];
+    geo.off[geo.nf + 1] = geo.off[geo.nf] + dims[m] * lp;
+    ++geo.nf;
+  }
+  return geo;
+}
+
+size_t omega_scratch(int kind, const int64_t* dims, int d, int k, int l) {
+  if (kind != TK_OMEGA_KR_GAUSS && kind != TK_OMEGA_KR_UNIFORM) return 0;
+  const OmegaGeom geo = omega_geom(dims, d, k, l);
+  return (size_t)geo.off[geo.nf] * sizeof(float);
+}
+
+cudaError_t launch_omega_fill(int kind, const int64_t* dims, int d, int k, int l, uint64_t seed,
+                              uint32_t tag, int64_t ka, int64_t kb, float* kr, void* out,
+                              bool f64, int64_t P, cudaStream_t st) {
+  const OmegaGeom geo = omega_geom(dims, d, k, l);
+  int64_t cols = 1;
+  for (int f = 0; f < geo.nf; ++f) cols *= geo.size[f];
+  if (cols <= 0 || l <= 0) return cudaSuccess;
+  if (ka <= 0) {
+    ka = cols;
+    kb = 1;
+  }
+  const int lp = (l + 3) / 4 * 4;
+  const int blocks_cap = 8 * num_sms();
+  if (kind == TK_OMEGA_KR_GAUSS || kind == TK_OMEGA_KR_UNIFORM) {
+    if (kr == nullptr) return cudaErrorInvalidValue;
+    const int64_t tot = geo.off[geo.nf] / 4;
+    if (tot > 0) {
+      count_kernels(1);
+      k_kr_factors<<<(unsigned)std::min<int64_t>((tot + 255) / 256, blocks_cap), 256, 0, st>>>(
+          geo, k, lp, kind == TK_OMEGA_KR_GAUSS, seed, tag, kr);
+    }
+  }
+  const int64_t tot = cols * ((l + 3) / 4);
+  const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4 * blocks_cap);
+  count_kernels(1);
+  if (f64)
+    k_omega_fill<double><<<blocks, 256, 0, st>>>(kind, k, cols, l, ka, kb, geo, lp, kr, seed, tag,
+                                                 (double*)out, P);
+  else
+    k_omega_fill<float><<<blocks, 256, 0, st>>>(kind, k, cols, l, ka, kb, geo, lp, kr, seed, tag,
+                                                (float*)out, P);
   return cudaGetLastError();
 }
 

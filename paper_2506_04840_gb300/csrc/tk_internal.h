@@ -149,6 +149,26 @@ cudaError_t launch_ritz_rotate(float* W, int64_t cols, int64_t P, int l, void* s
 cudaError_t launch_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed, uint32_t tag,
                          float* out, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* x, int64_t count, uint16_t* out, cudaStream_t st);
+// Structured test matrices (tk_omega): the modes m != k of a tensor with
+// sizes dims, in ascending order, with their sizes and the offsets (floats)
+// of their Khatri-Rao factors in the scratch (rows padded to l rounded up
+// to 4).
+struct OmegaGeom {
+  int nf;
+  int mode[TK_MAX_D];
+  int64_t size[TK_MAX_D];
+  int64_t off[TK_MAX_D + 1];
+};
+OmegaGeom omega_geom(const int64_t* dims, int d, int k, int l);
+// Scratch bytes launch_omega_fill needs for kind (0 for the dense kinds).
+size_t omega_scratch(int kind, const int64_t* dims, int d, int k, int l);
+// Writes Omega_k of the given kind for the unfolding's columns in the
+// layout's order (jk = j / ka + kb (j % ka); ka <= 0: the natural order):
+// P >= 1 the (P, l, S) W layout of the products, P = 0 column-major; FP64
+// (f64) or FP32 values.  kr: omega_scratch bytes (Khatri-Rao kinds).
+cudaError_t launch_omega_fill(int kind, const int64_t* dims, int d, int k, int l, uint64_t seed,
+                              uint32_t tag, int64_t ka, int64_t kb, float* kr, void* out,
+                              bool f64, int64_t P, cudaStream_t st);
 // dst (rows x cols, ld_dst) = src (FP64, ld_src) converted to dtype.
 cudaError_t launch_copy_matrix(const double* src, int64_t ld_src, void* dst, int64_t ld_dst,
                                int64_t rows, int64_t cols, XType dt, cudaStream_t st);

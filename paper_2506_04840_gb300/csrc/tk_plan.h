@@ -86,12 +86,14 @@ struct HosvdPlan {
   int q = 0;
   bool bf16 = false;
   tk_shift rule = TK_SHIFT_PAPER;
+  int omega = TK_OMEGA_GAUSS;   // test matrix kind (tk_omega)
   // rot (ST-HOSVD, FP32, modes in natural order): every TTM writes its output
   // with the contracted mode moved last, so each step sees its mode first
   // (a mode-major view) and the core comes out in natural order.
   bool rot = false;
   // sizes (bytes)
   size_t gbuf = 0, shadow = 0, wbuf = 0, part = 0, ymat = 0, small = 0, qd = 0;
+  size_t kr = 0;   // Khatri-Rao factor scratch
   std::vector<SmallPlan> sp;
   std::vector<std::vector<int64_t>> dims_at;  // tensor dims seen by each step
 };
@@ -133,6 +135,7 @@ struct HosvdWs {
   double* shist;
   double* sig;
   int* status;
+  float* kr;
 };
 
 tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st, HosvdPlan& p);

@@ -91,6 +91,8 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
   if (o->shift != TK_SHIFT_PAPER && o->shift != TK_SHIFT_NONE) return TK_EINVAL;
   if (o->prec != TK_PREC_PLAIN && o->prec != TK_PREC_BF16_POWER) return TK_EINVAL;
   if (p.bf16 && A->dtype != TK_F32) return TK_EINVAL;
+  if (o->omega < TK_OMEGA_GAUSS || o->omega > TK_OMEGA_KR_UNIFORM) return TK_EINVAL;
+  p.omega = o->omega;
   for (int k = 0; k < p.d; ++k) {
     if (p.r[k] < 1 || p.r[k] >= p.n[k]) return TK_EINVAL;   // Problem 2.1: r_k < n_k
     if (p.s[k] < 0) return TK_EINVAL;
@@ -139,7 +141,10 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
       p.part = std::max(p.part, xtb32_scratch(v, (int)lk));
       p.part = std::max(p.part, xtb32_scratch(v, p.r[k]));
     }
-    if (p.q > 0) p.wbuf = std::max(p.wbuf, (size_t)cols * lk * ta);
+    // W holds the power steps' X^T Q, and Omega_k when it is not generated
+    // inside the sketch pass
+    if (p.q > 0 || p.omega != TK_OMEGA_GAUSS) p.wbuf = std::max(p.wbuf, (size_t)cols * lk * ta);
+    p.kr = std::max(p.kr, omega_scratch(p.omega, cur.data(), p.d, k, (int)lk));
     p.ymat = std::max(p.ymat, (size_t)v.n * lk * sizeof(double));
     if (p.bf16 && p.q >= 2) {
       p.shadow = std::max(p.shadow, (size_t)prod(cur) * 2);
@@ -192,6 +197,7 @@ size_t carve(const HosvdPlan& p, unsigned char* base, HosvdWs* ws) {
     m.Q = (double*)a.take(p.ymat);
     m.small = a.take(p.small);
     m.alpha = (double*)a.take(sizeof(double));
+    m.kr = (float*)a.take(p.kr);
     if (ws) ws[c] = m;
   }
   return al(a.off) + 256;
@@ -220,9 +226,18 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
   const double nl = (double)v.n * l;
   const double red_bytes = (double)splits * v.n * lc * asize(xt) + nl * 8.0;
   const double svd_flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
+  const bool dense_gauss = p.omega == TK_OMEGA_GAUSS;
+  const double om_bytes = dense_gauss ? 0.0 : (double)v.cols() * l * asize(xt);
+  if (!dense_gauss) {
+    // the structured test matrices (Section 5.5) are written out into W
+    ProfScope ps(TK_K_SKETCH, om_bytes, 0.0, st);
+    TK_TRY(launch_omega_fill(p.omega, p.dims_at[k].data(), p.d, k, l, seed, tag, ka, kb, w.kr,
+                             w.w, fp64, v.P, st));
+  }
   {
-    ProfScope ps(TK_K_SKETCH, N * xsize(xt), 2.0 * N * l, st);
-    TK_TRY(launch_xb(xt, X, v, nullptr, l, seed, tag, k, w.part, splits, st, ka, kb));
+    ProfScope ps(TK_K_SKETCH, N * xsize(xt) + om_bytes, 2.0 * N * l, st);
+    TK_TRY(launch_xb(xt, X, v, dense_gauss ? nullptr : w.w, l, seed, tag, k, w.part, splits, st,
+                     ka, kb));
   }
   {
     ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
@@ -533,6 +548,23 @@ tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t 
   if (rows > 0 && l > 0 && out == nullptr) return TK_EINVAL;
   TK_TRY(launch_omega(k, row0, rows, l, seed, tag, out, (cudaStream_t)stream));
   return TK_OK;
+}
+
+tk_status tucker_debug_omega_matrix(tk_omega kind, int d, const int64_t* n, int k, int l,
+                                    uint64_t seed, uint32_t tag, float* out, void* stream) {
+  if (kind < TK_OMEGA_GAUSS || kind > TK_OMEGA_KR_UNIFORM || d < 1 || d > TK_MAX_D || !n ||
+      k < 0 || k >= d || l < 1 || l > TK_MAX_L || tag >= (1u << 24) || !out)
+    return TK_EINVAL;
+  for (int m = 0; m < d; ++m)
+    if (n[m] < 1) return TK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t kb = omega_scratch(kind, n, d, k, l);
+  float* kr = nullptr;
+  if (kb) TK_TRY(cudaMallocAsync((void**)&kr, kb, st));
+  cudaError_t e = launch_omega_fill(kind, n, d, k, l, seed, tag, 0, 1, kr, out, false, 0, st);
+  cudaError_t e2 = kr ? cudaFreeAsync(kr, st) : cudaSuccess;
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(e2);
 }
 
 tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_t tag, double* Y,

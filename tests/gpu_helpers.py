@@ -6,7 +6,8 @@ from paper_2506_04840_gb300 import api
 
 
 def run_hosvd(A, r, s, q, st=True, seed=0, tag=0, shift=api.TK_SHIFT_PAPER,
-              prec=api.TK_PREC_PLAIN, order=None, stats=True, workspace=False):
+              prec=api.TK_PREC_PLAIN, order=None, stats=True, workspace=False,
+              omega=api.TK_OMEGA_GAUSS):
     import torch
     d = A.ndim
     dims = list(A.shape)
@@ -16,12 +17,13 @@ def run_hosvd(A, r, s, q, st=True, seed=0, tag=0, shift=api.TK_SHIFT_PAPER,
     core = torch.empty(int(np.prod(r)), dtype=tdt, device="cuda")
     U = [torch.empty(dims[k] * r[k], dtype=tdt, device="cuda") for k in range(d)]
     ws = None
-    opts = api.make_opts(d, q, s, seed=seed, tag=tag, shift=shift, prec=prec, order=order)
+    opts = api.make_opts(d, q, s, seed=seed, tag=tag, shift=shift, prec=prec, order=order,
+                         omega=omega)
     if workspace:
         nbytes = api.tucker_workspace_size(Ad, dims, r, opts, 1 if st else 0)
         ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         opts = api.make_opts(d, q, s, seed=seed, tag=tag, shift=shift, prec=prec, order=order,
-                             workspace=ws)
+                             workspace=ws, omega=omega)
     fn = api.tucker_rsthosvd if st else api.tucker_rthosvd
     info = fn(Ad, dims, r, opts, core, U, stats=stats)
     torch.cuda.synchronize()

@@ -115,6 +115,20 @@ def test_argument_validation_before_launch():
     assert lib.tucker_debug_omega(0, -1, 4, 4, 0, 0, ctypes.c_void_p(0x3000),
                                   None) == api.TK_EINVAL
     assert lib.tucker_to_bf16(None, 5, None, None) == api.TK_EINVAL
+    # test matrix kinds: an unknown kind, and the debug writer's checks
+    oo = api.make_opts(3, 2, 5, omega=7)
+    assert lib.tucker_rsthosvd(ctypes.byref(A), rr, ctypes.byref(oo), ctypes.c_void_p(0x3000),
+                               U, None, None) == api.TK_EINVAL
+    n3 = (ctypes.c_int64 * 3)(10, 10, 10)
+    for args in ((4, 3, n3, 0, 4), (api.TK_OMEGA_KR_GAUSS, 3, n3, 3, 4),
+                 (api.TK_OMEGA_UNIFORM, 3, n3, 0, 0),
+                 (api.TK_OMEGA_UNIFORM, 3, n3, 0, api.TK_MAX_L + 1),
+                 (api.TK_OMEGA_UNIFORM, 0, n3, 0, 4),
+                 (api.TK_OMEGA_UNIFORM, 3, (ctypes.c_int64 * 3)(10, 0, 10), 0, 4)):
+        assert lib.tucker_debug_omega_matrix(*args, 0, 0, ctypes.c_void_p(0x3000),
+                                             None) == api.TK_EINVAL, args
+    assert lib.tucker_debug_omega_matrix(api.TK_OMEGA_UNIFORM, 3, n3, 0, 4, 0, 1 << 24,
+                                         ctypes.c_void_p(0x3000), None) == api.TK_EINVAL
     # Algorithm 4: tol >= 0, q_max >= 1, plain precision only
     for tol, oo in ((-1.0, api.make_opts(3, 2, 5)), (0.5, api.make_opts(3, 0, 5)),
                     (0.5, api.make_opts(3, 2, 5, prec=api.TK_PREC_BF16_POWER))):
@@ -138,6 +152,14 @@ def test_workspace_size_is_host_only_and_monotone():
                                    ctypes.byref(api.make_opts(3, 3, 5,
                                                               prec=api.TK_PREC_BF16_POWER)), 1)
     assert bf > big            # the bfloat16 shadow
+    # a stored test matrix needs W even without power steps; Khatri-Rao
+    # factors add their scratch
+    t = _fake_tensor([80, 80, 80])
+    ws = {kind: lib.tucker_workspace_size(ctypes.byref(t), rr,
+                                          ctypes.byref(api.make_opts(3, 0, 5, omega=kind)), 1)
+          for kind in range(4)}
+    assert ws[api.TK_OMEGA_UNIFORM] > ws[api.TK_OMEGA_GAUSS]
+    assert ws[api.TK_OMEGA_KR_GAUSS] == ws[api.TK_OMEGA_KR_UNIFORM] > ws[api.TK_OMEGA_UNIFORM]
     bad = (ctypes.c_int * 3)(80, 5, 5)
     assert lib.tucker_workspace_size(ctypes.byref(_fake_tensor([80, 80, 80])), bad,
                                      ctypes.byref(api.make_opts(3, 2, 5)), 1) == 0
