@@ -222,6 +222,37 @@ def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=Non
     return G, Us, qs, stats
 
 
+def holistic(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, st=True, omega=OMEGA_GAUSS):
+    """Algorithm B.1 (ST case, shifted power steps) and Algorithm A.2
+    (rule=SHIFT_NONE; ST or T-HOSVD case): range finding with all l_k
+    columns kept, then a deterministic ST-HOSVD of the small tensor.
+
+    Per mode k in 1..d: Q_k from the sketch and q power steps of Algorithm
+    3 on B (ST case; B shrinks as it goes) or on A (T-HOSVD case), keeping
+    Q_k with l_k columns; B <- B x_k Q_k^T.  Then {G; V_1..V_d} =
+    ST-HOSVD(B, r) (Algorithm 1) and U_k = Q_k V_k.
+    Returns (G, [U_k], stats) with stats per mode (l, alpha, sigma).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    d = A.ndim
+    s = [s] * d if np.isscalar(s) else list(s)
+    B = A
+    Qs, stats = [], []
+    for k in range(d):
+        X = B if st else A
+        cols = int(np.prod([X.shape[m] for m in range(d) if m != k]))
+        l = clamp_l(r[k], s[k], X.shape[k], cols)
+        if l < r[k]:
+            raise ValueError("mode %d: only %d columns for rank %d" % (k, l, r[k]))
+        Q, S = svd_econ(sketch(X, k, l, seed, tag, omega))
+        Q, S2, _, a_hist, s_hist = shifted_power(X, k, Q, 0.0, q, rule)
+        Qs.append(Q)
+        stats.append(dict(l=l, alpha=a_hist, sigma_l=s_hist, sigma=S2 if S2 is not None else S))
+        B = mode_product(B, Q.T, k)
+    G, Vs = hosvd(B, r, sequential=True)
+    return G, [Q @ V for Q, V in zip(Qs, Vs)], stats
+
+
 def hosvd(A, r, sequential):
     """Algorithm 1: deterministic T-HOSVD (sequential=False) or ST-HOSVD."""
     A = np.asarray(A, dtype=np.float64)

@@ -337,3 +337,72 @@ def test_structured_test_matrices_reach_the_tensor_C_optimum(kind, st):
         re = T.rel_error(A, G, Us)
         assert opt * (1 - 1e-9) <= re <= 1.02 * opt, (kind, decay, re, opt)
         assert re <= 1.015 * re_g, (kind, decay, re, re_g)
+
+
+# ---- Algorithms A.2 / B.1 (holistic range finding) -------------------------
+
+@pytest.mark.parametrize("st", [True, False])
+def test_holistic_without_oversampling_spans_algorithm3s_factors(st):
+    """With s = 0 the kept Q_k has r_k columns, so V_k is an r_k x r_k
+    rotation and U_k = Q_k V_k spans Q_k: the same subspaces and the same
+    error as Algorithm 3 (ST) / Algorithm 2 (T) with s = 0."""
+    A = I.tucker_plus_noise([30, 26, 22], [5, 5, 5], 3, noise=1e-2)
+    r = [4, 3, 5]
+    G, Us, _ = T.holistic(A, r, 0, 2, st=st)
+    f = T.rsthosvd if st else T.rthosvd
+    Gw, Uw, _ = f(A, r, 0, 2)
+    for U, V in zip(Us, Uw):
+        assert T.principal_sines(U, V).max() < 1e-10
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13
+    assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gw, Uw)) < 1e-12
+
+
+@pytest.mark.parametrize("st", [True, False])
+def test_holistic_recovers_exact_low_rank_and_meets_the_error_identity(st):
+    """A tensor of multilinear rank r is recovered exactly, and for noisy
+    data ||A - A_hat||^2 = ||A||^2 - ||G||^2 (orthonormal U_k, G = A x U^T)."""
+    A = I.tucker_plus_noise([24, 20, 18, 10], [3, 4, 2, 3], 5, noise=0.0, dtype=np.float64)
+    G, Us, _ = T.holistic(A, [3, 4, 2, 3], 4, 1, st=st)
+    assert T.rel_error(A, G, Us) < 1e-13
+    A = I.tucker_plus_noise([24, 20, 18], [4, 4, 4], 6, noise=1e-1, dtype=np.float64)
+    G, Us, _ = T.holistic(A, [3, 3, 3], 5, 1, st=st)
+    Ahat = T.reconstruct(G, Us)
+    lhs = np.linalg.norm(A - Ahat) ** 2
+    rhs = np.linalg.norm(A) ** 2 - np.linalg.norm(G) ** 2
+    assert abs(lhs - rhs) <= 1e-10 * np.linalg.norm(A) ** 2
+    # G is the projection of A on the returned factors
+    Gp = A
+    for k, U in enumerate(Us):
+        Gp = T.mode_product(Gp, U.T, k)
+    assert np.abs(Gp - G).max() <= 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("st", [True, False])
+@pytest.mark.parametrize("q", [0, 2])
+def test_holistic_with_full_range_is_algorithm1(st, q):
+    """With l_k = n_k every Q_k is square orthogonal, so B is A rotated in
+    every mode and the small ST-HOSVD's factors, rotated back, are those of
+    deterministic ST-HOSVD (Algorithm 1) of A, whatever q."""
+    A = I.tucker_plus_noise([12, 10, 8], [4, 4, 4], 9, noise=1e-2, decay=0.7,
+                            dtype=np.float64)
+    r = [3, 3, 3]
+    G, Us, st_ = T.holistic(A, r, 20, q, st=st)
+    assert [x["l"] for x in st_] == [12, 10, 8]
+    Gd, Ud = T.hosvd(A, r, sequential=True)
+    for U, V in zip(Us, Ud):
+        assert T.principal_sines(U, V).max() < 1e-10
+    assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gd, Ud)) < 1e-12
+
+
+@pytest.mark.parametrize("st", [True, False])
+def test_holistic_reaches_the_tensor_C_optimum(st):
+    """Appendix B compares the holistic variants with Algorithms 2/3 at
+    s = 10, q = 1 and finds the errors comparable: on tensor C within 1% of
+    the closed-form optimum."""
+    n, r = 60, 10
+    for decay in ("slow", "fast"):
+        A = I.superdiagonal(n, decay, seed=21)
+        opt = _closed_form(I.superdiagonal_values(n, decay), r)
+        G, Us, _ = T.holistic(A, [r] * 3, 10, 1, st=st)
+        re = T.rel_error(A, G, Us)
+        assert opt * (1 - 1e-9) <= re <= 1.01 * opt, (decay, re, opt)
