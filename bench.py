@@ -47,6 +47,11 @@ WORKLOADS = {
                                            "Gaussian factors as Omega_k (Section 5.5)",
                                       shape=[400, 400, 400], r=[20, 20, 20], s=10, q=2,
                                       st=True, dtype="f32", prec=0, omega=2),
+    "tucker400_fp32_st_holistic": dict(desc="as tucker400_fp32_st with Algorithm B.1: range "
+                                            "finder keeps l_k = 30 columns, FP64 ST-HOSVD of "
+                                            "the 30^3 tensor, U_k = Q_k V_k",
+                                       shape=[400, 400, 400], r=[20, 20, 20], s=10, q=2,
+                                       st=True, dtype="f32", prec=0, holistic=True),
     "invradius1000_fp32_st": dict(desc="1000^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise; randomized "
                                        "ST-HOSVD, r=(50,50,50), p=10, q=3, plain FP32",
                                   shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3, st=True,
@@ -173,6 +178,9 @@ def oracle_step(A, w):
     from oracle import tucker as T
     if w.get("pve") is not None:
         G, Us, _, _ = T.rsthosvd_pve(A, w["r"], w["s"], w["q"], w["pve"])
+        return T.rel_error(A, G, Us)
+    if w.get("holistic"):
+        G, Us, _ = T.holistic(A, w["r"], w["s"], w["q"], st=w["st"])
         return T.rel_error(A, G, Us)
     from oracle import omega as om
     kind = om.OMEGA_KINDS[w.get("omega", 0)]
@@ -597,7 +605,8 @@ def main():
     rel = torch.zeros(1, dtype=torch.float64, device="cuda")
     kind = w.get("omega", api.TK_OMEGA_GAUSS)
     opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], omega=kind)
-    nbytes = api.tucker_workspace_size(Ad, dims, r, opts, 1 if w["st"] else 0)
+    nbytes = (api.tucker_holistic_workspace_size if w.get("holistic") else
+              api.tucker_workspace_size)(Ad, dims, r, opts, 1 if w["st"] else 0)
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], workspace=ws, omega=kind)
     fn = api.tucker_rsthosvd if w["st"] else api.tucker_rthosvd
@@ -609,6 +618,8 @@ def main():
         if w.get("pve") is not None:
             qs, _ = api.tucker_rsthosvd_pve(X, dims, r, opts, w["pve"], core, U, stream=stream)
             q_chosen[:] = qs
+        elif w.get("holistic"):
+            api.tucker_holistic(X, dims, r, opts, 1 if w["st"] else 0, core, U, stream=stream)
         else:
             fn(X, dims, r, opts, core, U, stats=False, stream=stream)
         api.tucker_error(X, dims, core, r, U, rel, stream=stream)

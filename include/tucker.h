@@ -148,6 +148,25 @@ size_t tucker_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o,
 tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed,
                              uint32_t tag, float* out, void* stream);
 
+/* Holistic variants (Algorithm B.1 for ST-HOSVD with TK_SHIFT_PAPER;
+ * Algorithm A.2, ST or T-HOSVD case, with TK_SHIFT_NONE; the T-HOSVD case
+ * with the shift is the variant the remark after Algorithm B.1 names).
+ * Per mode k = 1..d: the sketch and q power steps of Algorithms 2/3 with all
+ * l_k = min(r_k + s_k, n_k, columns) columns kept as Q_k, on the shrinking
+ * tensor B (st = 1) or on A (st = 0); B <- B x_k Q_k^T.  Then the
+ * deterministic ST-HOSVD of the l_1 x ... x l_d tensor B (held in FP64;
+ * V_k = the leading r_k eigenvectors of B_(k) B_(k)^T, summed in FP64 and
+ * solved by the svd in the input's precision, sorted and sign-fixed like
+ * the svd results) gives the core, and U_k = Q_k V_k.  Modes in natural order
+ * (o->order ignored); plain precision only (TK_EINVAL otherwise); any
+ * tk_omega kind.  Outputs as tucker_rsthosvd; stats describe the range
+ * finder (l_k, its shifts and Sigma). */
+tk_status tucker_holistic(const tk_tensor* A, const int* r, const tk_opts* o, int st, void* core,
+                          void* const* U, tk_stats* stats, void* stream);
+/* Bytes of device workspace tucker_holistic needs; 0 for invalid arguments. */
+size_t tucker_holistic_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o,
+                                      int st);
+
 /* Omega_k of any kind (tk_omega) for a tensor of order d and sizes n, in the
  * unfolding's own row order, written as a (prod_{m != k} n_m) x l
  * column-major FP32 matrix `out` (device).  Returns TK_EINVAL for a bad

@@ -231,7 +231,9 @@ def holistic(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, st=True, omega=OMEGA_G
     3 on B (ST case; B shrinks as it goes) or on A (T-HOSVD case), keeping
     Q_k with l_k columns; B <- B x_k Q_k^T.  Then {G; V_1..V_d} =
     ST-HOSVD(B, r) (Algorithm 1) and U_k = Q_k V_k.
-    Returns (G, [U_k], stats) with stats per mode (l, alpha, sigma).
+    Returns (G, [U_k], stats) with stats per mode (l, alpha, sigma of the
+    range finder; sigma_small, the singular values of the small tensor's
+    unfolding that V_k comes from).
     """
     A = np.asarray(A, dtype=np.float64)
     d = A.ndim
@@ -250,6 +252,12 @@ def holistic(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, st=True, omega=OMEGA_G
         stats.append(dict(l=l, alpha=a_hist, sigma_l=s_hist, sigma=S2 if S2 is not None else S))
         B = mode_product(B, Q.T, k)
     G, Vs = hosvd(B, r, sequential=True)
+    # record the spectrum each small mode's V_k was taken from (the
+    # singular values of the unfolding Algorithm 1 factors at that step)
+    Bk = B
+    for k in range(d):
+        stats[k]["sigma_small"] = np.linalg.svd(unfold(Bk, k), compute_uv=False)
+        Bk = mode_product(Bk, Vs[k].T, k)
     return G, [Q @ V for Q, V in zip(Qs, Vs)], stats
 
 

@@ -103,6 +103,11 @@ SIGNATURES = {
                                     ctypes.POINTER(tk_opts), c_double, c_void_p,
                                     ctypes.POINTER(c_void_p), ctypes.POINTER(c_int),
                                     ctypes.POINTER(tk_stats), c_void_p]),
+    "tucker_holistic": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                ctypes.POINTER(tk_opts), c_int, c_void_p, ctypes.POINTER(c_void_p),
+                                ctypes.POINTER(tk_stats), c_void_p]),
+    "tucker_holistic_workspace_size": (c_size_t, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                                  ctypes.POINTER(tk_opts), c_int]),
     "tucker_error": (c_int, [ctypes.POINTER(tk_tensor), c_void_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
     "tucker_to_bf16": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
@@ -292,6 +297,24 @@ def tucker_rsthosvd_pve(A, dims, r, opts, tol, core, U, stats=False, stream=None
                                       ctypes.byref(st) if st is not None else None,
                                       _stream(stream)), "tucker_rsthosvd_pve")
     return [int(x) for x in qs], (_stats_dict(st) if st is not None else None)
+
+
+def tucker_holistic(A, dims, r, opts, st, core, U, stats=False, stream=None):
+    """Algorithms A.2 / B.1 (holistic range finding, then ST-HOSVD of the
+    small tensor).  Returns the stats dict or None."""
+    desc = tensor_desc(A, dims)
+    s = tk_stats() if stats else None
+    _check(load().tucker_holistic(ctypes.byref(desc), _ranks(r), ctypes.byref(opts), int(st),
+                                  _ptr(core), _ptr_array(U),
+                                  ctypes.byref(s) if s is not None else None, _stream(stream)),
+           "tucker_holistic")
+    return _stats_dict(s) if s is not None else None
+
+
+def tucker_holistic_workspace_size(A, dims, r, opts, st):
+    desc = tensor_desc(A, dims)
+    return int(load().tucker_holistic_workspace_size(ctypes.byref(desc), _ranks(r),
+                                                     ctypes.byref(opts), int(st)))
 
 
 def tucker_error(A, dims, core, r, U, rel_err, stream=None):

@@ -192,6 +192,82 @@ cudaError_t launch_omega_fill(int kind, const int64_t* dims, int d, int k, int l
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Holistic variants (Algorithms A.2 / B.1): the small deterministic
+// ST-HOSVD of the l_1 x ... x l_d tensor and U_k = Q_k V_k.
+// ---------------------------------------------------------------------------
+
+// M (n x n, column-major) = B_(k) B_(k)^T for the strided view (P, n, S) of an
+// FP64 tensor (entry (i, j = p + P s) at p + P (i + n s)).  Block t takes the
+// pair (i, i') of the lower triangle with t = i (i + 1) / 2 + i'; its threads
+// sum over the P S columns in a fixed order.
+__global__ void k_gram_unfold(const double* __restrict__ B, int64_t P, int64_t n, int64_t S,
+                              double* __restrict__ M) {
+  __shared__ double red[32];
+  const int64_t t = blockIdx.x;
+  int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  const int64_t ip = t - i * (i + 1) / 2;
+  const int64_t cols = P * S;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+    const int64_t s = j / P, p = j - s * P;
+    const double a = B[p + P * (i + n * s)];
+    const double b = B[p + P * (ip + n * s)];
+    acc = fma(a, b, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = acc;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    acc = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      M[i + n * ip] = acc;
+      M[ip + n * i] = acc;
+    }
+  }
+}
+
+cudaError_t launch_gram_unfold(const double* B, View v, double* M, cudaStream_t st) {
+  const int64_t pairs = v.n * (v.n + 1) / 2;
+  if (pairs <= 0) return cudaSuccess;
+  count_kernels(1);
+  k_gram_unfold<<<(unsigned)pairs, 256, 0, st>>>(B, v.P, v.n, v.S, M);
+  return cudaGetLastError();
+}
+
+// U (n x r, column-major, type T) = Q (n x l, FP64) V (l x r, FP64), each
+// entry summed over c in ascending order in FP64.
+template <typename T>
+__global__ void k_qv(const double* __restrict__ Q, int64_t n, int l, const double* __restrict__ V,
+                     int r, T* __restrict__ U) {
+  const int64_t tot = n * r;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    double acc = 0.0;
+    for (int c = 0; c < l; ++c) acc = fma(Q[i + n * c], V[c + (int64_t)l * j], acc);
+    U[idx] = (T)acc;
+  }
+}
+
+cudaError_t launch_qv(const double* Q, int64_t n, int l, const double* V, int r, void* U,
+                      XType dt, cudaStream_t st) {
+  const int64_t tot = n * r;
+  if (tot <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
+  count_kernels(1);
+  if (dt == X_F64)
+    k_qv<double><<<blocks, 256, 0, st>>>(Q, n, l, V, r, (double*)U);
+  else
+    k_qv<float><<<blocks, 256, 0, st>>>(Q, n, l, V, r, (float*)U);
+  return cudaGetLastError();
+}
+
 // Round to nearest even bfloat16, 8 values per thread per step (two 16-byte
 // loads, one 16-byte store) with a scalar tail.
 __global__ void k_to_bf16(const float* __restrict__ x, int64_t count, uint16_t* __restrict__ out) {

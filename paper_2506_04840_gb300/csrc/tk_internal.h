@@ -175,6 +175,11 @@ cudaError_t launch_copy_matrix(const double* src, int64_t ld_src, void* dst, int
 cudaError_t launch_copy_tensor(const void* src, void* dst, int64_t count, XType dt,
                                cudaStream_t st);
 cudaError_t launch_to_f64_from_f32(const float* x, int64_t count, double* y, cudaStream_t st);
+// Holistic variants: M (n x n) = B_(k) B_(k)^T of an FP64 tensor's strided
+// view; U (n x r, dt) = Q (n x l) V (l x r), FP64 sums.
+cudaError_t launch_gram_unfold(const double* B, View v, double* M, cudaStream_t st);
+cudaError_t launch_qv(const double* Q, int64_t n, int l, const double* V, int r, void* U,
+                      XType dt, cudaStream_t st);
 cudaError_t launch_check_finite(const double* x, int64_t count, int* status, cudaStream_t st);
 
 }  // namespace tk

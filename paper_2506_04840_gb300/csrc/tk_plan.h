@@ -138,7 +138,10 @@ struct HosvdWs {
   float* kr;
 };
 
-tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st, HosvdPlan& p);
+// full_ok: accept r_k = n_k (the holistic range finder keeps l_k = n_k
+// columns when r_k + s_k >= n_k).
+tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st, HosvdPlan& p,
+                    bool full_ok = false);
 // Lays the workspace out from `base` (nullptr: only measures); returns bytes.
 // ws (when given) receives workspace_copies(p) entries (one per concurrently
 // factored mode; they share the tensor buffers, histories and status).

@@ -75,7 +75,7 @@ ProfScope::~ProfScope() {
 // Plan of one tucker_rthosvd / tucker_rsthosvd call.
 // ---------------------------------------------------------------------------
 tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
-                    HosvdPlan& p) {
+                    HosvdPlan& p, bool full_ok) {
   if (!valid_tensor(A, false) || !r || !o) return TK_EINVAL;
   p.d = A->d;
   p.st = st;
@@ -94,7 +94,8 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
   if (o->omega < TK_OMEGA_GAUSS || o->omega > TK_OMEGA_KR_UNIFORM) return TK_EINVAL;
   p.omega = o->omega;
   for (int k = 0; k < p.d; ++k) {
-    if (p.r[k] < 1 || p.r[k] >= p.n[k]) return TK_EINVAL;   // Problem 2.1: r_k < n_k
+    if (p.r[k] < 1 || p.r[k] > p.n[k]) return TK_EINVAL;
+    if (p.r[k] == p.n[k] && !full_ok) return TK_EINVAL;      // Problem 2.1: r_k < n_k
     if (p.s[k] < 0) return TK_EINVAL;
   }
   if (o->order[0] < 0) {
@@ -516,11 +517,220 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
   return rs;
 }
 
+// ---------------------------------------------------------------------------
+// Holistic variants (Algorithms A.2 and B.1).
+// ---------------------------------------------------------------------------
+struct HolisticPlan {
+  HosvdPlan p;                  // the range finder: ranks r' = l, s' = 0
+  std::vector<int> r;           // the requested ranks
+  std::vector<SmallPlan> sm;    // svd of each l_k x l_k Gram matrix (FP64)
+  size_t qk = 0, bx = 0, b64 = 0, v = 0, small = 0, sig = 0;
+};
+
+static tk_status holistic_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
+                               HolisticPlan& h) {
+  if (!valid_tensor(A, false) || !r || !o) return TK_EINVAL;
+  if (o->prec != TK_PREC_PLAIN) return TK_EINVAL;
+  const int d = A->d;
+  std::vector<int64_t> cur(A->n, A->n + d);
+  int rl[TK_MAX_D];
+  for (int k = 0; k < d; ++k) {
+    if (r[k] < 1 || r[k] >= A->n[k] || o->s[k] < 0) return TK_EINVAL;
+    int64_t cols = 1;
+    for (int m = 0; m < d; ++m)
+      if (m != k) cols *= st ? cur[m] : A->n[m];
+    const int64_t lk = std::min<int64_t>({(int64_t)r[k] + o->s[k], A->n[k], cols});
+    if (lk < r[k]) return TK_EINVAL;
+    if (lk > TK_MAX_L) return TK_ENOTIMPL;
+    rl[k] = (int)lk;
+    if (st) cur[k] = lk;
+  }
+  tk_opts o2 = *o;
+  for (int k = 0; k < TK_MAX_D; ++k) o2.s[k] = 0;
+  o2.order[0] = -1;
+  tk_status s = make_plan(A, rl, &o2, st, h.p, true);
+  if (s != TK_OK) return s;
+  h.r.assign(r, r + d);
+  const size_t es = xsize(h.p.xt);
+  size_t lprod = 1;
+  h.sm.assign(d, SmallPlan{});
+  for (int k = 0; k < d; ++k) {
+    h.qk += al((size_t)A->n[k] * rl[k] * sizeof(double));
+    h.v += al((size_t)rl[k] * r[k] * sizeof(double));
+    lprod *= (size_t)rl[k];
+    // the eigenvectors need the accuracy of B's own arithmetic: the FP32
+    // register svd (then polished) for FP32 tensors, FP64 for FP64
+    h.sm[k] = small_plan(rl[k], rl[k], h.p.xt == X_F64);
+    if (h.sm[k].Pb <= 0) return TK_ENOTIMPL;
+    h.small = std::max(h.small, h.sm[k].scratch_bytes);
+    if (h.p.xt != X_F64) h.small = std::max(h.small, polish_scratch(rl[k], r[k]));
+  }
+  h.bx = lprod * es;
+  h.b64 = lprod * sizeof(double);
+  h.sig = TK_MAX_L * sizeof(double);
+  return TK_OK;
+}
+
+static size_t holistic_bytes(const HolisticPlan& h) {
+  return carve(h.p, nullptr, nullptr) + 256 + al(h.qk) + al(h.bx) + 2 * al(h.b64) + al(h.v) +
+         al(h.small) + al(h.sig) + 1024;
+}
+
+static tk_status run_holistic(const tk_tensor* A, const int* r, const tk_opts* o, void* core,
+                              void* const* U, tk_stats* stats, cudaStream_t st, bool sequential) {
+  HolisticPlan h;
+  tk_status s = holistic_plan(A, r, o, sequential, h);
+  if (s != TK_OK) return s;
+  const HosvdPlan& p = h.p;
+  if (!core || !U) return TK_EINVAL;
+  for (int k = 0; k < p.d; ++k)
+    if (!U[k]) return TK_EINVAL;
+  const size_t need = holistic_bytes(h);
+  unsigned char* base = (unsigned char*)o->workspace;
+  bool owned = false;
+  if (base == nullptr) {
+    TK_TRY(cudaMallocAsync((void**)&base, need, st));
+    owned = true;
+  } else if (o->workspace_bytes < need) {
+    return TK_EWORKSPACE;
+  }
+  unsigned char* b0 = (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255);
+  HosvdWs wm[TK_MAX_D];
+  const size_t main = carve(p, b0, wm);
+  Arena a;
+  a.base = b0 + al(main);
+  unsigned char* qk0 = (unsigned char*)a.take(h.qk);
+  void* bx = a.take(h.bx);
+  double* b64[2] = {(double*)a.take(h.b64), (double*)a.take(h.b64)};
+  unsigned char* v0 = (unsigned char*)a.take(h.v);
+  void* small = a.take(h.small);
+  double* sig = (double*)a.take(h.sig);
+  const HosvdWs& w = wm[0];
+  std::vector<double*> qk(p.d), vk(p.d);
+  {
+    size_t oq = 0, ov = 0;
+    for (int k = 0; k < p.d; ++k) {
+      qk[k] = (double*)(qk0 + oq);
+      vk[k] = (double*)(v0 + ov);
+      oq += al((size_t)p.n[k] * p.l[k] * sizeof(double));
+      ov += al((size_t)p.l[k] * h.r[k] * sizeof(double));
+    }
+  }
+  auto run = [&]() -> tk_status {
+    TK_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    TK_TRY(cudaMemsetAsync(w.ahist, 0, sizeof(double) * TK_MAX_D * TK_MAX_Q, st));
+    TK_TRY(cudaMemsetAsync(w.shist, 0, sizeof(double) * TK_MAX_D * TK_MAX_Q, st));
+    TK_TRY(cudaMemsetAsync(w.sig, 0, sizeof(double) * TK_MAX_D * TK_MAX_L, st));
+    // range finder: Q_k with l_k columns; B <- B x_k Q_k^T (ST case: on the
+    // shrinking tensor; T-HOSVD case: every Q_k from A, then the chain)
+    const void* X = A->data;
+    std::vector<int64_t> cur = p.n;
+    int pp = 0;
+    for (int k = 0; k < p.d; ++k) {
+      const int lk = p.l[k];
+      int64_t ka = 0, kb = 1;
+      const View v = p.st ? step_view(p, cur, k, &ka, &kb) : view_of(p.n, k);
+      const tk_status e = factor_mode(p, k, p.st ? X : A->data, p.xt, v, ka, kb, o->seed,
+                                      o->tag, w, st);
+      if (e != TK_OK) return e;
+      if (p.xt != X_F64) TK_TRY(polish(w.Q, v.n, lk, w.small, w.status, st));
+      TK_TRY(launch_copy_matrix(w.Q, v.n, qk[k], v.n, v.n, lk, X_F64, st));
+      if (p.st) {
+        void* out = (k == p.d - 1) ? bx : w.g[pp];
+        TK_TRY(ttm(p.xt, X, v, qk[k], lk, out, st, p.rot ? 1 : 0, w.part));
+        X = out;
+        pp ^= 1;
+        cur[k] = lk;
+      }
+    }
+    if (!p.st) {
+      for (int k = 0; k < p.d; ++k) {
+        const View v = view_of(cur, k);
+        void* out = (k == p.d - 1) ? bx : w.g[k & 1];
+        TK_TRY(ttm(p.xt, X, v, qk[k], p.l[k], out, st, 0, w.part));
+        X = out;
+        cur[k] = p.l[k];
+      }
+    }
+    // deterministic ST-HOSVD (Algorithm 1) of B, held in FP64: V_k = leading
+    // eigenvectors of B_(k) B_(k)^T (FP64 sums), B <- B x_k V_k^T; then
+    // U_k = Q_k V_k
+    const int64_t cnt = prod(cur);
+    if (p.xt == X_F64)
+      TK_TRY(cudaMemcpyAsync(b64[0], bx, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToDevice,
+                             st));
+    else
+      TK_TRY(launch_to_f64_from_f32((const float*)bx, cnt, b64[0], st));
+    int cb = 0;
+    for (int k = 0; k < p.d; ++k) {
+      const int lk = p.l[k];
+      const View v = view_of(cur, k);
+      {
+        ProfScope ps(TK_K_SMALL_SVD, (double)v.P * v.n * v.S * 8.0,
+                     2.0 * v.P * v.n * v.S * v.n, st);
+        TK_TRY(launch_gram_unfold(b64[cb], v, w.Y, st));
+        TK_TRY(launch_small_svd(p.xt == X_F64, h.sm[k], w.Y, lk, w.Q, sig, small,
+                                (int)TK_SHIFT_NONE, false, w.alpha, nullptr, nullptr, w.status,
+                                st));
+      }
+      if (p.xt != X_F64) TK_TRY(polish(w.Q, lk, h.r[k], small, w.status, st));
+      TK_TRY(launch_copy_matrix(w.Q, lk, vk[k], lk, lk, h.r[k], X_F64, st));
+      TK_TRY(ttm(X_F64, b64[cb], v, vk[k], h.r[k], b64[cb ^ 1], st));
+      cb ^= 1;
+      cur[k] = h.r[k];
+    }
+    TK_TRY(launch_copy_matrix(b64[cb], prod(cur), core, prod(cur), prod(cur), 1, p.xt, st));
+    for (int k = 0; k < p.d; ++k)
+      TK_TRY(launch_qv(qk[k], p.n[k], p.l[k], vk[k], h.r[k], U[k], p.xt, st));
+    if (stats) {
+      std::vector<double> ah(TK_MAX_D * TK_MAX_Q), sh(TK_MAX_D * TK_MAX_Q), sg(TK_MAX_D * TK_MAX_L);
+      int status = 0;
+      TK_TRY(cudaMemcpyAsync(ah.data(), w.ahist, ah.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(sh.data(), w.shist, sh.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(sg.data(), w.sig, sg.size() * 8, cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TK_TRY(cudaStreamSynchronize(st));
+      std::memset(stats, 0, sizeof(*stats));
+      stats->d = p.d;
+      stats->q = p.q;
+      for (int k = 0; k < p.d; ++k) {
+        stats->l[k] = p.l[k];
+        stats->order[k] = k;
+        for (int t = 0; t < TK_MAX_Q; ++t) {
+          stats->alpha[k][t] = ah[k * TK_MAX_Q + t];
+          stats->sigma_l[k][t] = sh[k * TK_MAX_Q + t];
+        }
+        for (int i = 0; i < TK_MAX_L; ++i) stats->sigma[k][i] = sg[k * TK_MAX_L + i];
+      }
+      if (status != 0) return (tk_status)status;
+    }
+    return TK_OK;
+  };
+  tk_status rs = run();
+  if (owned) {
+    cudaError_t e = cudaFreeAsync(base, st);
+    if (rs == TK_OK && e != cudaSuccess) rs = from_cuda(e);
+  }
+  return rs;
+}
+
 }  // namespace tk
 
 using namespace tk;
 
 extern "C" {
+
+size_t tucker_holistic_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o,
+                                      int st) {
+  HolisticPlan h;
+  if (holistic_plan(A, r, o, st != 0, h) != TK_OK) return 0;
+  return holistic_bytes(h);
+}
+
+tk_status tucker_holistic(const tk_tensor* A, const int* r, const tk_opts* o, int st, void* core,
+                          void* const* U, tk_stats* stats, void* stream) {
+  return run_holistic(A, r, o, core, U, stats, (cudaStream_t)stream, st != 0);
+}
 
 const char* tucker_status_string(tk_status s) {
   switch (s) {

@@ -129,6 +129,14 @@ def test_argument_validation_before_launch():
                                              None) == api.TK_EINVAL, args
     assert lib.tucker_debug_omega_matrix(api.TK_OMEGA_UNIFORM, 3, n3, 0, 4, 0, 1 << 24,
                                          ctypes.c_void_p(0x3000), None) == api.TK_EINVAL
+    # holistic variants: plain precision, r_k < n_k, outputs present
+    for oo, rk in ((api.make_opts(3, 2, 5, prec=api.TK_PREC_BF16_POWER), rr),
+                   (api.make_opts(3, 2, 5), (ctypes.c_int * 3)(5, 10, 5)),
+                   (api.make_opts(3, 2, -1), rr)):
+        assert lib.tucker_holistic(ctypes.byref(A), rk, ctypes.byref(oo), 1,
+                                   ctypes.c_void_p(0x3000), U, None, None) == api.TK_EINVAL
+    assert lib.tucker_holistic(ctypes.byref(A), rr, ctypes.byref(o), 1, None, U, None,
+                               None) == api.TK_EINVAL
     # Algorithm 4: tol >= 0, q_max >= 1, plain precision only
     for tol, oo in ((-1.0, api.make_opts(3, 2, 5)), (0.5, api.make_opts(3, 0, 5)),
                     (0.5, api.make_opts(3, 2, 5, prec=api.TK_PREC_BF16_POWER))):
@@ -160,6 +168,13 @@ def test_workspace_size_is_host_only_and_monotone():
           for kind in range(4)}
     assert ws[api.TK_OMEGA_UNIFORM] > ws[api.TK_OMEGA_GAUSS]
     assert ws[api.TK_OMEGA_KR_GAUSS] == ws[api.TK_OMEGA_KR_UNIFORM] > ws[api.TK_OMEGA_UNIFORM]
+    # the holistic range finder keeps l_k columns: more than the plain call
+    o2 = api.make_opts(3, 2, 5)
+    for st in (0, 1):
+        hw = lib.tucker_holistic_workspace_size(ctypes.byref(t), rr, ctypes.byref(o2), st)
+        assert hw > lib.tucker_workspace_size(ctypes.byref(t), rr, ctypes.byref(o2), st) > 0
+    assert lib.tucker_holistic_workspace_size(ctypes.byref(t), rr,
+                                              ctypes.byref(api.make_opts(3, 2, -1)), 1) == 0
     bad = (ctypes.c_int * 3)(80, 5, 5)
     assert lib.tucker_workspace_size(ctypes.byref(_fake_tensor([80, 80, 80])), bad,
                                      ctypes.byref(api.make_opts(3, 2, 5)), 1) == 0
