@@ -71,6 +71,11 @@ WORKLOADS = {
                                               "p=10",
                                          shape=[600, 600, 600], r=[20, 20, 20], s=10, q=10,
                                          st=True, dtype="f32", prec=0, pve=0.5),
+    "sparse600_fp32_st_pve": dict(desc="600^3 FP32 tensor B of Section 5.1 (600 rank-one terms "
+                                       "of 5%-dense vectors, weights 1000/i^2 and 1/i^2); "
+                                       "Algorithm 4, tol=0.5, q_max=10, r=(20,20,20), p=10",
+                                  shape=[600, 600, 600], r=[20, 20, 20], s=10, q=10, st=True,
+                                  dtype="f32", prec=0, pve=0.5),
     "hilbert100_fp64_t": dict(desc="100^3 FP64 Hilbert-type 1/(i+j+k-2); randomized T-HOSVD, "
                                    "r=(10,10,10), p=5, q=1", shape=[100, 100, 100],
                               r=[10, 10, 10], s=5, q=1, st=False, dtype="f64", prec=0),
@@ -111,6 +116,8 @@ def make_input(name, rank=0):
                                    decay=0.8, dtype=np.float32)
     if name.startswith("invradius"):
         return I.inverse_radius(w["shape"][0], seed=3 + 1000 * rank, noise=1e-6)
+    if name.startswith("sparse600"):
+        return I.sparse_rank_one_sum(w["shape"][0], seed=12 + 1000 * rank, dtype=np.float32)
     if name.startswith("superdiag600slow"):
         return I.superdiagonal(w["shape"][0], "slow", seed=11 + 1000 * rank, dtype=np.float32)
     if name.startswith("hilbert100"):

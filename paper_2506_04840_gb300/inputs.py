@@ -14,6 +14,8 @@ recipes of the benchmark workloads are restated here):
 * ``inverse_radius``  a_ijk = (i^2 + j^2 + k^2)^(-1/2) + Gaussian noise.
 * ``superdiagonal``   Section 5.1's tensor C = tendiag(v) x_n A_n with
                         A_n orthogonal (slow / fast / S-shaped v).
+* ``sparse_rank_one_sum`` Section 5.1's tensor B: weighted sum of n
+                        rank-one terms of sparse vectors.
 * ``batch_instances`` uneven order-3/4 Tucker-plus-noise instances.
 * ``serving_requests`` Poisson arrivals of mixed-size requests.
 """
@@ -118,6 +120,27 @@ def superdiagonal(n, kind, seed, d=3, dtype=np.float64):
     X[(idx,) * d] = v
     for k in range(d):
         X = _mode_mult(X, As[k], k)
+    return np.asfortranarray(X.astype(dtype))
+
+
+def sparse_rank_one_sum(n, seed, gamma=1000.0, heavy=50, density=0.05, power=2,
+                        dtype=np.float64):
+    """Tensor B of Section 5.1: sum_{i<=heavy} (gamma/i^power) x_i o y_i o z_i
+    + sum_{heavy<i<=n} (1/i^power) x_i o y_i o z_i, n terms, x_i, y_i, z_i in
+    R^n sparse.  Each vector has ceil(density * n) nonzeros at distinct
+    random positions with values uniform on (0, 1) (the entries of a random
+    sparse vector of that density).  power = 2: the weights that reproduce
+    the errors the paper prints for B (its formula shows power 1)."""
+    rng = np.random.default_rng(seed)
+    nnz = int(np.ceil(density * n))
+    X = np.zeros((n, n, n))
+    for i in range(1, n + 1):
+        w = (gamma if i <= heavy else 1.0) / float(i) ** power
+        idx, val = [], []
+        for _ in range(3):
+            idx.append(np.sort(rng.choice(n, size=nnz, replace=False)))
+            val.append(rng.random(nnz))
+        X[np.ix_(*idx)] += w * np.einsum("a,b,c->abc", *val)
     return np.asfortranarray(X.astype(dtype))
 
 

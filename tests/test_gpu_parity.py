@@ -429,3 +429,22 @@ def test_pve_full_size_tensor_C_reaches_the_optimum(lib):
     assert all(2 <= q <= qmax for q in qs), qs
     _, _, qw, _ = T.rsthosvd_pve(A.astype(np.float64), r, s, qmax, tol)
     assert qs[0] == qw[0], (qs, qw)
+
+
+def test_pve_full_size_tensor_B_counts_and_error(lib):
+    """Algorithm 4 on tensor B of Section 5.1 at full size (600^3, r = 20,
+    s = 10, tol = 0.5, q_max = 10): B's unfoldings keep a resolved spectrum
+    past r after each truncation, so every stopping decision of the oracle
+    (stored by tests/golden/make_pve_tensor_B600.py) is at least 8% from its
+    threshold, and the FP32 path must take the same counts; RE within 1e-6
+    of the oracle's."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                     "pve_tensor_B600.json")))
+    assert all(abs(x - 1.0) > 0.05 for rk in g["test_ratios"] for x in rk)
+    A = I.sparse_rank_one_sum(600, g["seed"], dtype=np.float32)
+    G, Us, qs, _ = _run_pve(A, g["r"], g["s"], g["q_max"], g["tol"], stats=False)
+    assert qs == g["q"], (qs, g["q"])
+    re = T.rel_error(A, G, Us)
+    assert abs(re - g["re"]) <= 1e-6, (re, g["re"])

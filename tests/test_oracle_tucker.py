@@ -406,3 +406,31 @@ def test_holistic_reaches_the_tensor_C_optimum(st):
         G, Us, _ = T.holistic(A, [r] * 3, 10, 1, st=st)
         re = T.rel_error(A, G, Us)
         assert opt * (1 - 1e-9) <= re <= 1.01 * opt, (decay, re, opt)
+
+
+def test_table_5_3_tensor_B_rows_follow_squared_weights():
+    """Table 5.3's rows for tensor B (600^3, tol = 0.5): the oracle's
+    Algorithm 4 on the generator's B (weights gamma/i^2, 1/i^2) lands within
+    15% of the printed RE at r = 10, 30 and 50 (1.8e-2 down to 1.7e-6) and
+    picks counts of 2 or 3 per mode as printed; the formula's printed
+    weights (gamma/i, 1/i) miss the r = 10 entry by an order of magnitude."""
+    g = json.load(open(os.path.join(HERE, "golden", "table5_3_tensor_B.json")))
+
+    def re_of(A, G):
+        # the error identity ||A - A_hat||^2 = ||A||^2 - ||G||^2 (orthonormal
+        # factors, G the projection; pinned above) instead of a 600^3
+        # reconstruction; cancellation costs ~1e-5 of RE at RE = 1.7e-6
+        nA2 = float(np.sum(A * A))
+        return np.sqrt(max(nA2 - float(np.sum(G * G)), 0.0) / nA2)
+
+    A = I.sparse_rank_one_sum(g["n"], 12)
+    for row in g["rows"][::2]:
+        r = [row["r"]] * 3
+        G, Us, qs, _ = T.rsthosvd_pve(A, r, 10, 10, g["tol"])
+        re = re_of(A, G)
+        assert abs(re / row["re"] - 1) < 0.15, (row, re, qs)
+        assert all(q in (2, 3) for q in qs) and max(qs) == max(row["q"]), (row, qs)
+    del A
+    A1 = I.sparse_rank_one_sum(g["n"], 12, power=1)
+    G, Us, _, _ = T.rsthosvd_pve(A1, [10] * 3, 10, 10, g["tol"])
+    assert re_of(A1, G) > 5 * g["rows"][0]["re"]
