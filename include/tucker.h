@@ -240,6 +240,13 @@ tk_status tucker_rsthosvd(const tk_tensor* A, const int* r, const tk_opts* o, vo
 tk_status tucker_rsthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o, double tol,
                               void* core, void* const* U, int* q_out, tk_stats* st,
                               void* stream);
+/* Algorithm 2 (T-HOSVD) with the same PVE-controlled counts: every mode's
+ * sketch and power steps read A; arguments, errors and q_out as
+ * tucker_rsthosvd_pve.  The modes run one after the other (the host reads
+ * each step's Sigma back). */
+tk_status tucker_rthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o, double tol,
+                             void* core, void* const* U, int* q_out, tk_stats* st,
+                             void* stream);
 
 /* Relative error RE = ||A - G x_1 U_1 ... x_d U_d|| / ||A|| (Section 5,
  * definition of RE).  core, U as returned by tucker_r(s)thosvd (A's dtype);

@@ -175,6 +175,28 @@ def pve_threshold_index(r_k, l):
     return min(r_k, l - 1)
 
 
+def rthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, omega=OMEGA_GAUSS):
+    """Algorithm 2 with the PVE-controlled counts of Algorithm 4 (the
+    T-HOSVD version Section 3.3 names and Section 5.6 measures): every
+    mode's sketch and power steps act on A, the stopping test as in
+    ``rsthosvd_pve``; G = A x_1 U_1^T ... x_d U_d^T.
+    Returns (G, [U_k], [q_k], stats)."""
+    A = np.asarray(A, dtype=np.float64)
+    d = A.ndim
+    s = [s] * d if np.isscalar(s) else list(s)
+    Us, qs, stats = [], [], []
+    for k in range(d):
+        _, Uk, qk, stk = rsthosvd_pve(A, r, s, q_max, tol, seed=seed, tag=tag, rule=rule,
+                                      order=[k], omega=omega)
+        Us.append(Uk[k])
+        qs.append(qk[k])
+        stats.append(stk[k])
+    G = A
+    for k in range(d):
+        G = mode_product(G, Us[k].T, k)
+    return G, Us, qs, stats
+
+
 def rsthosvd_pve(A, r, s, q_max, tol, seed=0, tag=0, rule=SHIFT_PAPER, order=None,
                  omega=OMEGA_GAUSS):
     """Algorithm 4: Algorithm 3 with the power count of each mode chosen by

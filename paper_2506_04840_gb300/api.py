@@ -108,6 +108,10 @@ SIGNATURES = {
                                 ctypes.POINTER(tk_stats), c_void_p]),
     "tucker_holistic_workspace_size": (c_size_t, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
                                                   ctypes.POINTER(tk_opts), c_int]),
+    "tucker_rthosvd_pve": (c_int, [ctypes.POINTER(tk_tensor), ctypes.POINTER(c_int),
+                                   ctypes.POINTER(tk_opts), c_double, c_void_p,
+                                   ctypes.POINTER(c_void_p), ctypes.POINTER(c_int),
+                                   ctypes.POINTER(tk_stats), c_void_p]),
     "tucker_error": (c_int, [ctypes.POINTER(tk_tensor), c_void_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
     "tucker_to_bf16": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
@@ -287,16 +291,25 @@ def tucker_rsthosvd(A, dims, r, opts, core, U, stats=False, stream=None):
     return _hosvd("tucker_rsthosvd", A, dims, r, opts, core, U, stats, stream)
 
 
-def tucker_rsthosvd_pve(A, dims, r, opts, tol, core, U, stats=False, stream=None):
-    """Algorithm 4 (opts.q = q_max).  Returns (q_k list, stats dict or None)."""
+def _pve(name, A, dims, r, opts, tol, core, U, stats, stream):
     desc = tensor_desc(A, dims)
     st = tk_stats() if stats else None
     qs = (c_int * len(dims))()
-    _check(load().tucker_rsthosvd_pve(ctypes.byref(desc), _ranks(r), ctypes.byref(opts),
-                                      float(tol), _ptr(core), _ptr_array(U), qs,
-                                      ctypes.byref(st) if st is not None else None,
-                                      _stream(stream)), "tucker_rsthosvd_pve")
+    _check(getattr(load(), name)(ctypes.byref(desc), _ranks(r), ctypes.byref(opts), float(tol),
+                                 _ptr(core), _ptr_array(U), qs,
+                                 ctypes.byref(st) if st is not None else None, _stream(stream)),
+           name)
     return [int(x) for x in qs], (_stats_dict(st) if st is not None else None)
+
+
+def tucker_rsthosvd_pve(A, dims, r, opts, tol, core, U, stats=False, stream=None):
+    """Algorithm 4 (opts.q = q_max).  Returns (q_k list, stats dict or None)."""
+    return _pve("tucker_rsthosvd_pve", A, dims, r, opts, tol, core, U, stats, stream)
+
+
+def tucker_rthosvd_pve(A, dims, r, opts, tol, core, U, stats=False, stream=None):
+    """Algorithm 2 with Algorithm 4's counts.  Returns (q_k list, stats or None)."""
+    return _pve("tucker_rthosvd_pve", A, dims, r, opts, tol, core, U, stats, stream)
 
 
 def tucker_holistic(A, dims, r, opts, st, core, U, stats=False, stream=None):

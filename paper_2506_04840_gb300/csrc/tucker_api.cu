@@ -459,7 +459,13 @@ static tk_status run_hosvd(const tk_tensor* A, const int* r, const tk_opts* o, v
         const HosvdWs& wk = wm[k];
         cudaStream_t sk = k == 0 ? st : ss.s[k];
         if (k > 0) TK_TRY(cudaStreamWaitEvent(sk, ss.fork, 0));
-        tk_status e = factor_mode(p, k, A->data, p.xt, v, 0, 1, o->seed, o->tag, wk, sk, true);
+        // with the PVE test the host reads each step back, so the modes
+        // then run one after the other
+        PveCtl pve;
+        pve.tol = pve_tol;
+        tk_status e = factor_mode(p, k, A->data, p.xt, v, 0, 1, o->seed, o->tag, wk, sk, true,
+                                  pve_tol >= 0.0 ? &pve : nullptr);
+        if (q_out) q_out[k] = pve_tol >= 0.0 ? pve.q_used : p.q;
         if (e == TK_OK && p.xt != X_F64) e = from_cuda(polish(wk.Q, v.n, p.r[k], wk.small, wk.status, sk));
         if (e == TK_OK) e = from_cuda(launch_copy_matrix(wk.Q, v.n, qd[k], v.n, v.n, p.r[k], X_F64, sk));
         if (e == TK_OK) e = from_cuda(launch_copy_matrix(wk.Q, v.n, U[k], v.n, v.n, p.r[k], p.xt, sk));
@@ -885,6 +891,13 @@ tk_status tucker_rsthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o
                               void* stream) {
   if (!o || !(tol >= 0.0) || o->q < 1 || o->prec != TK_PREC_PLAIN) return TK_EINVAL;
   return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, true, tol, q_out);
+}
+
+tk_status tucker_rthosvd_pve(const tk_tensor* A, const int* r, const tk_opts* o, double tol,
+                             void* core, void* const* U, int* q_out, tk_stats* st,
+                             void* stream) {
+  if (!o || !(tol >= 0.0) || o->q < 1 || o->prec != TK_PREC_PLAIN) return TK_EINVAL;
+  return run_hosvd(A, r, o, core, U, st, (cudaStream_t)stream, false, tol, q_out);
 }
 
 tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const void* const* U,

@@ -140,9 +140,10 @@ def test_argument_validation_before_launch():
     # Algorithm 4: tol >= 0, q_max >= 1, plain precision only
     for tol, oo in ((-1.0, api.make_opts(3, 2, 5)), (0.5, api.make_opts(3, 0, 5)),
                     (0.5, api.make_opts(3, 2, 5, prec=api.TK_PREC_BF16_POWER))):
-        assert lib.tucker_rsthosvd_pve(ctypes.byref(A), rr, ctypes.byref(oo), tol,
-                                       ctypes.c_void_p(0x3000), U, None, None,
-                                       None) == api.TK_EINVAL
+        for name in ("tucker_rsthosvd_pve", "tucker_rthosvd_pve"):
+            assert getattr(lib, name)(ctypes.byref(A), rr, ctypes.byref(oo), tol,
+                                      ctypes.c_void_p(0x3000), U, None, None,
+                                      None) == api.TK_EINVAL
     bad = _fake_tensor([10, 0, 10])
     assert lib.tucker_error(ctypes.byref(bad), ctypes.c_void_p(0x3000), rr, U,
                             ctypes.c_void_p(0x3000), None) == api.TK_EINVAL

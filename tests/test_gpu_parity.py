@@ -356,14 +356,15 @@ def test_precision_form_error_within_one_percent_at_full_size(lib):
     assert re_b <= 1.01 * re_p, (re_b, re_p)
 
 
-def _run_pve(A, r, s, qmax, tol, stats=True):
+def _run_pve(A, r, s, qmax, tol, stats=True, st_form=True):
     import torch
     d, dims = A.ndim, list(A.shape)
     Ad = api.to_device(A, np.float32)
     core = torch.empty(int(np.prod(r)), dtype=torch.float32, device="cuda")
     U = [torch.empty(dims[k] * r[k], dtype=torch.float32, device="cuda") for k in range(d)]
     opts = api.make_opts(d, qmax, s)
-    qs, st = api.tucker_rsthosvd_pve(Ad, dims, r, opts, tol, core, U, stats=stats)
+    fn = api.tucker_rsthosvd_pve if st_form else api.tucker_rthosvd_pve
+    qs, st = fn(Ad, dims, r, opts, tol, core, U, stats=stats)
     torch.cuda.synchronize()
     G = api.from_device(core, r)
     Us = [api.from_device(U[k], [dims[k], r[k]]) for k in range(d)]
@@ -448,3 +449,37 @@ def test_pve_full_size_tensor_B_counts_and_error(lib):
     assert qs == g["q"], (qs, g["q"])
     re = T.rel_error(A, G, Us)
     assert abs(re - g["re"]) <= 1e-6, (re, g["re"])
+
+
+def test_thosvd_pve_limits_equal_algorithm2_bitwise(lib):
+    """Algorithm 2 with the PVE counts: tol -> infinity is Algorithm 2 with
+    q = 1 and tol = 0 with q = q_max, bitwise against tucker_rthosvd."""
+    A = I.tucker_plus_noise([70, 50, 40], [6, 6, 6], 31, noise=1e-3, dtype=np.float32)
+    r, s, qmax = [5, 5, 5], 5, 4
+    for tol, q in ((1e300, 1), (0.0, qmax)):
+        G, Us, qs, _ = _run_pve(A, r, s, qmax, tol, stats=False, st_form=False)
+        Gr, Ur, _ = run_hosvd(A, r, s, q, st=False, stats=False)
+        assert qs == [q] * 3
+        assert np.array_equal(G, Gr)
+        for a, b in zip(Us, Ur):
+            assert np.array_equal(a, b)
+
+
+def test_thosvd_pve_full_size_tensor_C_counts(lib):
+    """Algorithm 2 with the PVE counts on tensor C at 600^3 (r = 20, s = 10,
+    tol = 0.5, q_max = 10): every mode reads A, whose unfoldings all have
+    the resolved spectrum v^2, so every decision of the oracle is at least
+    12% from its threshold and the counts must agree; RE within 1e-6."""
+    A = I.superdiagonal(600, "slow", seed=11, dtype=np.float32)
+    r, s, qmax, tol = [20, 20, 20], 10, 10, 0.5
+    Gw, Uw, qw, stw = T.rthosvd_pve(A.astype(np.float64), r, s, qmax, tol)
+    for k in range(3):
+        prev = np.zeros_like(stw[k]["sigma_hist"][0])
+        for sig in stw[k]["sigma_hist"]:
+            thr = tol * sig[T.pve_threshold_index(r[k], len(sig))]
+            assert abs(np.max(np.abs(sig[:r[k]] - prev[:r[k]])) - thr) > 0.1 * thr
+            prev = sig
+    G, Us, qs, _ = _run_pve(A, r, s, qmax, tol, stats=False, st_form=False)
+    assert qs == qw, (qs, qw)
+    re_w, re_g = T.rel_error(A, Gw, Uw), T.rel_error(A, G, Us)
+    assert abs(re_g - re_w) <= 1e-6, (re_g, re_w)

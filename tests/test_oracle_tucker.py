@@ -434,3 +434,25 @@ def test_table_5_3_tensor_B_rows_follow_squared_weights():
     A1 = I.sparse_rank_one_sum(g["n"], 12, power=1)
     G, Us, _, _ = T.rsthosvd_pve(A1, [10] * 3, 10, 10, g["tol"])
     assert re_of(A1, G) > 5 * g["rows"][0]["re"]
+
+
+def test_thosvd_pve_limits_and_tensor_C():
+    """Algorithm 2 with the PVE counts: tol -> infinity and tol = 0 are
+    Algorithm 2 with q = 1 and q = q_max result for result; with tol = 0.5
+    tensor C (every mode sees the full spectrum v) reaches the closed-form
+    optimum within 1% with counts >= 2."""
+    A = _pve_tensor()
+    r, s, qmax = [4, 3, 3], 3, 4
+    for tol, q in ((1e300, 1), (0.0, qmax)):
+        G, Us, qs, _ = T.rthosvd_pve(A, r, s, qmax, tol)
+        Gr, Ur, _ = T.rthosvd(A, r, s, q)
+        assert qs == [q] * 3
+        assert np.array_equal(G, Gr)
+        for a, b in zip(Us, Ur):
+            assert np.array_equal(a, b)
+    n, rk = 60, 10
+    A = I.superdiagonal(n, "slow", seed=14)
+    opt = _closed_form(I.superdiagonal_values(n, "slow"), rk)
+    G, Us, qs, _ = T.rthosvd_pve(A, [rk] * 3, 10, 10, 0.5)
+    assert opt * (1 - 1e-9) <= T.rel_error(A, G, Us) <= 1.01 * opt
+    assert all(2 <= q <= 10 for q in qs), qs
