@@ -766,12 +766,17 @@ constexpr int kRegRK = 4;                    // float4 chunks per lane per colum
 constexpr int kRegCPW = 4;                   // columns per warp
 constexpr int kRegRows = 4 * 32 * kRegRK;    // 512
 constexpr int kRegCols = 16 * kRegCPW;       // 64
+// Long-mode variant: eight float4 chunks per lane (1024 rows) with two
+// column slots per warp (l <= 32): the same 64 register floats per thread.
+constexpr int kRegRK2 = 8;
+constexpr int kRegRows2 = 4 * 32 * kRegRK2;  // 1024
+constexpr int kRegCols2 = 32;
 
 __host__ __device__ __forceinline__ int reg_ld(int64_t m) { return (int)((m + 3) / 4 * 4); }
 
-template <int CPW>
+template <int CPW, int RK = kRegRK>
 struct RegCols {
-  float y[CPW][4 * kRegRK];
+  float y[CPW][4 * RK];
   int lane, warp;
   __device__ __forceinline__ RegCols() : lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {}
   __device__ __forceinline__ int col(int s) const { return warp + 16 * s; }
@@ -780,7 +785,7 @@ struct RegCols {
 
   __device__ __forceinline__ void load_col(int s, const float* c, int md) {
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k) {
+    for (int k = 0; k < RK; ++k) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (has(k, md)) v = *reinterpret_cast<const float4*>(c + 4 * (lane + 32 * k));
       y[s][4 * k] = v.x; y[s][4 * k + 1] = v.y; y[s][4 * k + 2] = v.z; y[s][4 * k + 3] = v.w;
@@ -788,7 +793,7 @@ struct RegCols {
   }
   __device__ __forceinline__ void store_col(int s, float* c, int md) const {
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k)
+    for (int k = 0; k < RK; ++k)
       if (has(k, md))
         *reinterpret_cast<float4*>(c + 4 * (lane + 32 * k)) =
             make_float4(y[s][4 * k], y[s][4 * k + 1], y[s][4 * k + 2], y[s][4 * k + 3]);
@@ -808,7 +813,7 @@ struct RegCols {
 #pragma unroll
     for (int s = 0; s < CPW; ++s) d[s] = 0.f;
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k) {
+    for (int k = 0; k < RK; ++k) {
       if (!has(k, md)) continue;
       const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
       const float ve[4] = {v4.x, v4.y, v4.z, v4.w};
@@ -825,7 +830,7 @@ struct RegCols {
 #pragma unroll
     for (int s = 0; s < CPW; ++s) d[s] *= -tj;
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k) {
+    for (int k = 0; k < RK; ++k) {
       if (!has(k, md)) continue;
       const float4 v4 = *reinterpret_cast<const float4*>(v + 4 * (lane + 32 * k));
       const float ve[4] = {v4.x, v4.y, v4.z, v4.w};
@@ -843,7 +848,7 @@ struct RegCols {
                                         int rr, int rc) {
     float s0 = 0.f, s1 = 0.f, mine = 0.f;
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k)
+    for (int k = 0; k < RK; ++k)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = row(k, e);
@@ -868,7 +873,7 @@ struct RegCols {
       scal = __fdividef(1.f, alpha - beta);
     }
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k)
+    for (int k = 0; k < RK; ++k)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = row(k, e);
@@ -917,7 +922,7 @@ struct RegCols {
       const int c = col(s);
       const int cs = c < nb ? (perm ? perm[c] : c) : 0;
 #pragma unroll
-      for (int k = 0; k < kRegRK; ++k)
+      for (int k = 0; k < RK; ++k)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int r = row(k, e);
@@ -931,7 +936,7 @@ struct RegCols {
     float best = -1.f, bval = 0.f;
     int bi = 0;
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k)
+    for (int k = 0; k < RK; ++k)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = row(k, e);
@@ -952,7 +957,7 @@ struct RegCols {
   template <typename O>
   __device__ __forceinline__ void store_out(int s, O* out, int64_t ldo, int m, float sgn) const {
 #pragma unroll
-    for (int k = 0; k < kRegRK; ++k)
+    for (int k = 0; k < RK; ++k)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = row(k, e);
@@ -1072,9 +1077,9 @@ __host__ __device__ __forceinline__ size_t reg_one_smem(int64_t n, int l) {
   return ((size_t)reg_ld(n) * l + 2 * (size_t)l * l + 3 * (size_t)l) * sizeof(float);
 }
 
-// [Q, Sigma] = svd(Y) for n <= 512, l <= 64 (FP32 working precision), or
+// [Q, Sigma] = svd(Y) for n <= 128 RK, l <= 16 CPW (FP32 working precision), or
 // with basis_only an orthonormal basis of span(Y); as svd_one_body.
-template <int CPW>
+template <int CPW, int RK = kRegRK>
 __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n, int l,
                                              double* __restrict__ Q, double* __restrict__ sigma,
                                              int shift_rule, int update_shift, int basis_only,
@@ -1113,7 +1118,7 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
   if (!basis_only)
     for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
   __syncthreads();
-  RegCols<CPW> R;
+  RegCols<CPW, RK> R;
   R.qr(A, md, l, ts, basis_only ? nullptr : J, l, 1);   // J = R^T
   if (basis_only) {
     // only span(Y) is needed: Q = Q_h
@@ -1149,14 +1154,14 @@ __device__ __forceinline__ void svd_reg_body(const double* __restrict__ Y, int n
     shift_update((double)sg[perm[l - 1]] / scale, shift_rule, alpha, alpha_hist, sigl_hist);
 }
 
-template <int CPW>
+template <int CPW, int RK = kRegRK>
 __global__ void __launch_bounds__(kRegThreads)
 k_svd_reg(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
           double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
           double* __restrict__ alpha, double* __restrict__ alpha_hist,
           double* __restrict__ sigl_hist, int* __restrict__ status) {
-  svd_reg_body<CPW>(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha, alpha_hist,
-                    sigl_hist, status);
+  svd_reg_body<CPW, RK>(Y, n, l, Q, sigma, shift_rule, update_shift, basis_only, alpha,
+                        alpha_hist, sigl_hist, status);
 }
 
 // TSQR leaf (MB <= 512 rows, a multiple of 32): reflectors to V (ld MB), tau,
@@ -1287,14 +1292,15 @@ static size_t leafq_smem(int MB, int l, size_t es) {
 }
 
 // Pb == 1 selects the single-CTA path (MB = n).  FP32 problems with n <= 512
-// and l <= 64 take the register-resident single-CTA kernel; above the
+// and l <= 64, or n <= 1024 and l <= 32, take the register-resident
+// single-CTA kernel; above the
 // single-CTA shared-memory budget, FP32 TSQR takes the register-resident
 // kernels when the leaves (<= 512 rows) and the root (Pb l <= 512 rows) fit.
 // (The work-list svd follows the same single-CTA choice, so batched and
 // single calls run the same kernels.)
 bool svd_reg_fits(int64_t n, int l, bool fp64) {
-  return !fp64 && l >= 1 && l <= kRegCols && n >= l && n <= kRegRows &&
-         reg_one_smem(n, l) <= kSmemBudget;
+  if (fp64 || l < 1 || n < l || reg_one_smem(n, l) > kSmemBudget) return false;
+  return (n <= kRegRows && l <= kRegCols) || (n <= kRegRows2 && l <= kRegCols2);
 }
 
 SmallPlan small_plan(int64_t n, int l, bool fp64) {
@@ -1359,6 +1365,15 @@ static cudaError_t reg_go(const SmallPlan& pl, const double* Y, int64_t n, doubl
   const int l = pl.l, MB = pl.MB, Pb = pl.Pb;
   if (Pb == 1) {
     count_kernels(1);
+    if (n > kRegRows) {
+      if constexpr (CPW == 2) {
+        k_svd_reg<2, kRegRK2><<<1, kRegThreads, reg_one_smem(n, l), st>>>(
+            Y, (int)n, l, Q, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
+            alpha_hist, sigl_hist, status);
+        return cudaGetLastError();
+      }
+      return cudaErrorInvalidValue;
+    }
     k_svd_reg<CPW><<<1, kRegThreads, reg_one_smem(n, l), st>>>(
         Y, (int)n, l, Q, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
         alpha_hist, sigl_hist, status);
@@ -1399,6 +1414,7 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
     cudaFuncSetAttribute(k_leaf_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_svd_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_svd_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_svd_reg<2, kRegRK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_leaf_qr_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_leaf_qr_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_root_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1455,14 +1471,14 @@ __global__ void k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __r
   }
 }
 
-template <int CPW>
+template <int CPW, int RK = kRegRK>
 __global__ void __launch_bounds__(kRegThreads)
 k_svd_batch_reg(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
                 uint32_t total) {
   for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
     const SvdJob J = jobs[batch_job(start, njobs, b)];
-    svd_reg_body<CPW>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
-                 J.alpha, J.ahist, J.shist, J.status);
+    svd_reg_body<CPW, RK>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift,
+                          J.basis_only, J.alpha, J.ahist, J.shist, J.status);
     __syncthreads();
   }
 }
@@ -1489,8 +1505,11 @@ k_polish_batch(const PolishJob* __restrict__ jobs, const uint32_t* __restrict__ 
   }
 }
 
+// 0: not register-resident; 2 / 4: column slots per warp (512 rows); 3: two
+// slots, 1024 rows.
 int svd_variant(int64_t n, int l, bool fp64) {
   if (!svd_reg_fits(n, l, fp64)) return 0;
+  if (n > kRegRows) return 3;
   return l <= 32 ? 2 : 4;
 }
 int svd_threads(int64_t n, int l, bool fp64) {
@@ -1516,6 +1535,8 @@ void batch_kernels_init() {
   cudaFuncSetAttribute(k_svd_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_svd_batch_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_svd_batch_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_svd_batch_reg<2, kRegRK2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
   cudaFuncSetAttribute(k_gram_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_polish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   attr = true;
@@ -1530,6 +1551,7 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
       // run 512 threads, no other svd does
       if (b.tile == kRegThreads) {
         if (b.flag == 2) return run_batch(k_svd_batch_reg<2>, b, kRegThreads, st);
+        if (b.flag == 3) return run_batch(k_svd_batch_reg<2, kRegRK2>, b, kRegThreads, st);
         return run_batch(k_svd_batch_reg<4>, b, kRegThreads, st);
       }
       return run_batch(k_svd_batch<float>, b, b.tile, st);

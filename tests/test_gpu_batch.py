@@ -148,3 +148,17 @@ def test_batch_row_split_products_bitwise(lib):
     outs, _ = _run_batch(insts, True)
     for i, (A, r, s, q) in enumerate(insts):
         assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+
+
+def test_batch_long_mode_register_svd_bitwise(lib):
+    """Items whose first mode has 600 or 1000 rows with l <= 32: the batch
+    runs the long-mode register svd body, bitwise as the single calls."""
+    insts = []
+    for i, shape in enumerate([(600, 30, 20), (1000, 24, 16), (700, 20, 18)]):
+        r = [12, 5, 4]
+        A = I.tucker_plus_noise(list(shape), [14, 6, 5], 60 + i, noise=1e-3,
+                                noise_mode="relative", dtype=np.float32)
+        insts.append((A, r, 6, 2))
+    outs, _ = _run_batch(insts, True)
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
