@@ -46,6 +46,7 @@ extern "C" {
 #define TK_MAX_D 8     /* largest supported tensor order d */
 #define TK_MAX_Q 32    /* largest power-iteration count q */
 #define TK_MAX_L 128   /* largest sketch width l_k = r_k + s_k */
+#define TK_ORDER_DESCENDING (-2)   /* tk_opts.order[0]: modes by non-increasing n_k */
 
 typedef enum {
   TK_OK = 0,
@@ -117,7 +118,10 @@ typedef struct {
   tk_shift shift;
   tk_precision prec;
   int order[TK_MAX_D];     /* ST-HOSVD processing order (0-based modes, a
-                              permutation); order[0] < 0 means 0..d-1 */
+                              permutation); order[0] = TK_ORDER_DESCENDING:
+                              non-increasing n_k (Section 3.2, ties in
+                              ascending mode index); other order[0] < 0:
+                              0..d-1 */
   void* workspace;         /* device workspace or NULL (then the call
                               allocates and frees it on `stream`) */
   size_t workspace_bytes;

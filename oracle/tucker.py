@@ -168,6 +168,12 @@ def rsthosvd(A, r, s, q, seed=0, tag=0, rule=SHIFT_PAPER, order=None, bf16_power
     return G, Us, stats
 
 
+def descending_order(shape):
+    """The processing order of Section 3.2: n_{p_1} >= ... >= n_{p_d}, ties
+    in ascending mode index."""
+    return sorted(range(len(shape)), key=lambda k: (-shape[k], k))
+
+
 def pve_threshold_index(r_k, l):
     """0-based index of the estimate the Algorithm 4 test scales tol by: the
     (r_k+1)-th (the first one past the kept rank), or the last one when the

@@ -23,6 +23,7 @@ TK_F64, TK_F32, TK_BF16 = 0, 1, 2
 TK_SHIFT_PAPER, TK_SHIFT_NONE = 0, 1
 TK_PREC_PLAIN, TK_PREC_BF16_POWER = 0, 1
 TK_OMEGA_GAUSS, TK_OMEGA_UNIFORM, TK_OMEGA_KR_GAUSS, TK_OMEGA_KR_UNIFORM = 0, 1, 2, 3
+TK_ORDER_DESCENDING = -2   # make_opts(order="descending"): modes by non-increasing n_k
 
 c_int, c_int64, c_uint64, c_uint32, c_double = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                                  ctypes.c_uint32, ctypes.c_double)
@@ -210,6 +211,10 @@ def make_opts(d, q, s, seed=0, tag=0, shift=TK_SHIFT_PAPER, prec=TK_PREC_PLAIN, 
     o.omega = int(omega)
     if order is None:
         o.order[0] = -1
+    elif isinstance(order, str):
+        if order != "descending":
+            raise ValueError(order)
+        o.order[0] = TK_ORDER_DESCENDING
     else:
         for k, m in enumerate(order):
             o.order[k] = int(m)

@@ -98,7 +98,16 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     if (p.r[k] == p.n[k] && !full_ok) return TK_EINVAL;      // Problem 2.1: r_k < n_k
     if (p.s[k] < 0) return TK_EINVAL;
   }
-  if (o->order[0] < 0) {
+  if (o->order[0] == TK_ORDER_DESCENDING) {
+    // the processing order of Section 3.2: n_{p_1} >= n_{p_2} >= ... >= n_{p_d}
+    // (ties in ascending mode index)
+    p.order.resize(p.d);
+    for (int k = 0; k < p.d; ++k) p.order[k] = k;
+    std::stable_sort(p.order.begin(), p.order.end(),
+                     [&](int a, int b) { return p.n[a] > p.n[b]; });
+    if (!st)
+      for (int k = 0; k < p.d; ++k) p.order[k] = k;   // T-HOSVD: order is immaterial
+  } else if (o->order[0] < 0) {
     p.order.resize(p.d);
     for (int k = 0; k < p.d; ++k) p.order[k] = k;
   } else {

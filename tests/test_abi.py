@@ -161,6 +161,10 @@ def test_workspace_size_is_host_only_and_monotone():
                                    ctypes.byref(api.make_opts(3, 3, 5,
                                                               prec=api.TK_PREC_BF16_POWER)), 1)
     assert bf > big            # the bfloat16 shadow
+    # Section 3.2's order is a valid request
+    assert lib.tucker_workspace_size(ctypes.byref(_fake_tensor([40, 60, 80])), rr,
+                                     ctypes.byref(api.make_opts(3, 2, 5, order="descending")),
+                                     1) > 0
     # a stored test matrix needs W even without power steps; Khatri-Rao
     # factors add their scratch
     t = _fake_tensor([80, 80, 80])

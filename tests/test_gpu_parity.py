@@ -532,3 +532,24 @@ def test_long_mode_register_svd_matches_oracle(lib, shape, r, s):
     for U in Us[1:]:
         U = np.asarray(U, dtype=np.float64)
         assert np.abs(U.T @ U - np.eye(U.shape[1])).max() <= 1e-6
+
+
+def test_descending_processing_order_matches_explicit_order(lib):
+    """order[0] = TK_ORDER_DESCENDING processes the modes by non-increasing
+    n_k (Section 3.2): bitwise the explicit permutation, reported in the
+    stats, and the oracle's Algorithm 3 in that order; a shape already in
+    that order keeps the natural (rotated-layout) path."""
+    A = I.tucker_plus_noise([30, 44, 52], [7, 7, 7], 5, noise=1e-3, decay=0.85,
+                            dtype=np.float32)
+    r, s, q = [5, 5, 5], 4, 2
+    G, Us, info = run_hosvd(A, r, s, q, order="descending")
+    Ge, Ue, _ = run_hosvd(A, r, s, q, order=[2, 1, 0])
+    assert info["order"][:3] == [2, 1, 0]
+    assert np.array_equal(G, Ge) and all(np.array_equal(a, b) for a, b in zip(Us, Ue))
+    Gw, Uw, _ = T.rsthosvd(A, r, s, q, order=T.descending_order(A.shape))
+    assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gw, Uw)) <= 1e-6
+    B = np.asfortranarray(np.transpose(A, (2, 1, 0)))     # 52 x 44 x 30
+    G1, U1, i1 = run_hosvd(B, r, s, q, order="descending")
+    G2, U2, _ = run_hosvd(B, r, s, q)
+    assert i1["order"][:3] == [0, 1, 2]
+    assert np.array_equal(G1, G2) and all(np.array_equal(a, b) for a, b in zip(U1, U2))

@@ -456,3 +456,19 @@ def test_thosvd_pve_limits_and_tensor_C():
     G, Us, qs, _ = T.rthosvd_pve(A, [rk] * 3, 10, 10, 0.5)
     assert opt * (1 - 1e-9) <= T.rel_error(A, G, Us) <= 1.01 * opt
     assert all(2 <= q <= 10 for q in qs), qs
+
+
+def test_descending_processing_order():
+    """Section 3.2's processing order: n_{p_1} >= n_{p_2} >= ... >= n_{p_d}
+    (its example 600 x 700 x 800 gives (3, 2, 1)); ties keep the lower mode
+    first."""
+    assert T.descending_order((600, 700, 800)) == [2, 1, 0]
+    assert T.descending_order((5, 5, 3)) == [0, 1, 2]
+    assert T.descending_order((3, 9, 9, 1)) == [1, 2, 0, 3]
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        shape = tuple(int(x) for x in rng.integers(1, 6, size=int(rng.integers(1, 7))))
+        p = T.descending_order(shape)
+        assert sorted(p) == list(range(len(shape)))
+        for a, b in zip(p, p[1:]):
+            assert shape[a] > shape[b] or (shape[a] == shape[b] and a < b)
