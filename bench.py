@@ -108,18 +108,61 @@ NCU_TRAFFIC = {
 }
 
 
+# ---- ranks (one process per GPU; replicas, no data-path collective) ----
+def rank_seed(base, rank):
+    """Each rank's replica draws its own content: seed base + 1000 rank."""
+    return base + 1000 * rank
+
+
+def dist_init(world, local):
+    """The process group of a torchrun launch (NCCL), or None for one GPU.
+    It carries only barriers and the timing reductions below."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """The whole job's time: the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist, device="cuda"):
+    """Units all ranks processed."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_value(units_all_ranks, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (ms)."""
+    return units_all_ranks / (ms / 1e3)
+
+
 def make_input(name, rank=0):
     from paper_2506_04840_gb300 import inputs as I
     w = WORKLOADS[name]
     if name.startswith("tucker400"):
-        return I.tucker_plus_noise(w["shape"], w["r"], seed=2 + 1000 * rank, noise=1e-4,
+        return I.tucker_plus_noise(w["shape"], w["r"], seed=rank_seed(2, rank), noise=1e-4,
                                    decay=0.8, dtype=np.float32)
     if name.startswith("invradius"):
-        return I.inverse_radius(w["shape"][0], seed=3 + 1000 * rank, noise=1e-6)
+        return I.inverse_radius(w["shape"][0], seed=rank_seed(3, rank), noise=1e-6)
     if name.startswith("sparse600"):
-        return I.sparse_rank_one_sum(w["shape"][0], seed=12 + 1000 * rank, dtype=np.float32)
+        return I.sparse_rank_one_sum(w["shape"][0], seed=rank_seed(12, rank), dtype=np.float32)
     if name.startswith("superdiag600slow"):
-        return I.superdiagonal(w["shape"][0], "slow", seed=11 + 1000 * rank, dtype=np.float32)
+        return I.superdiagonal(w["shape"][0], "slow", seed=rank_seed(11, rank), dtype=np.float32)
     if name.startswith("hilbert100"):
         return I.hilbert(w["shape"])
     raise KeyError(name)
@@ -331,9 +374,10 @@ def run_batch_workload(args, w, local, world):
     from paper_2506_04840_gb300 import api
     from paper_2506_04840_gb300 import inputs as I
     torch.cuda.set_device(local)
+    dist = dist_init(world, local)
     api.load()
     rank = int(os.environ.get("RANK", "0"))
-    specs = I.batch_specs(w["count"], w["seed"] + 1000 * rank)
+    specs = I.batch_specs(w["count"], rank_seed(w["seed"], rank))
     Ads, cores, Us, rels, items = [], [], [], [], []
     for i, (shape, ranks, sub) in enumerate(specs):
         A = I.tucker_plus_noise_device(shape, ranks, sub, noise=1e-3)
@@ -355,6 +399,8 @@ def run_batch_workload(args, w, local, world):
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -363,9 +409,11 @@ def run_batch_workload(args, w, local, world):
         api.tucker_batch_run(h, stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     clk = clocks.stop()
-    value = world * w["count"] * args.steps / (ms / 1e3)
+    value = job_value(world * w["count"] * args.steps, ms)
     re = np.array([float(r.item()) for r in rels])
 
     # per-kind breakdown: the same launches without the graph, profiled
@@ -433,10 +481,12 @@ def run_batch_workload(args, w, local, world):
     e2e_run(2)
     torch.cuda.synchronize()
     ne2e = max(3, args.steps // 2)
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     e2e_run(ne2e)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ne2e
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist) / ne2e
     api.tucker_batch_destroy(h)
     api.tucker_batch_destroy(h2)
     del Ads2
@@ -444,6 +494,8 @@ def run_batch_workload(args, w, local, world):
     dom, roof = _roofline(prof, pk, pk_src)
     roof["traffic"] = NCU_TRAFFIC.get((args.workload, dom))
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return 0
     line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -456,7 +508,8 @@ def run_batch_workload(args, w, local, world):
                        "l2": "inputs (%.1f GB) larger than L2 (129 MB)"
                              % (sum(A.numel() * 4 for A in Ads) / 1e9)},
             "roofline": roof, "kernels": _kernels(prof, 1),
-            "e2e": {"value": w["count"] / e2e_s, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": world * w["count"] / e2e_s, "unit": "tensors/s",
+                    "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "host_memory": "pinned" if pinned else "pageable (pinning failed)",
                     "overlap": "step k+1's host->device copy overlaps step k's compute "
@@ -467,6 +520,8 @@ def run_batch_workload(args, w, local, world):
         line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),
                                 "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -476,11 +531,12 @@ def run_serve_workload(args, w, local, world):
     from paper_2506_04840_gb300 import api
     from paper_2506_04840_gb300 import inputs as I
     torch.cuda.set_device(local)
+    dist = dist_init(world, local)
     api.load()
     rank = int(os.environ.get("RANK", "0"))
     duration = args.duration if args.duration else w["duration"]
     count = int(w["rate"] * duration)
-    reqs = I.serving_requests(count, w["seed"] + 1000 * rank, rate=w["rate"])
+    reqs = I.serving_requests(count, rank_seed(w["seed"], rank), rate=w["rate"])
     hil = {}
     # warm-up: a few requests through a scratch server
     srv = api.tucker_server_create(0, 256, api.TK_SHIFT_PAPER)
@@ -514,6 +570,8 @@ def run_serve_workload(args, w, local, world):
     api.tucker_profile_enable(True)
     clocks = Clocks(local)
     clocks.start()
+    if dist:
+        dist.barrier()   # the ranks' arrival streams start together
     t_start = api.tucker_server_clock(srv)
     comps, lag, rels = [], [], {}
     for i, rq in enumerate(reqs):
@@ -537,10 +595,14 @@ def run_serve_workload(args, w, local, world):
     api.tucker_server_destroy(srv)
     lat = np.array([c["done_s"] - c["submit_s"] for c in comps]) * 1e3
     span = max(c["done_s"] for c in comps) - min(c["submit_s"] for c in comps)
-    value = len(comps) / span
+    # every rank serves its own arrival stream: the job completes the sum of
+    # the ranks' requests over the slowest rank's span (latencies: rank 0's)
+    value = sum_over_ranks(len(comps), dist) / max_over_ranks(span, dist)
     re = np.array([float(r.item()) for r in rels.values()])
     bad = sum(1 for c in comps if c["status"] != 0)
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return 0
     line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
             "steps": len(comps), "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / value,
@@ -564,6 +626,8 @@ def run_serve_workload(args, w, local, world):
         line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),
                                 "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -594,10 +658,7 @@ def main():
     import torch
     from paper_2506_04840_gb300 import api
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = dist_init(world, local)
     api.load()
 
     A = make_input(args.workload, rank)
@@ -656,12 +717,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     rel_err = float(rel.item())
-    value = world * args.steps / (ms / 1e3)
+    value = job_value(world * args.steps, ms)
 
     # ---- end to end through the public API, host buffers -----------------
     pin = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=ndt).ravel(order="F"))).pin_memory()
@@ -710,12 +768,8 @@ def main():
     e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * args.steps / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), dist)
+    e2e_value = job_value(world * args.steps, ms_e2e)
 
     # ---- roofline of the dominant kernel ----------------------------------
     pk, pk_src = peaks()
