@@ -163,8 +163,11 @@ tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t 
  * solved by the svd in the input's precision, sorted and sign-fixed like
  * the svd results) gives the core, and U_k = Q_k V_k.  Modes in natural order
  * (o->order ignored); plain precision only (TK_EINVAL otherwise); any
- * tk_omega kind.  Outputs as tucker_rsthosvd; stats describe the range
- * finder (l_k, its shifts and Sigma). */
+ * tk_omega kind.  Outputs, workspace (tucker_holistic_workspace_size bytes,
+ * or allocated on `stream` when o->workspace is NULL) and errors as
+ * tucker_rsthosvd: TK_EINVAL for r_k >= n_k or s_k < 0, TK_ENOTIMPL when an
+ * l_k exceeds TK_MAX_L.  stats describe the range finder (l_k, its shifts
+ * and Sigma).  Appendices A and B of the paper. */
 tk_status tucker_holistic(const tk_tensor* A, const int* r, const tk_opts* o, int st, void* core,
                           void* const* U, tk_stats* stats, void* stream);
 /* Bytes of device workspace tucker_holistic needs; 0 for invalid arguments. */
