@@ -3,9 +3,12 @@
 A step is one pass of the whole path over one synthetic tensor: sketch,
 q adaptively shifted power steps, the small SVDs and shift updates, the TTM
 shrink of every mode (randomized ST-HOSVD with adaptive shifts) and the
-relative-error pass.  Default workload: a 400 x 400 x 400 FP32 tensor
-G x_1 U_1 x_2 U_2 x_3 U_3 + E (G 20^3 N(0,1) scaled by 0.8^(i+j+k), Haar U_k,
-E at 1e-4 ||G||/sqrt(N)), Tucker rank (20,20,20), oversampling 10, q = 2.
+relative-error pass.  Default workload: the 1000 x 1000 x 1000 FP32 tensor
+a_ijk = (i^2+j^2+k^2)^(-1/2) plus Gaussian noise at 1e-6 relative, Tucker
+rank (50,50,50), oversampling 10, q = 3, in the precision form (power steps
+1..q-1 read a bfloat16 copy, the sketch, step q, the TTM and the error read
+FP32); the plain FP32 form runs on the same tensor beside it, and a short
+serving session (Poisson arrivals) reports p50/p99 latency from arrival.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...      # the FP64 CPU oracle, host cores
@@ -55,11 +58,12 @@ WORKLOADS = {
     "invradius1000_fp32_st": dict(desc="1000^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise; randomized "
                                        "ST-HOSVD, r=(50,50,50), p=10, q=3, plain FP32",
                                   shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3, st=True,
-                                  dtype="f32", prec=0),
+                                  dtype="f32", prec=0, oracle_slices=64),
     "invradius1000_bf16power_st": dict(desc="as invradius1000_fp32_st with power steps 1..q-1 on "
                                             "a bfloat16 copy (precision form)",
                                        shape=[1000, 1000, 1000], r=[50, 50, 50], s=10, q=3,
-                                       st=True, dtype="f32", prec=1),
+                                       st=True, dtype="f32", prec=1,
+                                       companion="invradius1000_fp32_st", oracle_slices=64),
     "invradius512_bf16power_st": dict(desc="512^3 FP32 (i^2+j^2+k^2)^-1/2 + 1e-6 noise, r=(50,50,50), "
                                            "p=10, q=3, precision form (a small profiling case)",
                                       shape=[512, 512, 512], r=[50, 50, 50], s=10, q=3, st=True,
@@ -94,17 +98,17 @@ WORKLOADS.update({
                              kind="serve", rate=200.0, duration=60.0, seed=5, s=10,
                              dtype="f32"),
 })
-DEFAULT_WORKLOAD = "tucker400_fp32_st"
+DEFAULT_WORKLOAD = "invradius1000_bf16power_st"
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# it stands (summaries under profiles/); absent = not measured.
-#  * power_fused at 1000^3: k_power_tc2 captured at 512^3 (268.58 MB read,
-#    3.80 MB written), reads scaled by the column count (1000^3 / 512^3) and
-#    the partial writes by the row count (1000 / 512).
-NCU_TRAFFIC = {
-    ("invradius512_bf16power_st", "power_fused"): 268.57984e6 + 3.802112e6,
-    ("invradius1000_bf16power_st", "power_fused"): 268.57984e6 * (1000 ** 3 / 512 ** 3) +
-                                                   3.802112e6 * (1000 / 512),
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of each power-pass kernel class, from one ncu capture of the kernel as
+# it stands (summaries under profiles/); a launch's traffic is taken as this
+# ratio times its algorithmic bytes (traffic grows in proportion with the
+# columns a launch processes).  Absent = not measured for the current code.
+#  * power_fused: k_power_tc2 captured on the 512^3 precision form, mode 1
+#    (268.58 MB read + 3.80 MB written for 268.44 MB of bfloat16 copy).
+NCU_TRAFFIC_RATIO = {
+    "power_fused": (268.57984e6 + 3.802112e6) / 268.435456e6,
 }
 
 
@@ -240,24 +244,62 @@ def oracle_step(A, w):
     return T.rel_error(A, G, Us)
 
 
-def cpu_baseline(A, w, budget_s=12.0, max_samples=4):
-    """The oracle as it stands on the host cores: whole instances of the workload."""
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def config_of(name):
+    """The workload's config, printed identically by both arms."""
+    w = WORKLOADS[name]
+    cfg = {"workload": name, "desc": w["desc"]}
+    if w.get("kind") is None:
+        nbytes = int(np.prod(w["shape"])) * (8 if w["dtype"] == "f64" else 4)
+        cfg["l2"] = ("input (%d MB) larger than L2 (129 MB)" % (nbytes >> 20)
+                     if nbytes > 129e6 else "input fits L2")
+    elif w["kind"] == "batch":
+        from paper_2506_04840_gb300 import inputs as I
+        tot = sum(int(np.prod(sh)) * 4 for sh, _, _ in I.batch_specs(w["count"], w["seed"]))
+        cfg["l2"] = "inputs (%.1f GB in total) larger than L2 (129 MB)" % (tot / 1e9)
+    else:
+        cfg["l2"] = "request tensors mostly larger than L2 (129 MB)"
+    return cfg
+
+
+def oracle_sample(name, w, A=None, rank=0):
+    """One bounded sample of a single-tensor workload for the oracle:
+    (fraction of one tensor it stands for, the sampled tensor, description).
+    Workloads with ``oracle_slices`` sample the first that many slices along
+    the last mode (same Tucker ranks, same algorithm); cost is counted in
+    proportion to the slices, as the streaming passes over modes 1..d-1 are.
+    Others take the whole tensor."""
+    S = w.get("oracle_slices")
+    if S:
+        n3 = w["shape"][-1]
+        if A is not None:
+            As = np.asfortranarray(A[..., :S])
+        else:
+            from paper_2506_04840_gb300 import inputs as I
+            As = I.inverse_radius(w["shape"][0], seed=rank_seed(3, rank), noise=1e-6, slices=S)
+        what = ("the first %d of the %d mode-%d slices (%s), counted as %d/%d of a tensor"
+                % (S, n3, len(w["shape"]), "x".join(str(x) for x in As.shape), S, n3))
+        return S / n3, As, what
+    return 1.0, (A if A is not None else make_input(name, rank)), "whole instances of the workload"
+
+
+def cpu_baseline(name, w, A, budget_s=15.0, max_samples=8):
+    """The oracle as it stands on the host cores, on a bounded sample."""
+    frac, As, what = oracle_sample(name, w, A)
     n, t0 = 0, time.perf_counter()
     re = None
     while True:
-        re = oracle_step(A, w)
+        re = oracle_step(As, w)
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s or n >= max_samples:
             break
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": n / el, "unit": "tensors/s", "cores": cores, "kind": "oracle",
-            "sample": "%d whole instance(s) of the workload (oracle FP64 numpy/LAPACK, %.1f s)"
-                      % (n, el), "rel_err": re}
-
-
-def _cores():
-    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n * frac / el, "unit": "tensors/s", "cores": _cores(), "kind": "oracle",
+            "sample": "%s; %d sample(s) in %.1f s (oracle FP64 numpy/LAPACK)" % (what, n, el),
+            "rel_err_of_sample": re}
 
 
 def _oracle_sample_batch(w, budget_s):
@@ -307,57 +349,71 @@ def run_reference(args, w, rank, world):
         line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": args.gpus,
                 "steps": 1, "warmup": 1, "ms_per_step": 1e3 * el, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "impl": "reference",
-                "config": {"workload": args.workload, "desc": w["desc"], "rel_err": re},
+                "impl": "reference", "config": config_of(args.workload), "rel_err": re,
                 "cpu_baseline": {"kind": "oracle", "cores": _cores(), "value": value,
                                  "unit": "tensors/s", "sample": sample},
                 "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
-    A = make_input(args.workload)
+    frac, As, what = oracle_sample(args.workload, w)
     for _ in range(args.warmup):
-        oracle_step(A, w)
+        oracle_step(As, w)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        re = oracle_step(A, w)
+        re = oracle_step(As, w)
     el = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    value = args.steps / el
+    value = args.steps * frac / el
     line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "desc": w["desc"], "rel_err": re},
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
-                             "unit": "tensors/s",
-                             "sample": "each step one whole instance of the workload"},
+            "data": "synthetic", "impl": "reference", "config": config_of(args.workload),
+            "rel_err": re,
+            "cpu_baseline": {"kind": "oracle", "cores": _cores(), "value": value,
+                             "unit": "tensors/s", "sample": "each step: " + what},
             "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _roofline(prof, pk, pk_src, fp64=False):
+def _roofline(prof, pk, pk_src, workload):
+    """Roofline of the shifted-power pass (the metric's kernel) against the
+    measured HBM copy bandwidth: algorithmic bytes per launch (one read of
+    the tensor the step works on) over the live CUDA-event launch time.
+    The fused tensor-core pass when it ran, else the two CUDA-core halves
+    W = X^T Q and Y = X W of each step taken together."""
     kinds = prof["kinds"]
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    kd = kinds[dom]
-    avg_s = kd["ms"] / max(kd["launches"], 1) / 1e3
-    per_b = kd["bytes"] / max(kd["launches"], 1)
-    per_f = kd["flops"] / max(kd["launches"], 1)
-    if dom == "power_fused":
-        bound, unit, achieved = "hbm", "GB/s", per_b / avg_s / 1e9
-        peak, note = float(pk["hbm_gbs"]), "HBM copy bandwidth (%s)" % pk_src
-    elif fp64:
-        bound, unit, achieved = "alu", "TFLOP/s", per_f / avg_s / 1e12
-        peak, note = FP64_TFLOPS, "FP64 nominal 1.25 TFLOP/s (recipe table)"
+    hbm = float(pk["hbm_gbs"])
+    if kinds["power_fused"]["launches"]:
+        name = "power_fused"
+        kd = kinds[name]
+        launches, ms, by = kd["launches"], kd["ms"], kd["bytes"]
+        what = "fused shifted-power pass, one read of the bfloat16 copy per step (tcgen05)"
+    elif kinds["power_w"]["launches"]:
+        name = "power_w+power_y"
+        launches = kinds["power_w"]["launches"]
+        ms = kinds["power_w"]["ms"] + kinds["power_y"]["ms"]
+        by = kinds["power_w"]["bytes"]
+        what = ("shifted-power step as two CUDA-core passes (W = X^T Q, Y = X W); "
+                "algorithmic bytes = one read of X per step, the kernels read it twice")
     else:
-        bound, unit, achieved = "alu", "TFLOP/s", per_f / avg_s / 1e12
-        peak, note = FP32_ALU_TFLOPS, "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
-    return dom, {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                 "frac": achieved / peak, "kernel": dom, "launches": kd["launches"],
-                 "avg_launch_ms": avg_s * 1e3, "bytes_per_launch": per_b,
-                 "flops_per_launch": per_f, "peak_source": note}
+        name = max(kinds, key=lambda k: kinds[k]["ms"])
+        kd = kinds[name]
+        launches, ms, by = kd["launches"], kd["ms"], kd["bytes"]
+        what = "no power step ran (q = 0): the kernel class with the most time"
+    launches = max(launches, 1)
+    avg_s = ms / launches / 1e3
+    per_b = by / launches
+    achieved = per_b / avg_s / 1e9 if avg_s > 0 else 0.0
+    return name, {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                  "frac": achieved / hbm,
+                  "traffic": (NCU_TRAFFIC_RATIO[name] * per_b if name in NCU_TRAFFIC_RATIO
+                              else None),
+                  "kernel": name, "what": what, "launches": launches,
+                  "avg_launch_ms": avg_s * 1e3, "bytes_per_launch": per_b,
+                  "peak_source": "HBM copy bandwidth (%s MEASURED_PEAKS.json)" % pk_src
+                  if pk_src == "measured" else "fallback 6.8 TB/s"}
 
 
 def _kernels(prof, steps):
@@ -365,6 +421,42 @@ def _kernels(prof, steps):
                 "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
                 "tflops": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0}
             for k, v in prof["kinds"].items() if v["launches"]}
+
+
+def _latency(prof, steps, ms_per_step):
+    """The small svd as a latency line (one CTA per call on a sequential chain)."""
+    kd = prof["kinds"]["small_svd"]
+    if not kd["launches"]:
+        return {}
+    return {"small_svd": {"launches_per_step": kd["launches"] / steps,
+                          "avg_launch_us": 1e3 * kd["ms"] / kd["launches"],
+                          "ms_per_step": kd["ms"] / steps,
+                          "share_of_step": (kd["ms"] / steps) / ms_per_step if ms_per_step else None}}
+
+
+def _power_pass(prof, steps, pk):
+    """HBM GB/s of each power-step form that ran: algorithmic bytes (one
+    read of the tensor per step) over the summed time of its kernels."""
+    kinds = prof["kinds"]
+    hbm = float(pk["hbm_gbs"])
+    out = {}
+    f = kinds["power_fused"]
+    if f["launches"]:
+        g = f["bytes"] / (f["ms"] / 1e3) / 1e9
+        out["bf16_fused"] = {"gbs": g, "frac_of_measured_hbm": g / hbm,
+                             "launches_per_step": f["launches"] / steps,
+                             "ms_per_step": f["ms"] / steps, "reads_of_x_per_step": 1}
+    if kinds["power_w"]["launches"]:
+        ms = kinds["power_w"]["ms"] + kinds["power_y"]["ms"] + kinds["ritz"]["ms"]
+        g = kinds["power_w"]["bytes"] / (ms / 1e3) / 1e9
+        out["fp32_two_pass"] = {"gbs": g, "frac_of_measured_hbm": g / hbm,
+                                "steps_per_step": kinds["power_w"]["launches"] / steps,
+                                "ms_per_step": ms / steps, "reads_of_x_per_step": 2,
+                                "traffic_model_bytes_per_step":
+                                    2.0 * kinds["power_w"]["bytes"] / steps,
+                                "note": "W = X^T Q and Y = X W each read X (plus the Ritz "
+                                        "rotation of the precision form's FP32 step)"}
+    return out
 
 
 def run_batch_workload(args, w, local, world):
@@ -491,8 +583,7 @@ def run_batch_workload(args, w, local, world):
     api.tucker_batch_destroy(h2)
     del Ads2
     pk, pk_src = peaks()
-    dom, roof = _roofline(prof, pk, pk_src)
-    roof["traffic"] = NCU_TRAFFIC.get((args.workload, dom))
+    dom, roof = _roofline(prof, pk, pk_src, args.workload)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -501,13 +592,13 @@ def run_batch_workload(args, w, local, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (device-generated, seeded)",
-            "config": {"workload": args.workload, "desc": w["desc"], "instances": w["count"],
-                       "tensor_gb": sum(A.numel() * 4 for A in Ads) / 1e9,
-                       "rel_err_median": float(np.median(re)), "rel_err_max": float(re.max()),
-                       "launches_per_step": launches, "device_gb": dev_bytes / 1e9,
-                       "l2": "inputs (%.1f GB) larger than L2 (129 MB)"
-                             % (sum(A.numel() * 4 for A in Ads) / 1e9)},
-            "roofline": roof, "kernels": _kernels(prof, 1),
+            "config": config_of(args.workload),
+            "rel_err": float(np.median(re)),
+            "batch": {"instances": w["count"], "tensor_gb": sum(A.numel() * 4 for A in Ads) / 1e9,
+                      "rel_err_median": float(np.median(re)), "rel_err_max": float(re.max()),
+                      "launches_per_step": launches, "device_gb": dev_bytes / 1e9},
+            "roofline": roof, "power_pass": _power_pass(prof, 1, pk),
+            "latency": _latency(prof, 1, ms / args.steps), "kernels": _kernels(prof, 1),
             "e2e": {"value": world * w["count"] / e2e_s, "unit": "tensors/s",
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
@@ -525,102 +616,121 @@ def run_batch_workload(args, w, local, world):
     return 0
 
 
-def run_serve_workload(args, w, local, world):
-    """Poisson arrivals into the serving loop; latency = completion - submit."""
+def serve_session(w, duration, rank=0, dist=None, warmup=3, pool=256, server_bytes=0):
+    """Poisson arrivals into the serving loop.  The request tensors of a
+    pool of ``pool`` requests (the recipe's first ones) are made on the
+    device before the arrival clock starts; the arrival stream then replays
+    them at the recipe's arrival times, so a submit is only the call itself.
+    Latency = completion - scheduled arrival (server clock); the submit lag
+    (submit - scheduled arrival) is reported beside it."""
     import torch
     from paper_2506_04840_gb300 import api
     from paper_2506_04840_gb300 import inputs as I
-    torch.cuda.set_device(local)
-    dist = dist_init(world, local)
-    api.load()
-    rank = int(os.environ.get("RANK", "0"))
-    duration = args.duration if args.duration else w["duration"]
     count = int(w["rate"] * duration)
     reqs = I.serving_requests(count, rank_seed(w["seed"], rank), rate=w["rate"])
-    hil = {}
-    # warm-up: a few requests through a scratch server
-    srv = api.tucker_server_create(0, 256, api.TK_SHIFT_PAPER)
-    live = {}
-
-    def make(rq, tag):
+    P = min(pool, count)
+    hil, content = {}, []
+    for rq in reqs[:P]:
         shape = rq["shape"]
         if rq["kind"] == "hilbert":
             key = tuple(shape)
             if key not in hil:
                 hil[key] = I.hilbert_device(shape)
-            A = hil[key]
+            content.append(hil[key])
         else:
-            A = I.tucker_plus_noise_device(shape, rq["ranks"], rq["seed"], noise=1e-3)
+            content.append(I.tucker_plus_noise_device(shape, rq["ranks"], rq["seed"], noise=1e-3))
+
+    def spec(i):
+        # request i is pool entry i mod P (shape, ranks, q, content)
+        return reqs[i % P], content[i % P]
+
+    def outputs(rq):
         core = torch.empty(int(np.prod(rq["ranks"])), dtype=torch.float32, device="cuda")
-        U = [torch.empty(shape[k] * rq["ranks"][k], dtype=torch.float32, device="cuda")
+        U = [torch.empty(rq["shape"][k] * rq["ranks"][k], dtype=torch.float32, device="cuda")
              for k in range(3)]
         rel = torch.zeros(1, dtype=torch.float64, device="cuda")
-        it = api.make_item(A, shape, rq["ranks"], w["s"], rq["q"], core, U, rel, seed=0,
-                           tag=tag % (1 << 24))
-        return it, (A, core, U, rel)
+        return core, U, rel
 
-    for i, rq in enumerate(reqs[:max(args.warmup, 3)]):
-        it, keep = make(rq, i)
-        torch.cuda.current_stream().synchronize()
-        live[api.tucker_server_submit(srv, it)] = keep
+    # outputs and item descriptors of every request, made before the clock
+    items, keep = [], []
+    for i in range(count):
+        rq, A = spec(i)
+        core, U, rel = outputs(rq)
+        items.append(api.make_item(A, rq["shape"], rq["ranks"], w["s"], rq["q"], core, U, rel,
+                                   seed=0, tag=i % (1 << 24)))
+        keep.append((core, U, rel))
+    torch.cuda.synchronize()
+
+    srv = api.tucker_server_create(server_bytes, 256, api.TK_SHIFT_PAPER)
+    for i in range(min(max(warmup, 3), count)):   # warm-up through the same server
+        api.tucker_server_submit(srv, items[i])
     api.tucker_server_drain(srv, 600.0)
     api.tucker_server_poll(srv, 1 << 16)
-    live.clear()
 
     api.tucker_profile_enable(True)
-    clocks = Clocks(local)
-    clocks.start()
     if dist:
         dist.barrier()   # the ranks' arrival streams start together
     t_start = api.tucker_server_clock(srv)
-    comps, lag, rels = [], [], {}
+    comps, lag, arrival_of = [], [], {}
     for i, rq in enumerate(reqs):
         while api.tucker_server_clock(srv) - t_start < rq["arrival"]:
-            for c in api.tucker_server_poll(srv, 4096):
-                comps.append(c)
-                rels[c["id"]] = live.pop(c["id"])[3]
-            time.sleep(0.0002)
-        it, keep = make(rq, i)
-        torch.cuda.current_stream().synchronize()   # content ready before the server reads it
-        rid = api.tucker_server_submit(srv, it)
-        live[rid] = keep
+            comps.extend(api.tucker_server_poll(srv, 4096))
+            time.sleep(0.0001)
+        rid = api.tucker_server_submit(srv, items[i])
+        arrival_of[rid] = (t_start + rq["arrival"], i)
         lag.append(api.tucker_server_clock(srv) - t_start - rq["arrival"])
     api.tucker_server_drain(srv, 1200.0)
-    for c in api.tucker_server_poll(srv, 1 << 16):
-        comps.append(c)
-        rels[c["id"]] = live.pop(c["id"])[3]
-    clk = clocks.stop()
+    comps.extend(api.tucker_server_poll(srv, 1 << 16))
     prof = api.tucker_profile_read()
     api.tucker_profile_enable(False)
     api.tucker_server_destroy(srv)
-    lat = np.array([c["done_s"] - c["submit_s"] for c in comps]) * 1e3
-    span = max(c["done_s"] for c in comps) - min(c["submit_s"] for c in comps)
+    lat = np.array([c["done_s"] - arrival_of[c["id"]][0] for c in comps]) * 1e3
+    span = max(c["done_s"] for c in comps) - t_start
+    rels = np.array([float(keep[arrival_of[c["id"]][1]][2].item()) for c in comps])
+    bad = sum(1 for c in comps if c["status"] != 0)
+    lag_ms = np.array(lag) * 1e3
+    return {"completed": len(comps), "failed": bad, "span_s": span, "duration_s": duration,
+            "offered_rps": w["rate"], "pool_requests": P,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()),
+            "submit_lag_p50_ms": float(np.percentile(lag_ms, 50)),
+            "submit_lag_p99_ms": float(np.percentile(lag_ms, 99)),
+            "rel_err_median": float(np.median(rels)), "rel_err_max": float(rels.max()),
+            "latency_from": "scheduled arrival (server clock)",
+            "kernels": prof["kernels"]}
+
+
+def run_serve_workload(args, w, local, world):
+    """The serving workload as the bench's step: requests completed per second."""
+    import torch
+    from paper_2506_04840_gb300 import api
+    torch.cuda.set_device(local)
+    dist = dist_init(world, local)
+    api.load()
+    rank = int(os.environ.get("RANK", "0"))
+    duration = args.duration if args.duration else w["duration"]
+    clocks = Clocks(local)
+    clocks.start()
+    sv = serve_session(w, duration, rank, dist, args.warmup)
+    clk = clocks.stop()
     # every rank serves its own arrival stream: the job completes the sum of
     # the ranks' requests over the slowest rank's span (latencies: rank 0's)
-    value = sum_over_ranks(len(comps), dist) / max_over_ranks(span, dist)
-    re = np.array([float(r.item()) for r in rels.values()])
-    bad = sum(1 for c in comps if c["status"] != 0)
+    value = sum_over_ranks(sv["completed"], dist) / max_over_ranks(sv["span_s"], dist)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
     line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
-            "steps": len(comps), "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / value,
+            "steps": sv["completed"], "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (device-generated per request, seeded)",
-            "config": {"workload": args.workload, "desc": w["desc"], "duration_s": duration,
-                       "offered_rps": w["rate"], "requests": len(comps), "failed": bad,
-                       "rel_err_median": float(np.median(re)), "rel_err_max": float(re.max()),
-                       "l2": "request tensors mostly larger than L2"},
-            "serve": {"p50_ms": float(np.percentile(lat, 50)),
-                      "p99_ms": float(np.percentile(lat, 99)),
-                      "mean_ms": float(lat.mean()),
-                      "submit_lag_p99_ms": float(np.percentile(np.array(lag) * 1e3, 99))},
+            "data": "synthetic (device-generated pool of requests, seeded)",
+            "config": config_of(args.workload), "rel_err": sv["rel_err_median"],
+            "serve": sv,
             "e2e": {"value": value, "unit": "tensors/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0,
                     "note": "requests are served from device memory; content is made on the "
-                            "device per request (no host copies)"},
-            "clocks": clk, "gpu_launches": prof["kernels"]}
+                            "device before the arrival clock starts (no host copies)"},
+            "clocks": clk, "gpu_launches": sv["kernels"]}
     if world == 1 and not args.no_cpu_baseline:
         n, el, sample, _ = _oracle_sample_serve(w, 15.0)
         line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),
@@ -641,6 +751,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--duration", type=float, default=0.0,
                     help="serving workload: seconds of arrivals (default: the workload's)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="default workload: skip the short serving session")
+    ap.add_argument("--serve-duration", type=float, default=10.0,
+                    help="default workload: seconds of arrivals of the serving session")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -671,27 +785,59 @@ def main():
     core = torch.empty(int(np.prod(r)), dtype=tdt, device="cuda")
     U = [torch.empty(dims[k] * r[k], dtype=tdt, device="cuda") for k in range(d)]
     rel = torch.zeros(1, dtype=torch.float64, device="cuda")
-    kind = w.get("omega", api.TK_OMEGA_GAUSS)
-    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], omega=kind)
-    nbytes = (api.tucker_holistic_workspace_size if w.get("holistic") else
-              api.tucker_workspace_size)(Ad, dims, r, opts, 1 if w["st"] else 0)
-    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    opts = api.make_opts(d, w["q"], w["s"], seed=0, prec=w["prec"], workspace=ws, omega=kind)
-    fn = api.tucker_rsthosvd if w["st"] else api.tucker_rthosvd
     stream = torch.cuda.current_stream()
 
-    q_chosen = []
+    def make_step(wl):
+        """One step of workload wl on the device tensor X (its own workspace)."""
+        kind = wl.get("omega", api.TK_OMEGA_GAUSS)
+        opts = api.make_opts(d, wl["q"], wl["s"], seed=0, prec=wl["prec"], omega=kind)
+        nbytes = (api.tucker_holistic_workspace_size if wl.get("holistic") else
+                  api.tucker_workspace_size)(Ad, dims, r, opts, 1 if wl["st"] else 0)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        opts = api.make_opts(d, wl["q"], wl["s"], seed=0, prec=wl["prec"], workspace=ws,
+                             omega=kind)
+        fn = api.tucker_rsthosvd if wl["st"] else api.tucker_rthosvd
+        q_chosen = []
 
-    def step(X):
-        if w.get("pve") is not None:
-            qs, _ = api.tucker_rsthosvd_pve(X, dims, r, opts, w["pve"], core, U, stream=stream)
-            q_chosen[:] = qs
-        elif w.get("holistic"):
-            api.tucker_holistic(X, dims, r, opts, 1 if w["st"] else 0, core, U, stream=stream)
-        else:
-            fn(X, dims, r, opts, core, U, stats=False, stream=stream)
-        api.tucker_error(X, dims, core, r, U, rel, stream=stream)
+        def step(X):
+            if wl.get("pve") is not None:
+                qs, _ = api.tucker_rsthosvd_pve(X, dims, r, opts, wl["pve"], core, U,
+                                                stream=stream)
+                q_chosen[:] = qs
+            elif wl.get("holistic"):
+                api.tucker_holistic(X, dims, r, opts, 1 if wl["st"] else 0, core, U,
+                                    stream=stream)
+            else:
+                fn(X, dims, r, opts, core, U, stats=False, stream=stream)
+            api.tucker_error(X, dims, core, r, U, rel, stream=stream)
+        step.ws = ws
+        step.q_chosen = q_chosen
+        return step
 
+    def timed(step, steps, warmup):
+        """CUDA-event time of `steps` device-resident steps, with the
+        library's live per-launch events (profile) over the same region."""
+        for _ in range(warmup):
+            step(Ad)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        api.tucker_profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(Ad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = api.tucker_profile_read()
+        api.tucker_profile_enable(False)
+        if dist:
+            dist.barrier()
+        return max_over_ranks(e0.elapsed_time(e1), dist), prof
+
+    step = make_step(w)
     for _ in range(args.warmup):
         step(Ad)
     torch.cuda.synchronize()
@@ -700,24 +846,8 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    api.tucker_profile_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(Ad)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    prof = api.tucker_profile_read()
-    api.tucker_profile_enable(False)
-    if dist:
-        dist.barrier()
+    ms, prof = timed(step, args.steps, 0)
     clk = clocks.stop()
-    ms = max_over_ranks(ms, dist)
     rel_err = float(rel.item())
     value = job_value(world * args.steps, ms)
 
@@ -764,59 +894,40 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), dist)
     e2e_value = job_value(world * args.steps, ms_e2e)
+    del Ae, pin
 
-    # ---- roofline of the dominant kernel ----------------------------------
     pk, pk_src = peaks()
-    kinds = prof["kinds"]
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    kd = kinds[dom]
-    avg_s = kd["ms"] / max(kd["launches"], 1) / 1e3
-    per_launch_bytes = kd["bytes"] / max(kd["launches"], 1)
-    per_launch_flops = kd["flops"] / max(kd["launches"], 1)
-    if dom == "power_fused":
-        bound, unit = "hbm", "GB/s"
-        achieved = per_launch_bytes / avg_s / 1e9
-        peak = float(pk["hbm_gbs"])
-        peak_note = "HBM copy bandwidth (%s)" % pk_src
-    elif w["dtype"] == "f64":
-        bound, unit = "alu", "TFLOP/s"
-        achieved = per_launch_flops / avg_s / 1e12
-        peak = FP64_TFLOPS
-        peak_note = "FP64 nominal 1.25 TFLOP/s (recipe table)"
-    else:
-        bound, unit = "alu", "TFLOP/s"
-        achieved = per_launch_flops / avg_s / 1e12
-        peak = FP32_ALU_TFLOPS
-        peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, dom)),
-            "kernel": dom, "launches": kd["launches"], "avg_launch_ms": avg_s * 1e3,
-            "bytes_per_launch": per_launch_bytes, "flops_per_launch": per_launch_flops,
-            "peak_source": peak_note}
-    hbm_frac = {k: (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0)
-                for k, v in kinds.items()}
-    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                   "gbs": round(hbm_frac[k], 1),
-                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0)}
-               for k, v in kinds.items() if v["launches"]}
+    dom, roof = _roofline(prof, pk, pk_src, args.workload)
+    kernels = _kernels(prof, args.steps)
 
-    # the shifted-power pass (fused, or the two CUDA-core halves) as HBM GB/s
-    pw = [kinds[k] for k in ("power_fused", "power_w", "power_y") if kinds[k]["launches"]]
-    pw_ms = sum(v["ms"] for v in pw)
-    pw_gbs = ((kinds["power_fused"]["bytes"] + kinds["power_w"]["bytes"]) / (pw_ms / 1e3) / 1e9
-              if pw_ms > 0 else 0.0)
-    power_pass = {"gbs": pw_gbs, "frac_of_measured_hbm": pw_gbs / float(pk["hbm_gbs"]),
-                  "fused_traffic_per_launch": NCU_TRAFFIC.get((args.workload, "power_fused")),
-                  "ms_per_step": pw_ms / args.steps,
-                  "note": "algorithmic bytes of X read once per power step / summed time of "
-                          "the power kernels"}
+    # ---- the plain FP32 form on the same tensor (precision-form workloads)
+    plain = None
+    if w.get("companion"):
+        wc = WORKLOADS[w["companion"]]
+        step_c = make_step(wc)
+        ms_c, prof_c = timed(step_c, args.steps, args.warmup)
+        pk2, pk2_src = peaks()
+        _, roof_c = _roofline(prof_c, pk2, pk2_src, w["companion"])
+        plain = {"workload": w["companion"], "value": job_value(world * args.steps, ms_c),
+                 "unit": "tensors/s", "ms_per_step": ms_c / args.steps,
+                 "rel_err": float(rel.item()),
+                 "speedup_of_precision_form": (ms_c / ms) if ms > 0 else None,
+                 "rel_err_ratio_precision_over_plain": rel_err / float(rel.item())
+                 if float(rel.item()) > 0 else None,
+                 "power_pass": _power_pass(prof_c, args.steps, pk2), "roofline": roof_c,
+                 "latency": _latency(prof_c, args.steps, ms_c / args.steps),
+                 "kernels": _kernels(prof_c, args.steps)}
+        del step_c
 
+    launches = prof["kernels"]
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -824,21 +935,28 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "tensors/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": w["dtype"], "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "rel_err": rel_err,
-                       "l2": "input (%d MB) larger than L2 (129 MB)" % (Ad.numel() *
-                                                                       Ad.element_size() >> 20)
-                       if Ad.numel() * Ad.element_size() > 129e6 else "input fits L2"},
-            "roofline": roof, "power_pass": power_pass, "kernels": kernels,
+            "dtype": w["dtype"], "data": "synthetic", "config": config_of(args.workload),
+            "rel_err": rel_err,
+            "roofline": roof, "power_pass": _power_pass(prof, args.steps, pk),
+            "latency": _latency(prof, args.steps, ms / args.steps), "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "overlap": "step k+1's host->device copy overlaps step k's compute "
                                "(two device input buffers)"},
-            "clocks": clk, "gpu_launches": prof["kernels"]}
-    if q_chosen:
-        line["config"]["pve"] = {"tol": w["pve"], "q_max": w["q"], "q_per_mode": list(q_chosen)}
+            "clocks": clk, "gpu_launches": launches}
+    if plain is not None:
+        line["plain_form"] = plain
+    if step.q_chosen:
+        line["pve"] = {"tol": w["pve"], "q_max": w["q"], "q_per_mode": list(step.q_chosen)}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, w)
+        line["cpu_baseline"] = cpu_baseline(args.workload, w, A)
+    if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_serve:
+        del step, Ad, core, U
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        ws_ = WORKLOADS["serve_poisson200"]
+        line["serve"] = dict(workload="serve_poisson200", desc=ws_["desc"],
+                             **serve_session(ws_, args.serve_duration, 0, None, 3))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

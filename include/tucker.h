@@ -203,7 +203,10 @@ tk_status tucker_sketch(const tk_tensor* A, int k, int l, uint64_t seed, uint32_
  * tensors) must not exceed TK_NOALLOC_SCRATCH_BYTES, else TK_EWORKSPACE is
  * returned and nothing runs.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  All calls share
+ * device); make that first call before any stream capture.  The address is
+ * kept for the life of the process and belongs to the device's primary
+ * context: after cudaDeviceReset, or with another driver context current,
+ * it is no longer valid, so use the primary context only.  All calls share
  * the array: calls that overlap on the GPU (different streams, concurrent
  * threads) race on it and must be serialised by the caller. */
 #define TK_NOALLOC_SCRATCH_BYTES (8u << 20)

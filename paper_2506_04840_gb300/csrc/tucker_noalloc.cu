@@ -8,9 +8,11 @@
 // cannot risk an allocation failing or stalling mid-request).  Such callers
 // cannot let the library call cudaMalloc or cudaMallocAsync on their behalf.
 #include <mutex>
+#include <vector>
 
 #include "tk_common.cuh"
 #include "tk_internal.h"
+#include "tk_plan.h"
 
 namespace tk {
 
@@ -50,17 +52,13 @@ using namespace tk;
 
 extern "C" tk_status tucker_sketch_noalloc(const tk_tensor* A, int k, int l, uint64_t seed,
                                            uint32_t tag, double* Y, void* stream) {
-  if (!A || A->d < 1 || A->d > TK_MAX_D || !A->data || k < 0 || k >= A->d || l < 1 ||
-      l > TK_MAX_L || !Y || tag >= (1u << 24))
+  // the same argument checks and mode-k view as tucker_sketch
+  if (!valid_tensor(A, true) || k < 0 || k >= A->d || l < 1 || l > TK_MAX_L || !Y ||
+      tag >= (1u << 24))
     return TK_EINVAL;
-  if (A->dtype != TK_F64 && A->dtype != TK_F32 && A->dtype != TK_BF16) return TK_EINVAL;
-  View v{1, A->n[k], 1};
-  for (int m = 0; m < A->d; ++m) {
-    if (A->n[m] < 1) return TK_EINVAL;
-    if (m < k) v.P *= A->n[m];
-    if (m > k) v.S *= A->n[m];
-  }
-  const XType xt = A->dtype == TK_F64 ? X_F64 : (A->dtype == TK_F32 ? X_F32 : X_BF16);
+  std::vector<int64_t> dims(A->n, A->n + A->d);
+  const View v = view_of(dims, k);
+  const XType xt = xtype(A->dtype);
   const int lc = xb_lc(l);
   const size_t per_split = (size_t)v.n * lc * asize(xt);
   if (per_split > (size_t)TK_NOALLOC_SCRATCH_BYTES) return TK_EWORKSPACE;
@@ -69,11 +67,11 @@ extern "C" tk_status tucker_sketch_noalloc(const tk_tensor* A, int k, int l, uin
   if (splits > fit) splits = fit;
   void* part = nullptr;
   cudaError_t e = scratch_address(&part);
-  if (e != cudaSuccess) return TK_ECUDA;
+  if (e != cudaSuccess) return from_cuda(e);
   cudaStream_t st = (cudaStream_t)stream;
   // k_xb writes every entry of the partial blocks it uses, so the scratch
   // needs no clearing between calls.
   e = launch_xb(xt, A->data, v, nullptr, l, seed, tag, k, part, splits, st);
   if (e == cudaSuccess) e = launch_reduce(xt, part, splits, v.n, l, lc, nullptr, nullptr, Y, st);
-  return e == cudaSuccess ? TK_OK : TK_ECUDA;
+  return from_cuda(e);
 }

@@ -73,11 +73,13 @@ def tucker_plus_noise(shape, ranks, seed, noise=1e-4, decay=None, noise_mode="co
     return np.asfortranarray((X + E).astype(dtype))
 
 
-def inverse_radius(n, seed, noise=1e-6, dtype=np.float32, chunk=64):
+def inverse_radius(n, seed, noise=1e-6, dtype=np.float32, chunk=64, slices=None):
     """a_ijk = (i^2+j^2+k^2)^(-1/2) (1-based) + N(0, (noise*||A0||/sqrt(N))^2).
 
     Built slab by slab along the last mode so an n = 1000 cube (4 GB FP32)
-    never needs an FP64 copy.
+    never needs an FP64 copy.  ``slices``: return only the first that many
+    slices along the last mode (n x n x slices), bitwise equal to the same
+    slices of the whole tensor (same noise level and draws).
     """
     rng = np.random.default_rng(seed)
     i = np.arange(1, n + 1, dtype=np.float64)
@@ -89,12 +91,14 @@ def inverse_radius(n, seed, noise=1e-6, dtype=np.float32, chunk=64):
         kk = sq[k0:k0 + chunk]
         norm2 += float(np.sum(1.0 / (ij[:, :, None] + kk[None, None, :])))
     sigma = noise * np.sqrt(norm2) / np.sqrt(float(n) ** 3)
-    A = np.empty((n, n, n), dtype=dtype, order="F")
-    for k0 in range(0, n, chunk):
+    m = n if slices is None else int(min(max(slices, 1), n))
+    A = np.empty((n, n, m), dtype=dtype, order="F")
+    for k0 in range(0, m, chunk):
         kk = sq[k0:k0 + chunk]
         slab = 1.0 / np.sqrt(ij[:, :, None] + kk[None, None, :])
         slab += sigma * rng.standard_normal(slab.shape)
-        A[:, :, k0:k0 + chunk] = slab.astype(dtype)
+        take = min(chunk, m - k0)
+        A[:, :, k0:k0 + take] = slab[:, :, :take].astype(dtype)
     return A
 
 

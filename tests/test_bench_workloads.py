@@ -65,3 +65,58 @@ def test_oracle_step_runs_each_variant(name):
     A = I.tucker_plus_noise(shape, [4] * d, 3, noise=1e-2, dtype=np.float64)
     re = bench.oracle_step(A, w)
     assert 0.0 <= re < 1.0, (name, re)
+
+
+def test_config_is_the_same_object_in_both_arms():
+    """The driver compares the two arms' config: it names the workload only
+    (no measured values), so both arms print the same dict."""
+    for name in bench.WORKLOADS:
+        cfg = bench.config_of(name)
+        assert cfg["workload"] == name and cfg["desc"] == bench.WORKLOADS[name]["desc"]
+        assert "l2" in cfg
+        assert set(cfg) == {"workload", "desc", "l2"}, name
+    assert bench.DEFAULT_WORKLOAD == "invradius1000_bf16power_st"
+    assert bench.WORKLOADS[bench.DEFAULT_WORKLOAD]["companion"] == "invradius1000_fp32_st"
+
+
+def test_oracle_slab_sample_is_a_prefix_of_the_tensor():
+    """The oracle's bounded sample of the 1000^3 workloads is the first
+    slices of the same tensor (built alone: bitwise the same values), counted
+    as that fraction of a tensor."""
+    w = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD])
+    full = I.inverse_radius(96, seed=3)
+    w["shape"] = [96, 96, 96]
+    w["oracle_slices"] = 20
+    frac, As, what = bench.oracle_sample("x", w, full)
+    assert frac == pytest.approx(20 / 96)
+    assert np.array_equal(As, full[:, :, :20])
+    alone = I.inverse_radius(96, seed=3, slices=20)
+    assert np.array_equal(alone, As)
+    assert "20 of the 96" in what
+
+
+def test_roofline_is_the_power_pass():
+    """The roofline object reports the shifted-power pass against HBM: the
+    fused pass when it ran, else the two CUDA-core halves together."""
+    def kind(launches=0, ms=0.0, by=0.0, fl=0.0):
+        return dict(launches=launches, ms=ms, bytes=by, flops=fl)
+    names = ["sketch", "power_w", "power_y", "power_fused", "small_svd", "ttm", "error",
+             "convert", "ritz"]
+    prof = {"kinds": {k: kind() for k in names}, "kernels": 0}
+    prof["kinds"]["small_svd"] = kind(12, 50.0, 1e6)
+    prof["kinds"]["power_w"] = kind(3, 6.0, 12e9)
+    prof["kinds"]["power_y"] = kind(3, 6.0, 12e9)
+    pk = {"hbm_gbs": 6000.0}
+    name, roof = bench._roofline(prof, pk, "measured", "x")
+    assert name == "power_w+power_y" and roof["bound"] == "hbm"
+    assert roof["achieved"] == pytest.approx(4e9 / 4e-3 / 1e9)
+    prof["kinds"]["power_fused"] = kind(2, 1.0, 4e9)
+    name, roof = bench._roofline(prof, pk, "measured", "x")
+    assert name == "power_fused"
+    assert roof["achieved"] == pytest.approx(2e9 / 0.5e-3 / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 6000.0)
+    assert roof["traffic"] == pytest.approx(bench.NCU_TRAFFIC_RATIO["power_fused"] * 2e9)
+    lat = bench._latency(prof, 1, 100.0)
+    assert lat["small_svd"]["avg_launch_us"] == pytest.approx(50.0 / 12 * 1e3)
+    pp = bench._power_pass(prof, 1, pk)
+    assert pp["fp32_two_pass"]["reads_of_x_per_step"] == 2

@@ -39,15 +39,14 @@ def _scale(Ad, dims, k, l, seed, tag, dtype):
     return float(torch.linalg.norm(Xk.abs() @ Om.abs()))
 
 
-@pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_noalloc_sketch_matches_sketch_twice(lib, dtype):
+def _run_twice(lib, dtype, calls, bf16=False):
     fn = _noalloc(lib)
     rng = np.random.default_rng(17)
-    calls = [((300, 40, 50), 0, 60, 5, 1),   # first call uses a large part of the scratch
-             ((23, 31, 17), 1, 9, 0, 2)]      # second call: smaller, stale data left behind
     for shape, k, l, seed, tag in calls:
-        A = np.asfortranarray(rng.standard_normal(shape).astype(dtype))
-        Ad = api.to_device(A, dtype)
+        A = np.asfortranarray(rng.standard_normal(shape).astype(np.float32 if bf16 else dtype))
+        Ad = api.to_device(A, np.float32 if bf16 else dtype)
+        if bf16:
+            Ad = Ad.to(torch.bfloat16)
         desc = api.tensor_desc(Ad, list(shape))
         Y_ref = torch.empty(shape[k] * l, dtype=torch.float64, device="cuda")
         api.tucker_sketch(Ad, list(shape), k, l, seed, tag, Y_ref)
@@ -59,7 +58,28 @@ def test_noalloc_sketch_matches_sketch_twice(lib, dtype):
         tol = 1e-12 if dtype == np.float64 else 1e-6
         err = float(torch.linalg.norm(Y - Y_ref))
         assert np.isfinite(err)
-        assert err <= tol * _scale(Ad, list(shape), k, l, seed, tag, dtype)
+        assert err <= tol * _scale(Ad.float() if bf16 else Ad, list(shape), k, l, seed, tag,
+                                   dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_noalloc_sketch_matches_sketch_twice(lib, dtype):
+    _run_twice(lib, dtype, [((300, 40, 50), 0, 60, 5, 1),   # a large part of the scratch
+                            ((23, 31, 17), 1, 9, 0, 2)])     # smaller, stale data left behind
+
+
+def test_noalloc_sketch_bfloat16_tensor(lib):
+    # a bfloat16 tensor takes the strided kernel with FP32 partials
+    _run_twice(lib, np.float32, [((64, 33, 20), 1, 40, 3, 4), ((50, 21, 30), 2, 17, 3, 5)],
+               bf16=True)
+
+
+def test_noalloc_sketch_with_fewer_splits_than_the_plain_call(lib):
+    # mode 0 of an FP32 tensor with 8000 rows and l = 60: each split's partial
+    # block is 8000 x 64 x 4 B = 2 MiB, so the scratch holds 4 of the ~15
+    # splits tucker_sketch uses, and the FP32 register-tiled kernel runs with
+    # a reduced split count; then a small call reuses the scratch
+    _run_twice(lib, np.float32, [((8000, 40, 50), 0, 60, 9, 6), ((30, 20, 10), 0, 12, 9, 7)])
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
