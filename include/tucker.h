@@ -152,6 +152,18 @@ size_t tucker_workspace_size(const tk_tensor* A, const int* r, const tk_opts* o,
 tk_status tucker_debug_omega(int k, int64_t row0, int64_t rows, int l, uint64_t seed,
                              uint32_t tag, float* out, void* stream);
 
+/* Test entry point: one product D = A B on the tcgen05 tensor cores in
+ * kind::tf32 (four K = 8 instructions accumulating in tensor memory), used to
+ * fix how the instruction rounds FP32 operands to TF32 and how its FP32
+ * accumulator rounds between instructions (the paper has no counterpart;
+ * the FP32 tensor-core contractions depend on both).
+ * A: 128 x 32, B: 32 x 64, D: 128 x 64, all row-major FP32, device.
+ * mode 0: A read from shared memory (K-major, 128-byte swizzle); 1: A from
+ * tensor memory.  Synchronises the stream; TK_ETIMEOUT if the tensor cores
+ * did not finish within 2 s; TK_EINVAL for another mode. */
+tk_status tucker_debug_tf32_mma(const float* A, const float* B, float* D, int mode,
+                                void* stream);
+
 /* Holistic variants (Algorithm B.1 for ST-HOSVD with TK_SHIFT_PAPER;
  * Algorithm A.2, ST or T-HOSVD case, with TK_SHIFT_NONE; the T-HOSVD case
  * with the shift is the variant the remark after Algorithm B.1 names).

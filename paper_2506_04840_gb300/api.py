@@ -90,6 +90,7 @@ SIGNATURES = {
                                           c_uint64, c_uint32, c_void_p, c_void_p]),
     "tucker_debug_omega": (c_int, [c_int, c_int64, c_int64, c_int, c_uint64, c_uint32, c_void_p,
                                    c_void_p]),
+    "tucker_debug_tf32_mma": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "tucker_sketch": (c_int, [ctypes.POINTER(tk_tensor), c_int, c_int, c_uint64, c_uint32,
                               c_void_p, c_void_p]),
     "tucker_shifted_power": (c_int, [ctypes.POINTER(tk_tensor), c_int, c_int, c_int, c_int,
@@ -339,6 +340,11 @@ def tucker_error(A, dims, core, r, U, rel_err, stream=None):
     desc = tensor_desc(A, dims)
     _check(load().tucker_error(ctypes.byref(desc), _ptr(core), _ranks(r), _ptr_array(U),
                                _ptr(rel_err), _stream(stream)), "tucker_error")
+
+
+def tucker_debug_tf32_mma(A, B, D, mode, stream=None):
+    _check(load().tucker_debug_tf32_mma(_ptr(A), _ptr(B), _ptr(D), int(mode), _stream(stream)),
+           "tucker_debug_tf32_mma")
 
 
 def tucker_to_bf16(x, out, stream=None):

@@ -220,12 +220,28 @@ __device__ __forceinline__ void xtb_body(const TX* __restrict__ X, int64_t P, in
       offx[tid] = -1;
     }
   }
-  TA acc[TMJ][TN];
+  // FP32, EPI = 0: each slab of TK rows is summed from zero and folded into
+  // an (acc, cmp) pair by TwoSum (the compensation of the FP32 mode-major
+  // kernels), so strided TTMs and the error pass's expansions keep their
+  // results to about one rounding.
+  // EPI = 1 accumulates the residual instead: the accumulator starts at
+  // A(p, c) and the products are subtracted, so it is rounded at the scale of
+  // what remains to be subtracted rather than of a_hat (the error pass).
+  constexpr bool COMP = sizeof(TA) == 4 && EPI == 0;
+  TA acc[TMJ][TN], cmp[TMJ][TN];
+  __syncthreads();
 #pragma unroll
   for (int a = 0; a < TMJ; ++a)
 #pragma unroll
-    for (int q = 0; q < TN; ++q) acc[a][q] = (TA)0;
-  __syncthreads();
+    for (int q = 0; q < TN; ++q) {
+      cmp[a][q] = (TA)0;
+      acc[a][q] = (TA)0;
+      if (EPI == 1) {
+        const int64_t j = j0 + tj + 16 * a;   // S == 1: j = p
+        const int c = c0 + tc + 16 * q;
+        if (j < ncols && c < m) acc[a][q] = A[j + P * (int64_t)c];
+      }
+    }
 
   for (int64_t ib = 0; ib < n; ib += TK) {
     for (int e = tid; e < TK * TJ; e += TK_THREADS) {
@@ -246,19 +262,57 @@ __device__ __forceinline__ void xtb_body(const TX* __restrict__ X, int64_t P, in
       Bs[ii][c] = v;
     }
     __syncthreads();
+    TA sl[TMJ][TN];
+#pragma unroll
+    for (int x = 0; x < TMJ; ++x)
+#pragma unroll
+      for (int q = 0; q < TN; ++q) sl[x][q] = COMP ? (TA)0 : acc[x][q];
 #pragma unroll
     for (int ii = 0; ii < TK; ++ii) {
       TA a[TMJ], b[TN];
 #pragma unroll
       for (int q = 0; q < TMJ; ++q) a[q] = Xs[ii][tj + 16 * q];
 #pragma unroll
-      for (int q = 0; q < TN; ++q) b[q] = Bs[ii][tc + 16 * q];
+      for (int q = 0; q < TN; ++q) b[q] = EPI == 1 ? -Bs[ii][tc + 16 * q] : Bs[ii][tc + 16 * q];
 #pragma unroll
       for (int x = 0; x < TMJ; ++x)
 #pragma unroll
-        for (int q = 0; q < TN; ++q) acc[x][q] = fma(a[x], b[q], acc[x][q]);
+        for (int q = 0; q < TN; ++q) sl[x][q] = fma(a[x], b[q], sl[x][q]);
+      if constexpr (COMP) {
+        // the first row is a slab of its own (a dominant leading term would
+        // otherwise set the rounding scale of its whole slab)
+        if (ii == 0 && ib == 0) {
+#pragma unroll
+          for (int x = 0; x < TMJ; ++x)
+#pragma unroll
+            for (int q = 0; q < TN; ++q) {
+              acc[x][q] = sl[x][q];
+              sl[x][q] = (TA)0;
+            }
+        }
+      }
     }
+#pragma unroll
+    for (int x = 0; x < TMJ; ++x)
+#pragma unroll
+      for (int q = 0; q < TN; ++q) {
+        if constexpr (COMP) {
+          const TA t = __fadd_rn(acc[x][q], sl[x][q]);
+          const TA z = __fsub_rn(t, acc[x][q]);
+          const TA se = __fadd_rn(__fsub_rn(acc[x][q], __fsub_rn(t, z)), __fsub_rn(sl[x][q], z));
+          acc[x][q] = t;
+          cmp[x][q] = __fadd_rn(cmp[x][q], se);
+        } else {
+          acc[x][q] = sl[x][q];
+        }
+      }
     __syncthreads();
+  }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int x = 0; x < TMJ; ++x)
+#pragma unroll
+      for (int q = 0; q < TN; ++q) acc[x][q] = __fadd_rn(acc[x][q], cmp[x][q]);
   }
 
   if (EPI == 0) {
@@ -287,7 +341,7 @@ __device__ __forceinline__ void xtb_body(const TX* __restrict__ X, int64_t P, in
         const int c = c0 + tc + 16 * q;
         if (c < m) {
           const TA av = A[j + P * (int64_t)c];
-          const TA dv = av - acc[x][q];
+          const TA dv = acc[x][q];   // the residual (accumulated from A)
           e2t = fma(dv, dv, e2t);
           a2t = fma(av, av, a2t);
         }
@@ -380,7 +434,7 @@ k_reduce_batch(const ReduceJob* __restrict__ jobs, const uint32_t* __restrict__ 
     const int j = batch_job(start, njobs, b);
     const ReduceJob J = jobs[j];
     reduce_body<TA>((const TA*)J.part, J.splits, J.n, J.l, J.lc, J.Q, J.alpha, J.Y,
-                    b - __ldg(start + j));
+                    b - __ldg(start + j), (const TA*)J.part_lo);
   }
 }
 
@@ -578,10 +632,10 @@ static cudaError_t xtb_lc_go(const void* X, View v, const double* B, int64_t b_r
 
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
                        int64_t b_cm, int m, void* out, cudaStream_t st, int tout,
-                       void* scratch, const float* B32) {
+                       void* scratch, const float* B32, bool comp) {
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
   if (xtb32_ok(xt, v, X))
-    return launch_xtb32(X, v, B, b_ri, b_cm, m, out, st, tout, scratch, B32);
+    return launch_xtb32(X, v, B, b_ri, b_cm, m, out, st, tout, scratch, B32, comp);
   if (tout) return cudaErrorInvalidValue;
   switch (xt) {
     case X_F64: return xtb_lc_go<double, 0>(X, v, B, b_ri, b_cm, m, out, nullptr, nullptr, st);

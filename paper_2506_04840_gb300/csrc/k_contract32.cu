@@ -31,7 +31,14 @@ constexpr int KS = 16;   // contraction rows staged per slab
 // out is written in the (1, m, cols) layout out[c + m j], or with tout in
 // the (cols, m) layout out[j + cols c] (the mode just contracted moves last).
 // ---------------------------------------------------------------------------
-template <int WJ, int WC, typename BT>
+// COMP: slab-compensated accumulation over the rows, as in xb32_body below:
+// each slab of KS rows is summed from zero and folded into a (hi, lo) pair by
+// TwoSum, and the output is hi + lo rounded once.  Used for the TTM, whose
+// output is the next mode's tensor and (after the last mode) the core: an
+// uncompensated FP32 sum over n_k rows of a positive, smooth tensor carries
+// errors of several units of roundoff of its large entries, which in the
+// later modes reach the size of the weak directions the factors must keep.
+template <int WJ, int WC, typename BT, bool COMP = false>
 __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
                                            const BT* __restrict__ B, int64_t b_ri,
                                            int64_t b_cm, int m, float* __restrict__ out,
@@ -57,6 +64,11 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  float cmp[COMP ? 8 : 1][4];
+#pragma unroll
+  for (int a = 0; a < (COMP ? 8 : 1); ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cmp[a][q] = 0.f;
 
   // slab t (rows ib + t KS ..) travels in register set t % PF, then shared
   // buffer t & 1
@@ -107,6 +119,13 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
   for (int s = 0; s < nsl; ++s) {
     const int buf = s & 1;
     if (PF == 1 && s + 1 < nsl) load(0, ib + (int64_t)(s + 1) * KS);
+    float sl[COMP ? 8 : 1][4];
+    if constexpr (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sl[a][q] = 0.f;
+    }
 #pragma unroll
     for (int ii = 0; ii < KS; ++ii) {
       const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][ii][ja]);
@@ -117,7 +136,37 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (COMP) sl[a][q] = fmaf(av[a], bv[q], sl[a][q]);
+          else acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+        }
+      if constexpr (COMP) {
+        // the first row is a slab of its own: when one term dominates (the
+        // leading index of a core being expanded), the running sum of a
+        // 16-row slab would be rounded at its scale 15 more times
+        if (ii == 0 && s == 0) {
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[a][q] = sl[a][q];
+              sl[a][q] = 0.f;
+            }
+        }
+      }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float x = sl[a][q];
+          const float t = __fadd_rn(acc[a][q], x);
+          const float z = __fsub_rn(t, acc[a][q]);
+          const float se = __fadd_rn(__fsub_rn(acc[a][q], __fsub_rn(t, z)), __fsub_rn(x, z));
+          acc[a][q] = t;
+          cmp[a][q] = __fadd_rn(cmp[a][q], se);
+        }
     }
     if (PF == 1) {
       if (s + 1 < nsl) store(0, (s + 1) & 1);
@@ -141,7 +190,9 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = c0 + cb + q;
-      if (c < m) out[tout ? j + cols * c : (int64_t)c + (int64_t)m * j] = acc[a][q];
+      float v = acc[a][q];
+      if constexpr (COMP) v = __fadd_rn(acc[a][q], cmp[a][q]);
+      if (c < m) out[tout ? j + cols * c : (int64_t)c + (int64_t)m * j] = v;
     }
   }
 }
@@ -327,7 +378,7 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
   }
 }
 
-template <int WJ, int WC, typename BT>
+template <int WJ, int WC, typename BT, bool COMP = false>
 __global__ void __launch_bounds__(32 * WJ * WC)
 k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const BT* __restrict__ B,
         int64_t b_ri, int64_t b_cm, int m, float* __restrict__ out, int tout, int64_t kps,
@@ -335,8 +386,8 @@ k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const BT* __restri
   // split z of the rows writes its partial sums to part (layout c + m j)
   const int64_t ib = (int64_t)blockIdx.z * kps, ie = min(n, ib + kps);
   float* o = part ? part + (int64_t)blockIdx.z * cols * m : out;
-  xtb32_body<WJ, WC, BT>(X, n, cols, B, b_ri, b_cm, m, o, part ? 0 : tout, ib, ie, blockIdx.x,
-                         blockIdx.y);
+  xtb32_body<WJ, WC, BT, COMP>(X, n, cols, B, b_ri, b_cm, m, o, part ? 0 : tout, ib, ie,
+                               blockIdx.x, blockIdx.y);
 }
 
 // out = sum over the ks row splits of the partials, in a fixed order.
@@ -377,7 +428,7 @@ k_xb32(const float* __restrict__ X, int64_t n, int64_t cols, const float* __rest
                                  blockIdx.x, blockIdx.y, blockIdx.z, part_lo);
 }
 
-template <int WJ, int WC>
+template <int WJ, int WC, bool COMP>
 __global__ void __launch_bounds__(32 * WJ * WC)
 k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
               uint32_t total) {
@@ -388,13 +439,13 @@ k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy, z = lb / gxy, r = lb % gxy;
     const int64_t ib = (int64_t)z * J.kps, ie = min(J.n, ib + J.kps);
     float* o = J.part ? (float*)J.part + (int64_t)z * J.cols * J.m : (float*)J.out;
-    xtb32_body<WJ, WC, float>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
+    xtb32_body<WJ, WC, float, COMP>((const float*)J.X, J.n, J.cols, J.B, J.b_ri, J.b_cm, J.m, o,
                        J.part ? 0 : J.tout, ib, ie, r % (uint32_t)J.gx, r / (uint32_t)J.gx);
     __syncthreads();
   }
 }
 
-template <int WI, int WC, bool OMEGA>
+template <int WI, int WC, bool OMEGA, bool COMP = false>
 __global__ void __launch_bounds__(32 * WI * WC)
 k_xb32_batch(const Xb32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
              uint32_t total) {
@@ -404,9 +455,10 @@ k_xb32_batch(const Xb32Job* __restrict__ jobs, const uint32_t* __restrict__ star
     const uint32_t lb = b - __ldg(start + j);
     const uint32_t gxy = (uint32_t)J.gx * (uint32_t)J.gy;
     const uint32_t r = lb % gxy;
-    xb32_body<WI, WC, OMEGA>((const float*)J.X, J.n, J.cols, (const float*)J.W, J.l, J.lc,
-                             J.seed, J.tag, J.mode, J.cps, J.ka, J.kb, (float*)J.part,
-                             r % (uint32_t)J.gx, r / (uint32_t)J.gx, lb / gxy);
+    xb32_body<WI, WC, OMEGA, COMP>((const float*)J.X, J.n, J.cols, (const float*)J.W, J.l,
+                                   J.lc, J.seed, J.tag, J.mode, J.cps, J.ka, J.kb,
+                                   (float*)J.part, r % (uint32_t)J.gx, r / (uint32_t)J.gx,
+                                   lb / gxy, (float*)J.part_lo);
     __syncthreads();
   }
 }
@@ -437,11 +489,22 @@ __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t
   const int c0 = (int)by * MC;
   const int pa = wp * 64 + lp * 4;
   const int cb = wc * 16 + lc * 4;
+  // The accumulator starts at a(p, c) and every product is subtracted from
+  // it, so it holds the running residual a - sum_{i<t} T(p,i) B(i,c): after
+  // the leading term it is already at the scale of the remaining terms, and
+  // the roundings are relative to that, not to a_hat.  (Summing a_hat first
+  // and subtracting at the end rounds every FMA at the scale of a_hat, which
+  // on the workloads here is ~1e6 times the residual.)
   float acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 8; ++a) {
+    const int64_t p = p0 + pa + (a < 4 ? a : 28 + a);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + cb + q;
+      acc[a][q] = (p < P && c < m) ? __ldg(A + p + P * c) : 0.f;
+    }
+  }
   float tr[XPT], br[BPT];
   auto load = [&](int i0) {
 #pragma unroll
@@ -486,7 +549,7 @@ __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t
       const float4 a1 = *reinterpret_cast<const float4*>(&Ts[buf][ii][pa + 32]);
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][ii][cb]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[4] = {b.x, b.y, b.z, b.w};
+      const float bv[4] = {-b.x, -b.y, -b.z, -b.w};
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -506,7 +569,7 @@ __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t
       const int64_t p = p0 + pa + (a < 4 ? a : 28 + a);
       if (p >= P) continue;
       const float av = __ldg(A + p + P * c);
-      const float dv = av - acc[a][q];
+      const float dv = acc[a][q];
       e2t = fmaf(dv, dv, e2t);
       a2t = fmaf(av, av, a2t);
     }
@@ -631,21 +694,29 @@ Xb32Shape xb32_shape(View v, int l, int splits_req) {
   return s;
 }
 
-template <int WJ, int WC, typename BT>
+template <int WJ, int WC, typename BT, bool COMP>
 static void xtb32_go(const float* X, View v, const BT* B, int64_t b_ri, int64_t b_cm, int m,
                      float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
-  c32::k_xtb32<WJ, WC, BT><<<dim3(s.gx, s.gy, s.ks), 32 * WJ * WC, 0, st>>>(
+  c32::k_xtb32<WJ, WC, BT, COMP><<<dim3(s.gx, s.gy, s.ks), 32 * WJ * WC, 0, st>>>(
       X, v.n, v.cols(), B, b_ri, b_cm, m, out, tout, s.kps, s.ks > 1 ? part : nullptr);
+}
+
+template <typename BT, bool COMP>
+static void xtb32_wcc(const float* X, View v, const BT* B, int64_t b_ri, int64_t b_cm, int m,
+                      float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
+  switch (s.wc) {
+    case 1: xtb32_go<4, 1, BT, COMP>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+    case 2: xtb32_go<4, 2, BT, COMP>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+    default: xtb32_go<2, 4, BT, COMP>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
+  }
 }
 
 template <typename BT>
 static void xtb32_wc(const float* X, View v, const BT* B, int64_t b_ri, int64_t b_cm, int m,
-                     float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st) {
-  switch (s.wc) {
-    case 1: xtb32_go<4, 1>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
-    case 2: xtb32_go<4, 2>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
-    default: xtb32_go<2, 4>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st); break;
-  }
+                     float* out, int tout, float* part, const Xtb32Shape& s, cudaStream_t st,
+                     bool comp) {
+  if (comp) xtb32_wcc<BT, true>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st);
+  else xtb32_wcc<BT, false>(X, v, B, b_ri, b_cm, m, out, tout, part, s, st);
 }
 
 namespace c32 {
@@ -665,7 +736,7 @@ __global__ void __launch_bounds__(256) k_b_to_f32(const double* __restrict__ B, 
 // same either way (each FMA sees (float)B).
 cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, void* out, cudaStream_t st, int tout, void* scratch,
-                         const float* B32) {
+                         const float* B32, bool comp) {
   if (v.cols() <= 0 || m <= 0) return cudaSuccess;
   const Xtb32Shape s = xtb32_shape(v, m, scratch != nullptr);
   const float* x = (const float*)X;
@@ -673,17 +744,17 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
   float* part = (float*)scratch;
   if (B32 != nullptr) {
     count_kernels(s.ks > 1 ? 2 : 1);
-    xtb32_wc(x, v, B32, b_ri, b_cm, m, o, tout, part, s, st);
+    xtb32_wc(x, v, B32, b_ri, b_cm, m, o, tout, part, s, st, comp);
   } else if (scratch == nullptr) {
     count_kernels(1);
-    xtb32_wc(x, v, B, b_ri, b_cm, m, o, tout, (float*)nullptr, s, st);
+    xtb32_wc(x, v, B, b_ri, b_cm, m, o, tout, (float*)nullptr, s, st, comp);
     return cudaGetLastError();
   } else {
     float* b32 = (float*)((unsigned char*)scratch + xtb32_b32_offset(v, m));
     count_kernels(s.ks > 1 ? 3 : 2);
     const int64_t nb = v.n * m;
     c32::k_b_to_f32<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B, b_ri, b_cm, v.n, m, b32);
-    xtb32_wc(x, v, (const float*)b32, 1, v.n, m, o, tout, part, s, st);
+    xtb32_wc(x, v, (const float*)b32, 1, v.n, m, o, tout, part, s, st, comp);
   }
   if (s.ks > 1) {
     const int64_t tot = v.cols() * m;
@@ -765,21 +836,31 @@ cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, i
   return cudaGetLastError();
 }
 
-// Work-list launches: tile = WC, flag = (omega ? 1 : 0) | (WI or WJ) << 1.
+// Work-list launches: tile = WC; xtb32: flag = compensated | WJ << 1; xb32:
+// flag = omega | WI << 1 | compensated << 4.
 cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st) {
-  const int wc = b.tile, wx = b.flag >> 1, omega = b.flag & 1;
+  const int wc = b.tile, wx = (b.flag >> 1) & 7, omega = b.flag & 1;
+  const bool comp_y = (b.flag >> 4) & 1;
   if (b.kind == BK_XTB32RED) return run_batch(c32::k_xtb32_red_batch, b, 256, st);
   if (b.kind == BK_ERR32) return run_batch(c32::k_err32_batch, b, 256, st);
   if (b.kind == BK_XTB32) {
-    if (wc == 1) return run_batch(c32::k_xtb32_batch<4, 1>, b, 128, st);
-    if (wc == 2) return run_batch(c32::k_xtb32_batch<4, 2>, b, 256, st);
-    return run_batch(c32::k_xtb32_batch<2, 4>, b, 256, st);
+    const bool comp = (b.flag & 1) != 0;
+    if (wc == 1)
+      return comp ? run_batch(c32::k_xtb32_batch<4, 1, true>, b, 128, st)
+                  : run_batch(c32::k_xtb32_batch<4, 1, false>, b, 128, st);
+    if (wc == 2)
+      return comp ? run_batch(c32::k_xtb32_batch<4, 2, true>, b, 256, st)
+                  : run_batch(c32::k_xtb32_batch<4, 2, false>, b, 256, st);
+    return comp ? run_batch(c32::k_xtb32_batch<2, 4, true>, b, 256, st)
+                : run_batch(c32::k_xtb32_batch<2, 4, false>, b, 256, st);
   }
   if (b.kind != BK_XB32) return cudaErrorInvalidValue;
 #define TK_XB32_CASE(WI, WC)                                                              \
   if (wx == WI && wc == WC)                                                               \
     return omega ? run_batch(c32::k_xb32_batch<WI, WC, true>, b, 32 * WI * WC, st)        \
-                 : run_batch(c32::k_xb32_batch<WI, WC, false>, b, 32 * WI * WC, st);
+                 : (comp_y ? run_batch(c32::k_xb32_batch<WI, WC, false, true>, b,           \
+                                       32 * WI * WC, st)                                 \
+                           : run_batch(c32::k_xb32_batch<WI, WC, false>, b, 32 * WI * WC, st));
   TK_XB32_CASE(1, 1)
   TK_XB32_CASE(1, 2)
   TK_XB32_CASE(1, 4)

@@ -385,6 +385,9 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
     case BK_XTB32RED:
     case BK_ERR32:
       return launch_batch_c32(b, st);
+    case BK_TC32SPLIT:
+    case BK_TC32XTB:
+      return launch_batch_tc32(b, st);
     default:
       return launch_batch_misc(b, st);
   }

@@ -7,7 +7,7 @@
 // of Q (c-part) and streams column slabs of 64 columns:
 //   GEMM1  D1[j, c] = sum_i X[i, j] Q[i, c]      (M = 64 slab columns,
 //          N = 32, K = n; A = the TMA tile read K-major, B = Q^T resident)
-//   epilogue: D1 (TMEM) -> bfloat16 W^T tile in shared memory
+//   epilogue: D1 (TMEM) -> W^T = W_hi^T + W_lo^T as two bfloat16 tiles in shared memory
 //   GEMM2  Y[i, c] += sum_j X[i, j] W[j, c]      (M = 128 rows per tile,
 //          N = 32, K = 64; A = the same TMA tile read MN-major)
 // Y stays in TMEM (ceil(n/128) tiles x 32 columns) for the whole launch and
@@ -26,6 +26,7 @@
 
 #include "tk_common.cuh"
 #include "tk_internal.h"
+#include "tk_tc.cuh"
 
 namespace tk {
 
@@ -38,102 +39,6 @@ constexpr int SUP_BYTES = 2 * CHUNK_I * BJ * 2;   // 128 rows x 64 cols bf16 = 1
 constexpr int QT_CHUNK_BYTES = NC * 128;           // 32 rows x 64 i bf16 = 4 KB
 constexpr int W_BYTES = NC * 128;                  // 32 rows (c) x 64 j bf16 = 4 KB
 constexpr int THREADS = 192;
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// 64-bit shared-memory matrix descriptor, 128-byte swizzle.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= 1ull << 46;
-  d |= 2ull << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: bf16 A and B, FP32 accumulator.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-               "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-  return ok != 0;
-}
-// Bounded wait: false if the limit ran out (and sets *abort).
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
-  if (mbar_try(a, parity)) return true;
-  const uint64_t t0 = now_ns();
-  while (true) {
-    if (mbar_try(a, parity)) return true;
-    if (*abort) return false;
-    if (now_ns() - t0 > WAIT_NS) {
-      *abort = 1;
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-               " [%0], [%1, {%2, %3}], [%4];"
-               :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               :: "r"(mbar) : "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-               "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                 "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                 "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                 "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 struct Params {
   int n;           // rows of X_(k)
@@ -169,7 +74,7 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
   const int nq = pr.nt * 2;                       // Q^T chunks of 64 rows
   unsigned char* sQ = sm;                         // nq x 4 KB
   unsigned char* sRing = sQ + nq * QT_CHUNK_BYTES;   // ring x 16 KB
-  unsigned char* sW = sRing + pr.ring * SUP_BYTES;   // 2 x 4 KB
+  unsigned char* sW = sRing + pr.ring * SUP_BYTES;   // W_hi^T: 2 x 4 KB, then W_lo^T: 2 x 4 KB
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpart = blockIdx.x % pr.cparts;
@@ -283,14 +188,18 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
         if (!mbar_wait(smem_u32(&bars.w_full[b]), v & 1, &abort_flag)) { ok = false; break; }
         fence_after();
         const uint32_t wbase = smem_u32(sW + b * W_BYTES);
+        const uint32_t wlo = smem_u32(sW + (2 + b) * W_BYTES);
         for (int t = 0; t < pr.nt; ++t) {
           const uint32_t sbase = smem_u32(sRing + slots[t] * SUP_BYTES);
           const uint32_t yt = tmem + (uint32_t)(t * NC);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
+            // W = W_hi + W_lo (bfloat16 pair, ~16 bits): Y += X W_hi + X W_lo
             const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
             const uint64_t db = desc_sw128(wbase + kk * 32, 16, 1024);
+            const uint64_t dl = desc_sw128(wlo + kk * 32, 16, 1024);
             mma_bf16(yt, da, db, ID2, (k | kk) != 0);
+            mma_bf16(yt, da, dl, ID2, 1);
           }
           mma_commit(smem_u32(&bars.empty[slots[t]]));
         }
@@ -323,10 +232,15 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
       if (lane < 16) {
         const int j = 16 * q + lane;
         unsigned char* wb = sW + b * W_BYTES;
+        unsigned char* wl = sW + (2 + b) * W_BYTES;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int off = c * 128 + ((((2 * j) >> 4) ^ (c & 7)) << 4) + ((2 * j) & 15);
-          *reinterpret_cast<__nv_bfloat16*>(wb + off) = __float2bfloat16_rn(__uint_as_float(r[c]));
+          const float w = __uint_as_float(r[c]);
+          const __nv_bfloat16 h = __float2bfloat16_rn(w);
+          *reinterpret_cast<__nv_bfloat16*>(wb + off) = h;
+          *reinterpret_cast<__nv_bfloat16*>(wl + off) =
+              __float2bfloat16_rn(__fsub_rn(w, __bfloat162float(h)));
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -394,49 +308,14 @@ constexpr int XBUF_BYTES = BJ * NC2 * 4;        // 64 x 64 FP32 partial = 16 KB
 constexpr int W2_BYTES = BJ * 128;              // 64 rows (j) x 64 c bf16 = 8 KB
 constexpr int QT2_CHUNK_BYTES = NC2 * 128;      // 64 rows (c) x 64 i bf16 = 8 KB
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;"
-               ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];"
-               :: "r"(cluster_addr) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-               "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t a, uint32_t parity,
-                                                  volatile int* abort) {
-  if (mbar_try_acq_cluster(a, parity)) return true;
-  const uint64_t t0 = now_ns();
-  while (true) {
-    if (mbar_try_acq_cluster(a, parity)) return true;
-    if (*abort) return false;
-    if (now_ns() - t0 > WAIT_NS) {
-      *abort = 1;
-      return false;
-    }
-  }
-}
-// Asynchronous store into a peer CTA's shared memory; completion counts 16
-// bytes on the peer's mbarrier (no fence needed on either side).
-__device__ __forceinline__ void st_async_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                            uint32_t d, uint32_t remote_mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
-               :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d), "r"(remote_mbar) : "memory");
+// (a, b) -> the bfloat16 pairs hi = (bf16(a), bf16(b)) and lo = the
+// bfloat16 roundings of the remainders, packed two per 32-bit word.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 l =
+      __floats2bfloat162_rn(__fsub_rn(a, __low2float(h)), __fsub_rn(b, __high2float(h)));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 struct Params2 {
@@ -475,8 +354,9 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
   const int ring = 2 * pr.nth;                         // two half-slab buffers
   unsigned char* sQ = sm;                              // nq x 8 KB
   unsigned char* sRing = sQ + nq * QT2_CHUNK_BYTES;    // ring x 16 KB
-  unsigned char* sW = sRing + ring * SUP_BYTES;        // 8 KB
-  float* sX = reinterpret_cast<float*>(sW + W2_BYTES);  // 16 KB exchange buffer
+  unsigned char* sW = sRing + ring * SUP_BYTES;        // W_hi: 8 KB
+  unsigned char* sWl = sW + W2_BYTES;                  // W_lo: 8 KB
+  float* sX = reinterpret_cast<float*>(sWl + W2_BYTES);  // 16 KB exchange buffer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -598,6 +478,7 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
     if (lane == 0 && my_slabs > 0) {
       const uint32_t ID2 = idesc_bf16(128, NC2, 1, 1);
       const uint32_t wbase = smem_u32(sW);
+      const uint32_t wlo = smem_u32(sWl);
       bool ok = true;
       for (int k = 0; k < my_slabs && ok; ++k) {
         if (!mbar_wait(smem_u32(&bars.w_full), k & 1, &abort_flag)) { ok = false; break; }
@@ -609,9 +490,12 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
           const uint32_t yt = tmem + (uint32_t)(t * NC2);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
+            // W = W_hi + W_lo (bfloat16 pair, ~16 bits): Y += X W_hi + X W_lo
             const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
             const uint64_t db = desc_sw128(wbase + kk * 2048, 1024, 1024);
+            const uint64_t dl = desc_sw128(wlo + kk * 2048, 1024, 1024);
             mma_bf16(yt, da, db, ID2, (k | kk) != 0);
+            mma_bf16(yt, da, dl, ID2, 1);
           }
           mma_commit(smem_u32(&bars.empty[slot]));
         }
@@ -663,26 +547,25 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       if (lane < 16) {
         const float* px = sX + j * NC2;
         unsigned char* wrow = sW + j * 128;
+        unsigned char* lrow = sWl + j * 128;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t* rr = ch < 4 ? r0 : r1;
           const int c0 = (ch & 3) * 8;
           const float4 pa = *reinterpret_cast<const float4*>(px + ch * 8);
           const float4 pb = *reinterpret_cast<const float4*>(px + ch * 8 + 4);
-          __nv_bfloat162 h0 = __floats2bfloat162_rn(__uint_as_float(rr[c0]) + pa.x,
-                                                    __uint_as_float(rr[c0 + 1]) + pa.y);
-          __nv_bfloat162 h1 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 2]) + pa.z,
-                                                    __uint_as_float(rr[c0 + 3]) + pa.w);
-          __nv_bfloat162 h2 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 4]) + pb.x,
-                                                    __uint_as_float(rr[c0 + 5]) + pb.y);
-          __nv_bfloat162 h3 = __floats2bfloat162_rn(__uint_as_float(rr[c0 + 6]) + pb.z,
-                                                    __uint_as_float(rr[c0 + 7]) + pb.w);
-          uint4 o;
-          o.x = *reinterpret_cast<uint32_t*>(&h0);
-          o.y = *reinterpret_cast<uint32_t*>(&h1);
-          o.z = *reinterpret_cast<uint32_t*>(&h2);
-          o.w = *reinterpret_cast<uint32_t*>(&h3);
-          *reinterpret_cast<uint4*>(wrow + ((ch ^ (j & 7)) << 4)) = o;
+          // own partial + peer's, in the same order in both CTAs (identical W)
+          uint4 ho, lo;
+          split_bf16x2(__uint_as_float(rr[c0]) + pa.x, __uint_as_float(rr[c0 + 1]) + pa.y, ho.x,
+                       lo.x);
+          split_bf16x2(__uint_as_float(rr[c0 + 2]) + pa.z, __uint_as_float(rr[c0 + 3]) + pa.w,
+                       ho.y, lo.y);
+          split_bf16x2(__uint_as_float(rr[c0 + 4]) + pb.x, __uint_as_float(rr[c0 + 5]) + pb.y,
+                       ho.z, lo.z);
+          split_bf16x2(__uint_as_float(rr[c0 + 6]) + pb.z, __uint_as_float(rr[c0 + 7]) + pb.w,
+                       ho.w, lo.w);
+          *reinterpret_cast<uint4*>(wrow + ((ch ^ (j & 7)) << 4)) = ho;
+          *reinterpret_cast<uint4*>(lrow + ((ch ^ (j & 7)) << 4)) = lo;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -787,7 +670,7 @@ bool tc_shape(int64_t n, int l, TcShape* s) {
   while (cols < need) cols <<= 1;
   if (cols > 512) return false;
   s->tmem_cols = cols;
-  const size_t fixed = (size_t)s->nq * tc::QT_CHUNK_BYTES + 2 * tc::W_BYTES + 1024;
+  const size_t fixed = (size_t)s->nq * tc::QT_CHUNK_BYTES + 4 * tc::W_BYTES + 1024;
   const size_t budget = 227 * 1024 - 2048;   // static smem (barriers) kept aside
   if (fixed + (size_t)(s->nt + 1) * tc::SUP_BYTES > budget) return false;
   int ring = (int)((budget - fixed) / tc::SUP_BYTES);
@@ -819,7 +702,7 @@ bool tc2_shape(int64_t n, int l, Tc2Shape* s) {
   if (cols > 512 || s->ring > 12) return false;
   s->tmem_cols = cols;
   s->smem = (size_t)s->nq * tc::QT2_CHUNK_BYTES + (size_t)s->ring * tc::SUP_BYTES +
-            tc::W2_BYTES + tc::XBUF_BYTES + 1024;
+            2 * tc::W2_BYTES + tc::XBUF_BYTES + 1024;
   return s->smem <= 227 * 1024 - 2048;
 }
 

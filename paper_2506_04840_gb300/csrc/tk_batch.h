@@ -7,6 +7,8 @@
 // launch.
 #pragma once
 
+#include <cuda.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -35,6 +37,7 @@ struct ReduceJob {
   const double* alpha;
   double* Y;
   int splits, l, lc;
+  const void* part_lo;  // compensated partials: the lo plane (or NULL)
 };
 
 // svd of an n x l iterate in one CTA (+ shift update), grid 1.
@@ -123,17 +126,43 @@ struct Xb32Job {
   const void* W;
   int64_t cps, ka, kb;
   void* part;
+  void* part_lo;        // compensated sums of Y = X W: the lo plane (flag bit 4)
   uint64_t seed;
   uint32_t tag;
   int l, lc, mode, gx, gy;
 };
 
-enum BatchKind {
-  BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
-  BK_XB32, BK_XTB32RED, BK_ERR32
+// W = X^T B on the tensor cores (k_tc32.cu): one problem's tensor maps and
+// sizes; a single call passes it as a kernel parameter, batches and the
+// server keep it in their job tables (64-byte aligned).
+struct alignas(64) Tc32XtbJob {
+  CUtensorMap mx;     // X_(k): inner n (rows), outer cols, box 32 x 128
+  CUtensorMap mb;     // the B planes: inner n_pad, outer 128, box 32 x 64
+  float* out;
+  int* err;           // the problem's status word (TK_ETIMEOUT if a wait ran out)
+  long long cols;     // columns of X_(k)
+  long long units;    // ceil(cols / 256)
+  long long ld;       // out_mode 2: row stride of the planes
+  int n;              // rows of X_(k) (the contraction)
+  int nk;             // stages per unit: ceil(n / 32)
+  int m;              // outputs written (<= 64)
+  int out_mode;       // 0: out[c + m j]; 1: out[j + cols c]; 2: planes (hi, lo)
 };
 
-constexpr size_t kJobBytes = 128;   // every job struct fits
+// B (n x m, FP64) -> its hi/lo TF32 planes for one problem.
+struct Tc32SplitJob {
+  const double* B;
+  int64_t b_ri, b_cm;
+  float* B2;
+  int n, m, n_pad;
+};
+
+enum BatchKind {
+  BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
+  BK_XB32, BK_XTB32RED, BK_ERR32, BK_TC32SPLIT, BK_TC32XTB
+};
+
+constexpr size_t kJobBytes = 384;   // every job struct fits (two tensor maps + sizes)
 
 struct BatchLaunch {
   int kind;           // BatchKind
@@ -155,6 +184,15 @@ cudaError_t launch_batch_contract(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_misc(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_tc32(const BatchLaunch& b, cudaStream_t st);
+
+// The tensor-core W = X^T B of one problem as job structs (false when the
+// view is not eligible, tc32_ok); blocks of its split job.
+bool tc32_xtb_jobs(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm, int m,
+                   float* out, int out_mode, int64_t ld, void* scratch, int* err,
+                   Tc32SplitJob* sj, Tc32XtbJob* xj);
+uint32_t tc32_split_blocks(const Tc32SplitJob& j);
+size_t tc32_xtb_smem();
 
 // Launch shapes of the FP32 mode-major kernels.
 struct Xtb32Shape {

@@ -51,10 +51,25 @@ bool xtb32_ok(XType xt, View v, const void* X);
 // their rows over more CTAs and holds B rounded to FP32 once.
 // B32 (may be NULL): B already in FP32 with the same strides (then B is
 // not read).
+// comp: slab-compensated sums over the rows (the TTM: its output is the next
+// mode's tensor and the core).
 cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, void* out, cudaStream_t st, int tout = 0,
-                         void* scratch = nullptr, const float* B32 = nullptr);
+                         void* scratch = nullptr, const float* B32 = nullptr,
+                         bool comp = false);
 size_t xtb32_scratch(View v, int m);
+// W = X_(k)^T B in 3xTF32 on tcgen05 tensor cores (k_tc32.cu), for an FP32
+// mode-major view with n_k % 4 == 0 and m <= 64.  out_mode 0: out[c + m j];
+// 1: out[j + cols c]; 2: the planes out[c][j] = hi(w), out[64 + c][j] = lo(w)
+// with row stride ld (the B operand of the tensor-core Y = X W).  scratch:
+// tc32_xtb_scratch(v) bytes (B split into hi/lo planes).  err: device status
+// word (TK_ETIMEOUT if a wait ran out).
+bool tc32_ok(View v, int m, const void* X);
+size_t tc32_xtb_scratch(View v);
+cudaError_t launch_tc32_xtb(const void* X, View v, const double* B, int64_t b_ri, int64_t b_cm,
+                            int m, float* out, int out_mode, int64_t ld, void* scratch, int* err,
+                            cudaStream_t st);
+
 // offset of the FP32 copy of B inside that scratch
 size_t xtb32_b32_offset(View v, int m);
 // FP32 last-mode expansion fused with the error sums (S == 1): err_part gets
@@ -88,7 +103,8 @@ cudaError_t launch_reduce(XType xt, const void* part, int splits, int64_t n, int
 // mode-major kernels.
 cudaError_t launch_xtb(XType xt, const void* X, View v, const double* B, int64_t b_ri,
                        int64_t b_cm, int m, void* out, cudaStream_t st, int tout = 0,
-                       void* scratch = nullptr, const float* B32 = nullptr);
+                       void* scratch = nullptr, const float* B32 = nullptr,
+                       bool comp = false);
 // Fused last-mode expansion and error sums: for S == 1, a_hat(p, c) =
 // sum_i T(p, i) B(i, c); accumulates (A - a_hat)^2 and A^2 per block into
 // err_part[2*block].  Returns the number of blocks via *blocks.

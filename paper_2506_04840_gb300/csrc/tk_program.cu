@@ -42,6 +42,8 @@ size_t job_size(int kind) {
     case BK_XTB32RED: return sizeof(Xtb32RedJob);
     case BK_ERR32: return sizeof(Err32Job);
     case BK_XB32: return sizeof(Xb32Job);
+    case BK_TC32SPLIT: return sizeof(Tc32SplitJob);
+    case BK_TC32XTB: return sizeof(Tc32XtbJob);
     default: return sizeof(ErrFinalJob);
   }
 }
@@ -55,7 +57,8 @@ uint32_t cdiv(int64_t a, int64_t b) { return (uint32_t)((a + b - 1) / b); }
 // first rounded into the scratch (at position pos - 1; scratch required).
 void xtb_ops(Phase& ph, int pos, int prof, XType xt, const void* X, View v, const double* B,
              int64_t b_ri, int64_t b_cm, int m, void* out, double bytes, double flops,
-             int tout = 0, void* scratch = nullptr, const float* B32 = nullptr) {
+             int tout = 0, void* scratch = nullptr, const float* B32 = nullptr,
+             bool comp = false) {
   if (xtb32_ok(xt, v, X)) {
     const Xtb32Shape sh = xtb32_shape(v, m, scratch != nullptr);
     void* part = sh.ks > 1 ? scratch : nullptr;
@@ -70,7 +73,7 @@ void xtb_ops(Phase& ph, int pos, int prof, XType xt, const void* X, View v, cons
       b_cm = v.n;
     }
     Xtb32Job j{X, v.n, v.cols(), B32, b_ri, b_cm, out, part, sh.kps, m, sh.gx, sh.gy, tout};
-    ph.push_back(make_op(pos, prof, BK_XTB32, xt, sh.wc, sh.wj << 1, 0,
+    ph.push_back(make_op(pos, prof, BK_XTB32, xt, sh.wc, (sh.wj << 1) | (comp ? 1 : 0), 0,
                          (uint32_t)sh.gx * sh.gy * sh.ks, bytes, flops, j));
     if (part) {
       Xtb32RedJob rj{part, out, v.cols(), m, sh.ks, tout};
@@ -89,16 +92,18 @@ void xtb_ops(Phase& ph, int pos, int prof, XType xt, const void* X, View v, cons
 // partials of Y = X_(k) B (B = W, or Omega_k when W == NULL) as launch_xb runs them.
 Op xb_op(int pos, int prof, XType xt, const void* X, View v, const void* W, int l,
          uint64_t seed, uint32_t tag, int mode, void* part, int splits, double bytes,
-         double flops, int64_t ka = 0, int64_t kb = 1) {
+         double flops, int64_t ka = 0, int64_t kb = 1, void* part_lo = nullptr) {
   if (xtb32_ok(xt, v, X)) {
     const Xb32Shape sh = xb32_shape(v, l, splits);
     if (ka <= 0) {
       ka = v.cols();
       kb = 1;
     }
-    Xb32Job j{X, v.n, v.cols(), W, sh.cps, ka, kb, part, seed, tag, l, sh.lc, mode, sh.gx,
-              sh.gy};
-    return make_op(pos, prof, BK_XB32, xt, sh.wc, (W == nullptr ? 1 : 0) | (sh.wi << 1), 0,
+    void* plo = W != nullptr ? part_lo : nullptr;
+    Xb32Job j{X, v.n, v.cols(), W, sh.cps, ka, kb, part, plo, seed, tag, l, sh.lc, mode,
+              sh.gx, sh.gy};
+    return make_op(pos, prof, BK_XB32, xt, sh.wc,
+                   (W == nullptr ? 1 : 0) | (sh.wi << 1) | (plo != nullptr ? 16 : 0), 0,
                    (uint32_t)sh.gx * sh.gy * sh.splits, bytes, flops, j);
   }
   const int lc = xb_lc(l);
@@ -215,7 +220,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       Phase ph;
       ph.push_back(xb_op(0, TK_K_SKETCH, xt, X, v, nullptr, l, it.seed, it.tag, k, w.part, splits,
                          N * es, 2.0 * N * l, ka, kb));
-      ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc};
+      ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc, nullptr};
       ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,
@@ -228,10 +233,25 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     // ---- power phases
     for (int t = 1; t <= p.q; ++t) {
       Phase ph;
-      xtb_ops(ph, 1, TK_K_POWER_W, xt, X, v, w.Q, 1, v.n, l, w.w, N * es, 2.0 * N * l, 0, w.part);
+      Tc32SplitJob sj;
+      Tc32XtbJob xj;
+      if (xt == X_F32 &&
+          tc32_xtb_jobs(X, v, w.Q, 1, v.n, l, (float*)w.w, 0, 0, w.small, w.status, &sj, &xj)) {
+        // W = X^T Q in 3xTF32 on the tensor cores, as the single call runs it
+        ph.push_back(make_op(0, TK_K_CONVERT, BK_TC32SPLIT, xt, 0, 0, 0, tc32_split_blocks(sj),
+                             (double)v.n * l * 16.0, 0.0, sj));
+        ph.push_back(make_op(1, TK_K_POWER_W, BK_TC32XTB, xt, 0, 0, tc32_xtb_smem(),
+                             (uint32_t)xj.units, N * es, 2.0 * N * l, xj));
+      } else {
+        xtb_ops(ph, 1, TK_K_POWER_W, xt, X, v, w.Q, 1, v.n, l, w.w, N * es, 2.0 * N * l, 0,
+                w.part);
+      }
+      // compensated Y = X W on FP32 mode-major views, as the single call runs it
+      void* plo = xtb32_ok(xt, v, X)
+                      ? (unsigned char*)w.part + (size_t)splits * v.n * lc * asize(xt) : nullptr;
       ph.push_back(xb_op(3, TK_K_POWER_Y, xt, X, v, w.w, l, it.seed, it.tag, k, w.part, splits,
-                         N * es, 2.0 * N * l));
-      ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc};
+                         N * es, 2.0 * N * l, 0, 1, plo));
+      ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc, plo};
       ph.push_back(make_op(4, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
@@ -267,7 +287,8 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       void* out = (step == d - 1) ? it.core : w.g[pp];
       // the TTM reads the returned factor (FP32 for an FP32 tensor)
       xtb_ops(ph, 3, TK_K_TTM, xt, X, v, w.Q, 1, v.n, r, out, (N + N / v.n * r) * es,
-              2.0 * N * r, p.rot ? 1 : 0, w.part, fp64 ? nullptr : (const float*)it.U[k]);
+              2.0 * N * r, p.rot ? 1 : 0, w.part, fp64 ? nullptr : (const float*)it.U[k],
+              /*comp=*/true);
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + TK_MAX_Q + 1);
       X = out;
@@ -287,7 +308,7 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       const double cin = (double)v.P * v.n * v.S;
       xtb_ops(ph, k, TK_K_ERROR, xt, Xe, v, qd[k], p.n[k], 1, m, tb[k & 1],
               (cin + cin / v.n * m) * es, 2.0 * cin / v.n * m * v.n, 0, nullptr,
-              fp64 ? nullptr : (const float*)it.U[k]);
+              fp64 ? nullptr : (const float*)it.U[k], /*comp=*/true);
       Xe = tb[k & 1];
       dims[k] = p.n[k];
     }
@@ -332,7 +353,8 @@ static bool key_less(const Op* a, const Op* b) {
 static bool key_eq(const Op* a, const Op* b) { return !key_less(a, b) && !key_less(b, a); }
 
 static size_t blob_take(std::vector<unsigned char>& blob, size_t bytes) {
-  const size_t off = (blob.size() + 15) & ~(size_t)15;
+  // 64-byte aligned: job structs may hold TMA tensor maps
+  const size_t off = (blob.size() + 63) & ~(size_t)63;
   blob.resize(off + bytes);
   return off;
 }

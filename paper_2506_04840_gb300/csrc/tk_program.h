@@ -33,7 +33,7 @@ struct Op {
   BatchLaunch key;    // kind, xt, tile, flag, smem (jobs/start unset)
   uint32_t blocks;    // this job's blocks
   double bytes, flops;
-  alignas(16) unsigned char job[kJobBytes];
+  alignas(64) unsigned char job[kJobBytes];
 };
 typedef std::vector<Op> Phase;
 

@@ -141,11 +141,15 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     p.sp[k] = small_plan(v.n, (int)lk, p.xt == X_F64);
     if (p.sp[k].Pb <= 0) return TK_ENOTIMPL;
     p.small = std::max(p.small, p.sp[k].scratch_bytes);
+    // the tensor-core W = X^T Q splits Q into that scratch
+    if (p.q > 0 && p.xt == X_F32 && v.P == 1 && (v.n % 4) == 0 && lk <= 64)
+      p.small = std::max(p.small, tc32_xtb_scratch(v));
     if (p.xt != X_F64) p.small = std::max(p.small, polish_scratch(v.n, p.r[k]));
     const int lc = xb_lc((int)lk);
     const int splits = xb_splits(p.xt, v, (int)lk);
-    // the precision form's FP32 step keeps (hi, lo) partial pairs
-    p.part = std::max(p.part, (size_t)splits * v.n * lc * ta * (p.bf16 && p.q >= 2 ? 2 : 1));
+    // the power steps' Y = X W on FP32 mode-major views keep (hi, lo) partial pairs
+    const bool comp_y = p.q >= 1 && xtb32_ok(p.xt, v, (const void*)1);
+    p.part = std::max(p.part, (size_t)splits * v.n * lc * ta * (comp_y ? 2 : 1));
     if (p.bf16 && p.q >= 2) p.part = std::max(p.part, ritz_scratch((int)lk));
     if (xtb32_ok(p.xt, v, (const void*)1)) {   // row-split scratch of W = X^T Q and the TTM
       p.part = std::max(p.part, xtb32_scratch(v, (int)lk));
@@ -294,7 +298,14 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     } else {
       {
         ProfScope ps(TK_K_POWER_W, N * xsize(xp), 2.0 * N * l, st);
-        TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st, 0, w.part));
+        if (xp == X_F32 && tc32_ok(v, l, Xp)) {
+          // W = X^T Q in 3xTF32 on the tensor cores (Q split into the small
+          // solver's scratch, which the svd only needs after this step)
+          TK_TRY(launch_tc32_xtb(Xp, v, w.Q, 1, v.n, l, (float*)w.w, 0, 0, w.small, w.status,
+                                 st));
+        } else {
+          TK_TRY(launch_xtb(xp, Xp, v, w.Q, 1, v.n, l, w.w, st, 0, w.part));
+        }
       }
       // The precision form's FP32 step has to resolve the weak directions
       // the bfloat16 steps left inexact, to the FP32 path's accuracy:
@@ -310,8 +321,11 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
         ProfScope ps(TK_K_RITZ, 3.0 * cw * 4.0, 4.0 * cw * l, st);
         TK_TRY(launch_ritz_rotate((float*)w.w, v.cols(), v.P, l, w.part, w.status, st));
       }
+      // Y = X W on FP32 mode-major views: compensated sums (slab sums folded
+      // into (hi, lo) pairs), so the weak directions of the iterate are not
+      // lost under the rounding of sums over the unfolding's ~N/n columns
       void* plo = nullptr;
-      if (last32 && xtb32_ok(xp, v, Xp))
+      if (xtb32_ok(xp, v, Xp))
         plo = (unsigned char*)w.part + (size_t)splits * v.n * lc * asize(xp);
       {
         ProfScope ps(TK_K_POWER_Y, N * xsize(xp), 2.0 * N * l, st);
@@ -362,7 +376,7 @@ static cudaError_t ttm(XType xt, const void* X, View v, const double* U, int r, 
   const double N = (double)v.P * (double)v.n * (double)v.S;
   ProfScope ps(TK_K_TTM, (N + N / v.n * r) * xsize(xt), 2.0 * N * r, st);
   return launch_xtb(xt, X, v, U, 1, v.n, r, out, st, tout, scratch,
-                    xt == X_F32 ? (const float*)U32 : nullptr);
+                    xt == X_F32 ? (const float*)U32 : nullptr, /*comp=*/true);
 }
 
 static cudaError_t polish(double* Q, int64_t n, int r, void* scratch, int* status,
@@ -834,10 +848,14 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
   const int lp = power_tc_lpad(v, l);
   Arena b;
   const size_t o_w = b.offset(tc ? 0 : (size_t)v.cols() * l * asize(xt));
+  const bool comp_y = !tc && xtb32_ok(xt, v, A->data);
   const size_t o_part = b.offset(tc ? (size_t)groups * v.n * lp * sizeof(float)
-                                    : (size_t)splits * v.n * lc * asize(xt));
+                                    : (size_t)splits * v.n * lc * asize(xt) * (comp_y ? 2 : 1));
   const size_t o_y = b.offset((size_t)v.n * l * sizeof(double));
-  const size_t o_sm = b.offset(std::max(sp.scratch_bytes, tc ? power_tc_scratch(v, l) : 0));
+  // FP32 mode-major views take W = X^T Q on the tensor cores (Q split into B2)
+  const bool tcw = !tc && xt == X_F32 && tc32_ok(v, l, A->data);
+  const size_t o_sm = b.offset(std::max({sp.scratch_bytes, tc ? power_tc_scratch(v, l) : 0,
+                                         tcw ? tc32_xtb_scratch(v) : 0}));
   const size_t o_st = b.offset(sizeof(int));
   unsigned char* base = nullptr;
   TK_TRY(cudaMallocAsync((void**)&base, b.off + 256, st));
@@ -860,14 +878,17 @@ tk_status tucker_shifted_power(const tk_tensor* A, int k, int l, int q, tk_shift
       } else {
         {
           ProfScope ps(TK_K_POWER_W, N * xsize(xt), 2.0 * N * l, st);
-          e = launch_xtb(xt, A->data, v, Q, 1, v.n, l, wv, st);
+          e = tcw ? launch_tc32_xtb(A->data, v, Q, 1, v.n, l, (float*)wv, 0, 0, sm, stt, st)
+                  : launch_xtb(xt, A->data, v, Q, 1, v.n, l, wv, st);
         }
+        void* plo = comp_y ? (unsigned char*)part + (size_t)splits * v.n * lc * asize(xt)
+                           : nullptr;
         if (e == cudaSuccess) {
           ProfScope ps(TK_K_POWER_Y, N * xsize(xt), 2.0 * N * l, st);
-          e = launch_xb(xt, A->data, v, wv, l, 0, 0, k, part, splits, st);
+          e = launch_xb(xt, A->data, v, wv, l, 0, 0, k, part, splits, st, 0, 1, plo);
         }
         if (e == cudaSuccess)
-          e = launch_reduce(xt, part, splits, v.n, l, lc, Q, alpha, (double*)Y, st);
+          e = launch_reduce(xt, part, splits, v.n, l, lc, Q, alpha, (double*)Y, st, plo);
       }
       if (e == cudaSuccess)
         e = launch_small_svd(fp64, sp, (const double*)Y, v.n, Q, sigma, sm, (int)rule, true,
@@ -957,7 +978,7 @@ tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const
       ProfScope ps(TK_K_ERROR, (cin + cin / v.n * A->n[k]) * es, 2.0 * cin / v.n * A->n[k] * v.n,
                    st);
       e = launch_xtb(xt, X, v, Ud[k], A->n[k], 1, (int)A->n[k], tb[k & 1], st, 0, nullptr,
-                     xt == X_F32 ? (const float*)U[k] : nullptr);
+                     xt == X_F32 ? (const float*)U[k] : nullptr, /*comp=*/true);
       X = tb[k & 1];
       dims[k] = A->n[k];
     }

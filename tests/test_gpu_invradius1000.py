@@ -1,0 +1,92 @@
+"""The 1000^3 inverse-radius workload at full size against the oracle.
+
+a_ijk = (i^2+j^2+k^2)^(-1/2) + N(0, (1e-6 ||A0|| / sqrt(N))^2), FP32, 4 GB;
+Algorithm 3 with r = (50,50,50), s = 10, q = 3, in the plain FP32 form and in
+the precision form (power steps 1..q-1 on the bfloat16 copy).  The oracle's
+result is stored in tests/golden/invradius1000.json (+ _factors.npz), written
+by tests/golden/make_invradius1000.py, which calls only oracle/.
+
+Gates (relative, since the relative error is itself ~1e-6 here, so an
+absolute 1e-6 difference would pass anything):
+* RE of the returned core and factors, computed in FP64 on the host,
+  RE_gpu <= 1.02 RE_oracle;
+* the library's own error pass (tucker_error) within 1.02 RE_oracle too;
+* principal-angle sines <= 1e-5 between the returned factors and the
+  oracle's on each mode's well-separated leading block.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tucker as T
+from paper_2506_04840_gb300 import api
+from paper_2506_04840_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden", "invradius1000.json")
+GOLD_U = os.path.join(HERE, "golden", "invradius1000_factors.npz")
+
+
+@pytest.fixture(scope="module")
+def tensor():
+    g = json.load(open(GOLD))
+    A = I.inverse_radius(g["n"], seed=g["seed"], noise=1e-6)
+    A64s = float(np.sum(A, dtype=np.float64))
+    assert abs(A64s - g["sum"]) <= 1e-9 * abs(g["sum"]), "input differs from the golden's"
+    return A, g
+
+
+def _fp64_rel_error(A, G, Us):
+    """||A - G x_1 U_1 x_2 U_2 x_3 U_3|| / ||A|| in FP64, slab by slab along
+    mode 3 (Section 5's relative error, without a full-size FP64 copy)."""
+    n3 = A.shape[2]
+    T12 = np.einsum("abc,ia,jb->ijc", G.astype(np.float64), Us[0].astype(np.float64),
+                    Us[1].astype(np.float64), optimize=True)
+    num, den = 0.0, 0.0
+    U3 = Us[2].astype(np.float64)
+    for k0 in range(0, n3, 50):
+        Ah = np.einsum("ijc,kc->ijk", T12, U3[k0:k0 + 50], optimize=True)
+        Ak = A[:, :, k0:k0 + 50].astype(np.float64)
+        D = Ak - Ah
+        num += float(np.sum(D * D))
+        den += float(np.sum(Ak * Ak))
+    return float(np.sqrt(num / den))
+
+
+@pytest.mark.parametrize("form", ["plain", "bf16_power"])
+def test_invradius1000_matches_the_oracle(lib, tensor, form):
+    A, g = tensor
+    n, r = g["n"], g["r"]
+    gold = g["forms"][form]
+    prec = api.TK_PREC_BF16_POWER if form == "bf16_power" else api.TK_PREC_PLAIN
+    Ad = api.to_device(A, np.float32)
+    core = torch.empty(int(np.prod(r)), dtype=torch.float32, device="cuda")
+    U = [torch.empty(n * r[k], dtype=torch.float32, device="cuda") for k in range(3)]
+    opts = api.make_opts(3, g["q"], g["s"], seed=0, prec=prec)
+    api.tucker_rsthosvd(Ad, [n] * 3, r, opts, core, U)
+    rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+    api.tucker_error(Ad, [n] * 3, core, r, U, rel)
+    torch.cuda.synchronize()
+    re_kernel = float(rel.item())
+    G = api.from_device(core, r)
+    Us = [api.from_device(U[k], [n, r[k]]) for k in range(3)]
+    del Ad
+    re_gpu = _fp64_rel_error(A, G, Us)
+    re_o = gold["rel_err"]
+    assert re_gpu <= 1.02 * re_o, (form, re_gpu, re_o, re_gpu / re_o)
+    assert re_kernel <= 1.02 * re_o, (form, re_kernel, re_o, re_kernel / re_o)
+    assert abs(re_kernel - re_gpu) <= 0.01 * re_gpu, (form, re_kernel, re_gpu)
+    Uw = np.load(GOLD_U)
+    for k in range(3):
+        j = gold["modes"][k]["separated_block"]
+        assert j >= 1, (form, k, j)
+        Ug = Us[k].astype(np.float64)
+        assert np.abs(Ug.T @ Ug - np.eye(r[k])).max() <= 1e-6
+        s = T.principal_sines(Ug[:, :j], Uw["%s_U%d" % (form, k)].astype(np.float64)).max()
+        assert s <= 1e-5, (form, k, j, s)
