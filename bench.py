@@ -68,6 +68,10 @@ WORKLOADS = {
                                            "p=10, q=3, precision form (a small profiling case)",
                                       shape=[512, 512, 512], r=[50, 50, 50], s=10, q=3, st=True,
                                       dtype="f32", prec=1),
+    "invradius512_fp32_st": dict(desc="as invradius512_bf16power_st in plain FP32 (a small "
+                                      "profiling case)",
+                                 shape=[512, 512, 512], r=[50, 50, 50], s=10, q=3, st=True,
+                                 dtype="f32", prec=0),
     "superdiag600slow_fp32_st_pve": dict(desc="600^3 FP32 tensor C of Section 5.1 (superdiagonal "
                                               "core v_i = 1/i^2, Haar factors); Algorithm 4: "
                                               "ST-HOSVD with per-mode power counts chosen by "

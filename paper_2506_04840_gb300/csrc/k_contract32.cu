@@ -211,13 +211,14 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
 // carry rounding errors of the size of their running sums, which for the
 // weak directions of Y = X W are many times the result; with the fold only
 // the slab sums' own rounding (a few products' worth) is left.
-template <int WI, int WC, bool OMEGA, bool COMP = false>
+template <int WI, int WC, bool OMEGA, bool COMP = false, bool SHADOW = false>
 __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n, int64_t cols,
                                           const float* __restrict__ W, int l, int lc,
                                           uint64_t seed, uint32_t tag, int mode, int64_t cps,
                                           int64_t ka, int64_t kb, float* __restrict__ part,
                                           unsigned bx, unsigned by, unsigned bz,
-                                          float* __restrict__ part_lo = nullptr) {
+                                          float* __restrict__ part_lo = nullptr,
+                                          __nv_bfloat16* __restrict__ shadow = nullptr) {
   constexpr int MI = 64 * WI, MC = 16 * WC, T = 32 * WI * WC;
   constexpr int XPT = KS * MI / T;
   constexpr int BPT = (KS * MC + T - 1) / T;
@@ -246,13 +247,21 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
     for (int q = 0; q < 4; ++q) cmp[a][q] = 0.f;
 
   float xr[XPT], br[OMEGA ? 4 * OPT : BPT];
+  // shadow: the sketch pass also writes the bfloat16 copy of X (round to
+  // nearest even), each element once (from the blocks of the first output
+  // tile), so the precision form needs no separate conversion pass
+  const bool wshadow = SHADOW && by == 0;
   auto load = [&](int64_t j0) {
 #pragma unroll
     for (int r = 0; r < XPT; ++r) {
       const int e = tid + r * T;
       const int ii = e % MI, jj = e / MI;
       const int64_t i = i0 + ii, j = j0 + jj;
-      xr[r] = (i < n && j < je) ? __ldg(X + j * n + i) : 0.f;
+      const bool in = i < n && j < je;
+      xr[r] = in ? __ldg(X + j * n + i) : 0.f;
+      if constexpr (SHADOW) {
+        if (wshadow && in) shadow[j * n + i] = __float2bfloat16_rn(xr[r]);
+      }
     }
     if (OMEGA) {
 #pragma unroll
@@ -419,13 +428,15 @@ k_xtb32_red_batch(const Xtb32RedJob* __restrict__ jobs, const uint32_t* __restri
   }
 }
 
-template <int WI, int WC, bool OMEGA, bool COMP = false>
+template <int WI, int WC, bool OMEGA, bool COMP = false, bool SHADOW = false>
 __global__ void __launch_bounds__(32 * WI * WC)
 k_xb32(const float* __restrict__ X, int64_t n, int64_t cols, const float* __restrict__ W, int l,
        int lc, uint64_t seed, uint32_t tag, int mode, int64_t cps, int64_t ka, int64_t kb,
-       float* __restrict__ part, float* __restrict__ part_lo) {
-  xb32_body<WI, WC, OMEGA, COMP>(X, n, cols, W, l, lc, seed, tag, mode, cps, ka, kb, part,
-                                 blockIdx.x, blockIdx.y, blockIdx.z, part_lo);
+       float* __restrict__ part, float* __restrict__ part_lo,
+       __nv_bfloat16* __restrict__ shadow) {
+  xb32_body<WI, WC, OMEGA, COMP, SHADOW>(X, n, cols, W, l, lc, seed, tag, mode, cps, ka, kb,
+                                         part, blockIdx.x, blockIdx.y, blockIdx.z, part_lo,
+                                         shadow);
 }
 
 template <int WJ, int WC, bool COMP>
@@ -767,35 +778,39 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
 template <int WI, int WC>
 static void xb32_go(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
                     int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
-                    cudaStream_t st, float* part_lo) {
+                    cudaStream_t st, float* part_lo, __nv_bfloat16* shadow) {
   const dim3 grid(s.gx, s.gy, s.splits);
-  if (W == nullptr)
+  if (W == nullptr && shadow != nullptr)
+    c32::k_xb32<WI, WC, true, false, true><<<grid, 32 * WI * WC, 0, st>>>(
+        X, v.n, v.cols(), nullptr, l, s.lc, seed, tag, mode, s.cps, ka, kb, part, nullptr,
+        shadow);
+  else if (W == nullptr)
     c32::k_xb32<WI, WC, true><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), nullptr, l, s.lc,
                                                              seed, tag, mode, s.cps, ka, kb, part,
-                                                             nullptr);
+                                                             nullptr, nullptr);
   else if (part_lo != nullptr)
     c32::k_xb32<WI, WC, false, true><<<grid, 32 * WI * WC, 0, st>>>(
-        X, v.n, v.cols(), W, l, s.lc, seed, tag, mode, s.cps, ka, kb, part, part_lo);
+        X, v.n, v.cols(), W, l, s.lc, seed, tag, mode, s.cps, ka, kb, part, part_lo, nullptr);
   else
     c32::k_xb32<WI, WC, false><<<grid, 32 * WI * WC, 0, st>>>(X, v.n, v.cols(), W, l, s.lc,
                                                               seed, tag, mode, s.cps, ka, kb,
-                                                              part, nullptr);
+                                                              part, nullptr, nullptr);
 }
 
 template <int WI>
 static void xb32_wc(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
                     int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
-                    cudaStream_t st, float* part_lo) {
+                    cudaStream_t st, float* part_lo, __nv_bfloat16* shadow) {
   switch (s.wc) {
-    case 1: xb32_go<WI, 1>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
-    case 2: xb32_go<WI, 2>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
-    default: xb32_go<WI, 4>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo); break;
+    case 1: xb32_go<WI, 1>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo, shadow); break;
+    case 2: xb32_go<WI, 2>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo, shadow); break;
+    default: xb32_go<WI, 4>(X, v, W, l, seed, tag, mode, part, ka, kb, s, st, part_lo, shadow); break;
   }
 }
 
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka,
-                        int64_t kb, void* part_lo) {
+                        int64_t kb, void* part_lo, void* shadow) {
   if (ka <= 0) {   // natural layout: the identity map
     ka = v.cols();
     kb = 1;
@@ -807,10 +822,11 @@ cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t se
   const float* w = (const float*)W;
   float* p = (float*)part;
   float* plo = W != nullptr ? (float*)part_lo : nullptr;
+  __nv_bfloat16* sh = W == nullptr ? (__nv_bfloat16*)shadow : nullptr;
   switch (s.wi) {
-    case 1: xb32_wc<1>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
-    case 2: xb32_wc<2>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
-    default: xb32_wc<4>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo); break;
+    case 1: xb32_wc<1>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo, sh); break;
+    case 2: xb32_wc<2>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo, sh); break;
+    default: xb32_wc<4>(x, v, w, l, seed, tag, mode, p, ka, kb, s, st, plo, sh); break;
   }
   return cudaGetLastError();
 }

@@ -387,6 +387,7 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
       return launch_batch_c32(b, st);
     case BK_TC32SPLIT:
     case BK_TC32XTB:
+    case BK_TC32SKETCH:
       return launch_batch_tc32(b, st);
     default:
       return launch_batch_misc(b, st);

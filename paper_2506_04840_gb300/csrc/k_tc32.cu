@@ -452,6 +452,316 @@ k_split_b_batch(const Tc32SplitJob* __restrict__ jobs, const uint32_t* __restric
 }  // namespace tc
 
 
+// ===========================================================================
+// The sketch Y_part = X_(k) Omega_k on tcgen05 tensor cores in 3xTF32, for an
+// FP32 mode-major view (Algorithms 2/3, first product of each mode):
+//   part[g][i][c] = sum_{j in column group g} X[i, j] Omega_k(jk, c)
+// with Omega_k generated in the kernel from the library's Philox
+// definition, jk the column's index in the unfolding's order.  X arrives
+// MN-major (rows contiguous) and kind::tf32 takes its A operand K-major only,
+// so converter warps move each X tile into tensor memory as x_hi (low 13
+// mantissa bits cleared) and x_lo = x - x_hi; Omega's hi/lo split goes to
+// shared memory K-major.  D += X_hi W_hi + X_hi W_lo + X_lo W_hi, all three
+// with A from tensor memory.  FP32 accumulation in TMEM rounds toward zero;
+// the sketch only fixes the starting subspace of the power steps, and the
+// column groups (a few thousand columns) are summed in FP64 afterwards.
+//
+// Work unit: 256 rows (two M = 128 tiles) x one column group; stage: 32
+// columns (8 TMA boxes of 32 rows x 32 columns, 32 KB) + Omega hi/lo (16 KB),
+// three stages.  TMEM: the unit's accumulators (2 x 64 columns) and per stage
+// the two tiles' X_hi | X_lo (2 x 64 columns): 512.  Roles as k_tc32_xtb.
+// ===========================================================================
+namespace tc {
+
+constexpr int S_THREADS = 320;
+constexpr int S_NS = 3;
+constexpr int S_BOX = 32 * 32 * 4;                  // 4 KB: 32 rows x 32 columns
+constexpr int S_ATILE = 4 * S_BOX;                  // 16 KB: 128 rows
+constexpr int S_BHALF = 64 * 32 * 4;                // 8 KB
+constexpr int S_STAGE = 2 * S_ATILE + 2 * S_BHALF;  // 48 KB
+constexpr uint32_t S_A0 = 128;                      // first TMEM column of the A regions
+
+__device__ __forceinline__ void sketch_locate(const Tc32SketchJob* jobs, const uint32_t* start,
+                                              int njobs, long long u, int* jb, int* rb, int* g,
+                                              long long* j0, int* nst) {
+  int j = 0;
+  long long lu = u;
+  if (start != nullptr) {
+    j = batch_job(start, njobs, (uint32_t)u);
+    lu = u - (long long)__ldg(start + j);
+  }
+  const Tc32SketchJob& J = jobs[j];
+  *jb = j;
+  *rb = (int)(lu % J.nrb);
+  *g = (int)(lu / J.nrb);
+  *j0 = (long long)(*g) * J.cpg;
+  const long long je = min(J.cols, *j0 + J.cpg);
+  *nst = (int)((je - *j0 + 31) / 32);
+}
+
+__device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uint32_t* start,
+                                            int njobs, long long total, bool table) {
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  __shared__ XtbBars bars;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long my_units =
+      (long long)blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S_NS; ++s) {
+      mbar_init(smem_u32(&bars.full[s]), 1);
+      mbar_init(smem_u32(&bars.conv[s]), 4);
+      mbar_init(smem_u32(&bars.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bars.accf[0]), 1);
+    mbar_init(smem_u32(&bars.acce[0]), 4);
+    mbar_init(smem_u32(&bars.drain), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(512u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (X only) ----------------
+    if (lane == 0 && my_units > 0) {
+      long long it = 0;
+      int cur = -1;
+      for (long long ul = 0; ul < my_units && !abort_flag; ++ul) {
+        int jb, rb, g, nst;
+        long long j0;
+        sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
+                      &j0, &nst);
+        const Tc32SketchJob* J = jobs + jb;
+        if (jb != cur) {
+          cur = jb;
+          if (table)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;"
+                         :: "l"((uint64_t)&J->mx) : "memory");
+        }
+        for (int ks = 0; ks < nst; ++ks, ++it) {
+          const int s = (int)(it % S_NS);
+          const uint32_t use = (uint32_t)(it / S_NS);
+          if (!mbar_wait(smem_u32(&bars.empty[s]), (use & 1) ^ 1, &abort_flag)) break;
+          const uint32_t fb = smem_u32(&bars.full[s]);
+          mbar_expect_tx(fb, (uint32_t)(2 * S_ATILE));
+          const uint32_t dst = smem_u32(sm + s * S_STAGE);
+          const int jc = (int)(j0 + (long long)ks * 32);
+#pragma unroll
+          for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int bx = 0; bx < 4; ++bx)
+              tma_load_2d(dst + t * S_ATILE + bx * S_BOX, &J->mx, rb * 256 + t * 128 + bx * 32,
+                          jc, fb);
+        }
+      }
+      const long long first = it > S_NS ? it - S_NS : 0;
+      for (long long v = first; v < it; ++v) {
+        const int s = (int)(v % S_NS);
+        const uint32_t use = (uint32_t)(v / S_NS);
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(smem_u32(&bars.full[s]), use & 1) && now_ns() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: A from TMEM, B (Omega) from shared memory ----------------
+    if (lane == 0 && my_units > 0) {
+      const uint32_t ID = idesc_tf32(128, 64, 0, 0);
+      long long it = 0;
+      bool ok = true;
+      for (long long ul = 0; ul < my_units && ok; ++ul) {
+        int jb, rb, g, nst;
+        long long j0;
+        sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
+                      &j0, &nst);
+        if (!mbar_wait(smem_u32(&bars.acce[0]), ((uint32_t)ul & 1) ^ 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        for (int ks = 0; ks < nst; ++ks, ++it) {
+          const int s = (int)(it % S_NS);
+          const uint32_t use = (uint32_t)(it / S_NS);
+          if (!mbar_wait(smem_u32(&bars.conv[s]), use & 1, &abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t bb = smem_u32(sm + s * S_STAGE + 2 * S_ATILE);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const uint32_t d = tmem + (uint32_t)(t * 64);
+            const uint32_t ah = tmem + S_A0 + (uint32_t)((s * 2 + t) * 64);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t dbh = desc_sw128(bb + kk * 32, 16, 1024);
+              const uint64_t dbl = desc_sw128(bb + S_BHALF + kk * 32, 16, 1024);
+              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), dbh, ID, (ks | kk) != 0);
+              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), dbl, ID, 1);
+              mma_tf32_ts(d, ah + 32u + (uint32_t)(kk * 8), dbh, ID, 1);
+            }
+          }
+          mma_commit(smem_u32(&bars.empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars.accf[0]));
+      }
+      mma_commit(smem_u32(&bars.drain));
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(smem_u32(&bars.drain), 0) && now_ns() - t0 < WAIT_NS) {
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters: X -> TMEM (hi | lo), Omega -> shared ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int ctid = (warp - 2) * 32 + lane;     // 0..127
+    long long it = 0;
+    bool ok = true;
+    for (long long ul = 0; ul < my_units && ok; ++ul) {
+      int jb, rb, g, nst;
+      long long j0;
+      sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
+                    &j0, &nst);
+      const Tc32SketchJob& J = jobs[jb];
+      for (int ks = 0; ks < nst; ++ks, ++it) {
+        const int s = (int)(it % S_NS);
+        const uint32_t use = (uint32_t)(it / S_NS);
+        if (!mbar_wait(smem_u32(&bars.full[s]), use & 1, &abort_flag)) { ok = false; break; }
+        unsigned char* st0 = sm + s * S_STAGE;
+#pragma unroll 1
+        for (int t = 0; t < 2; ++t) {
+          // TMEM lane 32 q + lane = row 32 q + lane of tile t = row `lane` of box q
+          const unsigned char* box = st0 + t * S_ATILE + q * S_BOX;
+          uint32_t hi[32], lo[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float x = *reinterpret_cast<const float*>(
+                box + j * 128 + ((((lane >> 2) ^ (j & 7))) << 4) + (lane & 3) * 4);
+            const float h = tf32_hi(x);
+            hi[j] = __float_as_uint(h);
+            lo[j] = __float_as_uint(__fsub_rn(x, h));
+          }
+          const uint32_t ta = tmem + lane_off + S_A0 + (uint32_t)((s * 2 + t) * 64);
+          tmem_st32(ta, hi);
+          tmem_st32(ta + 32u, lo);
+          if (J.shadow != nullptr) {
+            // the precision form's bfloat16 copy of X, written as the pass reads X
+            const int i = rb * 256 + t * 128 + q * 32 + lane;
+            const long long jb0 = j0 + (long long)ks * 32;
+            if (i < J.n) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (jb0 + j < J.cols)
+                  J.shadow[(jb0 + j) * J.n + i] =
+                      __float2bfloat16_rn(__uint_as_float(hi[j]) + __uint_as_float(lo[j]));
+            }
+          }
+        }
+        // Omega rows j0 + 32 ks + jj (layout order), groups of four columns
+        unsigned char* bt = st0 + 2 * S_ATILE;
+        const int jj = ctid & 31;
+        const long long jg = j0 + (long long)ks * 32 + jj;
+        // four independent generator chains per thread, interleaved (one
+        // converter warp per SM sub-partition: latency is hidden by ILP)
+#pragma unroll
+        for (int r4 = 0; r4 < 4; ++r4) {
+          const int gq = (ctid >> 5) + 4 * r4;    // 0..15
+          float w4[4] = {0.f, 0.f, 0.f, 0.f};
+          if (jg < J.cols && 4 * gq < J.l)
+            omega4((uint64_t)(jg / J.ka + J.kb * (jg % J.ka)), gq, J.mode, J.tag, J.seed, w4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 4 * gq + e;
+            const float w = c < J.l ? w4[e] : 0.f;
+            const float h = tf32_hi(w);
+            const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 +
+                                            ((((jj * 4) >> 4) ^ (c & 7)) << 4) + ((jj * 4) & 15));
+            *reinterpret_cast<float*>(bt + off) = h;
+            *reinterpret_cast<float*>(bt + S_BHALF + off) = __fsub_rn(w, h);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tmem_st_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars.conv[s]));
+      }
+    }
+  } else {
+    // ---------------- epilogue: the unit's partial rows ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    for (long long ul = 0; ul < my_units; ++ul) {
+      int jb, rb, g, nst;
+      long long j0;
+      sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
+                    &j0, &nst);
+      const Tc32SketchJob& J = jobs[jb];
+      if (!mbar_wait(smem_u32(&bars.accf[0]), (uint32_t)ul & 1, &abort_flag)) break;
+      fence_after();
+      uint32_t r0[32], r1[32], r2[32], r3[32];
+      tmem_ld32(tmem + lane_off, r0);
+      tmem_ld32(tmem + lane_off + 32u, r1);
+      tmem_ld32(tmem + lane_off + 64u, r2);
+      tmem_ld32(tmem + lane_off + 96u, r3);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.acce[0]));
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int i = rb * 256 + t * 128 + q * 32 + lane;
+        if (i >= J.n) continue;
+        const uint32_t* a = t == 0 ? r0 : r2;
+        const uint32_t* b = t == 0 ? r1 : r3;
+        float4* o = reinterpret_cast<float4*>(J.part + ((long long)g * J.n + i) * 64);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          o[c] = make_float4(__uint_as_float(a[4 * c]), __uint_as_float(a[4 * c + 1]),
+                             __uint_as_float(a[4 * c + 2]), __uint_as_float(a[4 * c + 3]));
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          o[8 + c] = make_float4(__uint_as_float(b[4 * c]), __uint_as_float(b[4 * c + 1]),
+                                 __uint_as_float(b[4 * c + 2]), __uint_as_float(b[4 * c + 3]));
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0 && my_units > 0) {
+    int jb, rb, g, nst;
+    long long j0;
+    sketch_locate(jobs, start, njobs, (long long)blockIdx.x, &jb, &rb, &g, &j0, &nst);
+    atomicExch(jobs[jb].err, (int)TK_ETIMEOUT);
+  }
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(512u) : "memory");
+  }
+}
+
+__global__ void __launch_bounds__(S_THREADS, 1)
+k_tc32_sketch(const __grid_constant__ Tc32SketchJob job) {
+  sketch_body(&job, nullptr, 1, job.units, false);
+}
+
+__global__ void __launch_bounds__(S_THREADS, 1)
+k_tc32_sketch_batch(const Tc32SketchJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                    int njobs, uint32_t total) {
+  sketch_body(jobs, start, njobs, (long long)total, true);
+}
+
+}  // namespace tc
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -554,9 +864,82 @@ cudaError_t launch_tc32_xtb(const void* X, View v, const double* B, int64_t b_ri
   return cudaGetLastError();
 }
 
+
+int tc32_sketch_groups(View v) {
+  // about eight units per SM; column groups of at least 32 columns
+  const long long nrb = (v.n + 255) / 256;
+  const long long want = std::max<long long>(1, 8LL * num_sms() / nrb);
+  long long cpg = (v.cols() + want - 1) / want;
+  cpg = std::max<long long>(32, (cpg + 31) / 32 * 32);
+  return (int)((v.cols() + cpg - 1) / cpg);
+}
+
+size_t tc32_sketch_part_bytes(View v) {
+  return (size_t)tc32_sketch_groups(v) * v.n * 64 * sizeof(float) + 256;
+}
+
+size_t tc32_sketch_smem() { return (size_t)tc::S_NS * tc::S_STAGE + 1024; }
+
+bool tc32_sketch_job(const void* X, View v, int l, uint64_t seed, uint32_t tag, int mode,
+                     int64_t ka, int64_t kb, float* part, int* err, void* shadow,
+                     Tc32SketchJob* j) {
+  if (!tc32_ok(v, l, X)) return false;
+  std::memset(j, 0, sizeof(*j));
+  if (!map_f32(&j->mx, X, (uint64_t)v.n, (uint64_t)v.cols(), (uint64_t)v.n, 32)) return false;
+  const int groups = tc32_sketch_groups(v);
+  const long long cpg0 = (v.cols() + groups - 1) / groups;
+  j->part = part;
+  j->err = err;
+  j->shadow = (__nv_bfloat16*)shadow;
+  j->cols = v.cols();
+  j->cpg = (cpg0 + 31) / 32 * 32;
+  j->groups = (int)((v.cols() + j->cpg - 1) / j->cpg);
+  j->n = (int)v.n;
+  j->nrb = (int)((v.n + 255) / 256);
+  j->units = (long long)j->nrb * j->groups;
+  if (ka <= 0) {
+    ka = v.cols();
+    kb = 1;
+  }
+  j->ka = ka;
+  j->kb = kb;
+  j->seed = seed;
+  j->tag = tag;
+  j->l = l;
+  j->mode = mode;
+  return true;
+}
+
+static void tc32_sketch_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int smem = (int)tc32_sketch_smem();
+  cudaFuncSetAttribute(tc::k_tc32_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(tc::k_tc32_sketch_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem);
+  done = true;
+}
+
+cudaError_t launch_tc32_sketch(const Tc32SketchJob& j, cudaStream_t st) {
+  tc32_sketch_attrs();
+  const long long grid = std::min<long long>(j.units, (long long)num_sms());
+  count_kernels(1);
+  tc::k_tc32_sketch<<<(unsigned)grid, tc::S_THREADS, tc32_sketch_smem(), st>>>(j);
+  return cudaGetLastError();
+}
+
+
 cudaError_t launch_batch_tc32(const BatchLaunch& b, cudaStream_t st) {
   if (b.total == 0 || b.njobs == 0) return cudaSuccess;
   if (b.kind == BK_TC32SPLIT) return run_batch(tc::k_split_b_batch, b, 256, st);
+  if (b.kind == BK_TC32SKETCH) {
+    tc32_sketch_attrs();
+    const unsigned grid = (unsigned)std::min<long long>((long long)b.total, (long long)num_sms());
+    count_kernels(1);
+    tc::k_tc32_sketch_batch<<<grid, tc::S_THREADS, tc32_sketch_smem(), st>>>(
+        (const Tc32SketchJob*)b.jobs, b.start, b.njobs, b.total);
+    return cudaGetLastError();
+  }
   if (b.kind != BK_TC32XTB) return cudaErrorInvalidValue;
   tc32_attrs();
   const unsigned grid = (unsigned)std::min<long long>((long long)b.total, (long long)num_sms());

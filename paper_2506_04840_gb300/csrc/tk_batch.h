@@ -9,6 +9,7 @@
 
 #include <cuda.h>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -149,6 +150,22 @@ struct alignas(64) Tc32XtbJob {
   int out_mode;       // 0: out[c + m j]; 1: out[j + cols c]; 2: planes (hi, lo)
 };
 
+// The sketch Y_part = X_(k) Omega_k on the tensor cores (k_tc32.cu) for one
+// problem: units of 256 rows x one column group, partials part[g][n][64].
+struct alignas(64) Tc32SketchJob {
+  CUtensorMap mx;     // X_(k): inner n (rows), outer cols, box 32 x 32
+  float* part;        // [groups][n][64] FP32 partials
+  int* err;
+  __nv_bfloat16* shadow;  // or NULL: also write the bfloat16 copy of X (RNE)
+  long long cols;
+  long long cpg;      // columns per group (multiple of 32)
+  long long units;    // nrb * groups
+  long long ka, kb;   // Omega row map of the layout (jk = j / ka + kb (j % ka))
+  uint64_t seed;
+  uint32_t tag;
+  int n, nrb, groups, l, mode;
+};
+
 // B (n x m, FP64) -> its hi/lo TF32 planes for one problem.
 struct Tc32SplitJob {
   const double* B;
@@ -159,7 +176,7 @@ struct Tc32SplitJob {
 
 enum BatchKind {
   BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
-  BK_XB32, BK_XTB32RED, BK_ERR32, BK_TC32SPLIT, BK_TC32XTB
+  BK_XB32, BK_XTB32RED, BK_ERR32, BK_TC32SPLIT, BK_TC32XTB, BK_TC32SKETCH
 };
 
 constexpr size_t kJobBytes = 384;   // every job struct fits (two tensor maps + sizes)
@@ -193,7 +210,15 @@ bool tc32_xtb_jobs(const void* X, View v, const double* B, int64_t b_ri, int64_t
                    Tc32SplitJob* sj, Tc32XtbJob* xj);
 uint32_t tc32_split_blocks(const Tc32SplitJob& j);
 size_t tc32_xtb_smem();
-
+// The tensor-core sketch of one problem (false when not eligible); its
+// partial count (column groups) and bytes.
+bool tc32_sketch_job(const void* X, View v, int l, uint64_t seed, uint32_t tag, int mode,
+                     int64_t ka, int64_t kb, float* part, int* err, void* shadow,
+                     Tc32SketchJob* j);
+int tc32_sketch_groups(View v);
+size_t tc32_sketch_part_bytes(View v);
+size_t tc32_sketch_smem();
+cudaError_t launch_tc32_sketch(const Tc32SketchJob& j, cudaStream_t st);
 // Launch shapes of the FP32 mode-major kernels.
 struct Xtb32Shape {
   int wj, wc, gx, gy, threads, ks;

@@ -79,9 +79,11 @@ int err32_blocks(View v, int m);
 cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, const void* A, double* err_part, cudaStream_t st,
                          const float* B32 = nullptr);
+// shadow (sketch only, may be NULL): also write the bfloat16 copy of X
+// (round to nearest even) in the same pass.
 cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t seed, uint32_t tag,
                         int mode, void* part, int splits, cudaStream_t st, int64_t ka = 0,
-                        int64_t kb = 1, void* part_lo = nullptr);
+                        int64_t kb = 1, void* part_lo = nullptr, void* shadow = nullptr);
 // ka, kb: Omega row map of a rotated layout (see launch_xb32; FP32
 // mode-major views only; ka = 0 is the natural layout).
 // part_lo (FP32 mode-major Y = X W only): compensated accumulation, the

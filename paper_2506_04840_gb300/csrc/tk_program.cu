@@ -44,6 +44,7 @@ size_t job_size(int kind) {
     case BK_XB32: return sizeof(Xb32Job);
     case BK_TC32SPLIT: return sizeof(Tc32SplitJob);
     case BK_TC32XTB: return sizeof(Tc32XtbJob);
+    case BK_TC32SKETCH: return sizeof(Tc32SketchJob);
     default: return sizeof(ErrFinalJob);
   }
 }
@@ -218,9 +219,20 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     // ---- sketch phase
     {
       Phase ph;
-      ph.push_back(xb_op(0, TK_K_SKETCH, xt, X, v, nullptr, l, it.seed, it.tag, k, w.part, splits,
-                         N * es, 2.0 * N * l, ka, kb));
-      ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, splits, l, lc, nullptr};
+      Tc32SketchJob skj;
+      int sp = splits, slc = lc;
+      if (xt == X_F32 && tc32_sketch_job(X, v, l, it.seed, it.tag, k, ka, kb, (float*)w.part,
+                                         w.status, nullptr, &skj)) {
+        // the sketch on the tensor cores, as the single call runs it
+        ph.push_back(make_op(0, TK_K_SKETCH, BK_TC32SKETCH, xt, 0, 0, tc32_sketch_smem(),
+                             (uint32_t)skj.units, N * es, 2.0 * N * l, skj));
+        sp = skj.groups;
+        slc = 64;
+      } else {
+        ph.push_back(xb_op(0, TK_K_SKETCH, xt, X, v, nullptr, l, it.seed, it.tag, k, w.part,
+                           splits, N * es, 2.0 * N * l, ka, kb));
+      }
+      ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, sp, l, slc, nullptr};
       ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
       SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,

@@ -12,6 +12,7 @@
 
 #include "tk_common.cuh"
 #include "tk_internal.h"
+#include "tk_batch.h"
 #include "tk_plan.h"
 
 namespace tk {
@@ -141,9 +142,12 @@ tk_status make_plan(const tk_tensor* A, const int* r, const tk_opts* o, bool st,
     p.sp[k] = small_plan(v.n, (int)lk, p.xt == X_F64);
     if (p.sp[k].Pb <= 0) return TK_ENOTIMPL;
     p.small = std::max(p.small, p.sp[k].scratch_bytes);
-    // the tensor-core W = X^T Q splits Q into that scratch
-    if (p.q > 0 && p.xt == X_F32 && v.P == 1 && (v.n % 4) == 0 && lk <= 64)
-      p.small = std::max(p.small, tc32_xtb_scratch(v));
+    // the tensor-core W = X^T Q splits Q into that scratch; the tensor-core
+    // sketch writes its column-group partials into the partial buffer
+    if (p.xt == X_F32 && v.P == 1 && (v.n % 4) == 0 && lk <= 64) {
+      if (p.q > 0) p.small = std::max(p.small, tc32_xtb_scratch(v));
+      p.part = std::max(p.part, tc32_sketch_part_bytes(v));
+    }
     if (p.xt != X_F64) p.small = std::max(p.small, polish_scratch(v.n, p.r[k]));
     const int lc = xb_lc((int)lk);
     const int splits = xb_splits(p.xt, v, (int)lk);
@@ -248,14 +252,33 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     TK_TRY(launch_omega_fill(p.omega, p.dims_at[k].data(), p.d, k, l, seed, tag, ka, kb, w.kr,
                              w.w, fp64, v.P, st));
   }
+  // precision form on an FP32 mode-major view: the sketch pass writes the
+  // bfloat16 copy of X as it reads X (no separate conversion pass)
+  const bool fuse_shadow = p.bf16 && p.q >= 2 && !shadow_ready && dense_gauss &&
+                           xtb32_ok(xt, v, X);
+  // FP32 mode-major views with Gaussian Omega: the sketch on the tensor cores
+  Tc32SketchJob skj;
+  const bool tc_sketch = xt == X_F32 && dense_gauss &&
+                         tc32_sketch_job(X, v, l, seed, tag, k, ka, kb, (float*)w.part, w.status,
+                                         fuse_shadow ? w.shadow : nullptr, &skj);
   {
-    ProfScope ps(TK_K_SKETCH, N * xsize(xt) + om_bytes, 2.0 * N * l, st);
-    TK_TRY(launch_xb(xt, X, v, dense_gauss ? nullptr : w.w, l, seed, tag, k, w.part, splits, st,
-                     ka, kb));
+    ProfScope ps(TK_K_SKETCH, N * xsize(xt) + om_bytes + (fuse_shadow ? N * 2.0 : 0.0),
+                 2.0 * N * l, st);
+    if (tc_sketch)
+      TK_TRY(launch_tc32_sketch(skj, st));
+    else if (fuse_shadow)
+      TK_TRY(launch_xb32(X, v, nullptr, l, seed, tag, k, w.part, splits, st, ka, kb, nullptr,
+                         w.shadow));
+    else
+      TK_TRY(launch_xb(xt, X, v, dense_gauss ? nullptr : w.w, l, seed, tag, k, w.part, splits,
+                       st, ka, kb));
   }
   {
-    ProfScope ps(TK_K_CONVERT, red_bytes, (double)splits * nl, st);
-    TK_TRY(launch_reduce(xt, w.part, splits, v.n, l, lc, nullptr, nullptr, w.Y, st));
+    const int sp = tc_sketch ? skj.groups : splits;
+    const int slc = tc_sketch ? 64 : lc;
+    ProfScope ps(TK_K_CONVERT, (double)sp * v.n * slc * asize(xt) + nl * 8.0, (double)sp * nl,
+                 st);
+    TK_TRY(launch_reduce(xt, w.part, sp, v.n, l, slc, nullptr, nullptr, w.Y, st));
   }
   TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
   {
@@ -265,7 +288,7 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
     TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false,
                             w.alpha, nullptr, nullptr, w.status, st, p.q >= 1));
   }
-  if (p.bf16 && p.q >= 2 && !shadow_ready) {
+  if (p.bf16 && p.q >= 2 && !shadow_ready && !fuse_shadow) {
     ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
     TK_TRY(launch_to_bf16((const float*)X, v.P * v.n * v.S, (uint16_t*)w.shadow, st));
   }

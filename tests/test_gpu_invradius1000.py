@@ -12,7 +12,9 @@ absolute 1e-6 difference would pass anything):
   RE_gpu <= 1.02 RE_oracle;
 * the library's own error pass (tucker_error) within 1.02 RE_oracle too;
 * principal-angle sines <= 1e-5 between the returned factors and the
-  oracle's on each mode's well-separated leading block.
+  oracle's on each mode's well-separated leading block;
+* the precision form's error within 1% of the plain FP32 form's, both by the
+  library's error pass (the oracle's two forms differ by 0.39% here).
 """
 import json
 import os
@@ -59,6 +61,9 @@ def _fp64_rel_error(A, G, Us):
     return float(np.sqrt(num / den))
 
 
+_RESULTS = {}
+
+
 @pytest.mark.parametrize("form", ["plain", "bf16_power"])
 def test_invradius1000_matches_the_oracle(lib, tensor, form):
     A, g = tensor
@@ -74,6 +79,7 @@ def test_invradius1000_matches_the_oracle(lib, tensor, form):
     api.tucker_error(Ad, [n] * 3, core, r, U, rel)
     torch.cuda.synchronize()
     re_kernel = float(rel.item())
+    _RESULTS[form] = re_kernel
     G = api.from_device(core, r)
     Us = [api.from_device(U[k], [n, r[k]]) for k in range(3)]
     del Ad
@@ -90,3 +96,13 @@ def test_invradius1000_matches_the_oracle(lib, tensor, form):
         assert np.abs(Ug.T @ Ug - np.eye(r[k])).max() <= 1e-6
         s = T.principal_sines(Ug[:, :j], Uw["%s_U%d" % (form, k)].astype(np.float64)).max()
         assert s <= 1e-5, (form, k, j, s)
+
+
+def test_invradius1000_precision_form_within_one_percent_of_plain(lib, tensor):
+    """The benchmark spec's target for the precision form: RE within 1% of the
+    plain FP32 path's on the same tensor (both measured by tucker_error)."""
+    for form in ("plain", "bf16_power"):
+        if form not in _RESULTS:
+            test_invradius1000_matches_the_oracle(lib, tensor, form)
+    re_p, re_b = _RESULTS["plain"], _RESULTS["bf16_power"]
+    assert re_b <= 1.01 * re_p, (re_b, re_p, re_b / re_p)

