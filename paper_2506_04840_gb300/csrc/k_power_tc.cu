@@ -120,11 +120,14 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
       for (int ch = 0; ch < nq; ++ch)
         tma_load_2d(smem_u32(sQ + ch * QT_CHUNK_BYTES), &tmQ, ch * CHUNK_I, cpart * NC, qb);
       long long issued = 0;
+      int slot = 0;
+      uint32_t use = 0;
       for (int k = 0; k < my_slabs && !abort_flag; ++k) {
         const int slab = group + k * ngroups;
         for (int t = 0; t < pr.nt; ++t, ++issued) {
-          const int slot = (int)(issued % pr.ring);
-          const uint32_t use = (uint32_t)(issued / pr.ring);
+          if (t > 0 || k > 0) {
+            if (++slot == pr.ring) { slot = 0; ++use; }
+          }
           if (!mbar_wait(smem_u32(&bars.empty[slot]), (use & 1) ^ 1, &abort_flag)) break;
           const uint32_t fb = smem_u32(&bars.full[slot]);
           mbar_expect_tx(fb, SUP_BYTES);
@@ -154,8 +157,11 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
       const uint32_t ID2 = idesc_bf16(128, NC, 1, 0);
       bool ok = mbar_wait(smem_u32(&bars.qfull), 0, &abort_flag);
       fence_after();
-      long long consumed = 0;
-      const uint32_t qbase = smem_u32(sQ);
+      int slot = -1;
+      uint32_t use = 0;
+      const uint64_t dring1 = desc_sw128(smem_u32(sRing), 16, 1024);
+      const uint64_t dring2 = desc_sw128(smem_u32(sRing), SUP_BYTES / 2, 1024);
+      const uint64_t dq = desc_sw128(smem_u32(sQ), 16, 1024);
       int slots[16];
       for (int k = 0; k < my_slabs && ok; ++k) {
         const int b = k & 1;
@@ -164,22 +170,19 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
         if (!mbar_wait(smem_u32(&bars.d1_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
         fence_after();
         // GEMM1: D1 = X_slab^T Q_part  (K over the n rows)
-        for (int t = 0; t < pr.nt; ++t, ++consumed) {
-          const int slot = (int)(consumed % pr.ring);
-          const uint32_t use = (uint32_t)(consumed / pr.ring);
+        for (int t = 0; t < pr.nt; ++t) {
+          if (++slot == pr.ring) { slot = 0; ++use; }
           slots[t] = slot;
           if (!mbar_wait(smem_u32(&bars.full[slot]), use & 1, &abort_flag)) { ok = false; break; }
           fence_after();
-          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+          const uint64_t da0 = desc_off(dring1, (uint32_t)slot * SUP_BYTES);
+          const uint64_t db0 = desc_off(dq, (uint32_t)(2 * t) * QT_CHUNK_BYTES);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t da = desc_sw128(sbase + h * (SUP_BYTES / 2) + kk * 32, 16, 1024);
-              const uint64_t db = desc_sw128(qbase + (2 * t + h) * QT_CHUNK_BYTES + kk * 32, 16,
-                                             1024);
-              mma_bf16(d1, da, db, ID1, (t | h | kk) != 0);
-            }
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(d1, desc_off(da0, h * (SUP_BYTES / 2) + kk * 32),
+                       desc_off(db0, h * QT_CHUNK_BYTES + kk * 32), ID1, (t | h | kk) != 0);
           }
         }
         if (!ok) break;
@@ -187,19 +190,16 @@ k_power_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
         // GEMM2: Y_tile(t) += X_tile(t) W   (K over the 64 slab columns)
         if (!mbar_wait(smem_u32(&bars.w_full[b]), v & 1, &abort_flag)) { ok = false; break; }
         fence_after();
-        const uint32_t wbase = smem_u32(sW + b * W_BYTES);
-        const uint32_t wlo = smem_u32(sW + (2 + b) * W_BYTES);
+        const uint64_t dwh = desc_sw128(smem_u32(sW + b * W_BYTES), 16, 1024);
+        const uint64_t dwl = desc_sw128(smem_u32(sW + (2 + b) * W_BYTES), 16, 1024);
         for (int t = 0; t < pr.nt; ++t) {
-          const uint32_t sbase = smem_u32(sRing + slots[t] * SUP_BYTES);
+          const uint64_t da0 = desc_off(dring2, (uint32_t)slots[t] * SUP_BYTES);
           const uint32_t yt = tmem + (uint32_t)(t * NC);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             // W = W_hi + W_lo (bfloat16 pair, ~16 bits): Y += X W_hi + X W_lo
-            const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
-            const uint64_t db = desc_sw128(wbase + kk * 32, 16, 1024);
-            const uint64_t dl = desc_sw128(wlo + kk * 32, 16, 1024);
-            mma_bf16(yt, da, db, ID2, (k | kk) != 0);
-            mma_bf16(yt, da, dl, ID2, 1);
+            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwh, kk * 32), ID2, (k | kk) != 0);
+            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwl, kk * 32), ID2, 1);
           }
           mma_commit(smem_u32(&bars.empty[slots[t]]));
         }
@@ -407,12 +407,14 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       mbar_expect_tx(qb, (uint32_t)(nq * QT2_CHUNK_BYTES));
       for (int ch = 0; ch < nq; ++ch)
         tma_load_2d(smem_u32(sQ + ch * QT2_CHUNK_BYTES), &tmQ, row0 + ch * CHUNK_I, 0, qb);
+      // slab k uses slots (k & 1) nth .. (k & 1) nth + nth - 1 (ring == 2 nth),
+      // the (k >> 1)-th time each
       long long issued = 0;
       for (int k = 0; k < my_slabs && !abort_flag; ++k) {
         const int slab = cid + k * nclusters;
+        const uint32_t use = (uint32_t)(k >> 1);
         for (int t = 0; t < pr.nth; ++t, ++issued) {
-          const int slot = (int)(issued % ring);
-          const uint32_t use = (uint32_t)(issued / ring);
+          const int slot = (k & 1) * pr.nth + t;
           if (!mbar_wait(smem_u32(&bars.empty[slot]), (use & 1) ^ 1, &abort_flag)) break;
           const uint32_t fb = smem_u32(&bars.full[slot]);
           mbar_expect_tx(fb, SUP_BYTES);
@@ -424,8 +426,9 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       }
       const long long first = issued > ring ? issued - ring : 0;
       for (long long u = first; u < issued; ++u) {
-        const int slot = (int)(u % ring);
-        const uint32_t use = (uint32_t)(u / ring);
+        const int kk = (int)(u / pr.nth);
+        const int slot = (kk & 1) * pr.nth + (int)(u - (long long)kk * pr.nth);
+        const uint32_t use = (uint32_t)(kk >> 1);
         const uint64_t t0 = now_ns();
         while (!mbar_try(smem_u32(&bars.full[slot]), use & 1) && now_ns() - t0 < WAIT_NS) {
         }
@@ -440,7 +443,10 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       const uint32_t ID1 = idesc_bf16(64, NC2, 0, 0);
       bool ok = mbar_wait(smem_u32(&bars.qfull), 0, &abort_flag);
       fence_after();
-      const uint32_t qbase = smem_u32(sQ);
+      // descriptors of the first ring slot and of Q^T; the others are at
+      // constant offsets (one add each: the issue loop stays short)
+      const uint64_t dring = desc_sw128(smem_u32(sRing), 16, 1024);
+      const uint64_t dq = desc_sw128(smem_u32(sQ), 16, 1024);
       for (int k = 0; k < my_slabs && ok; ++k) {
         const int b = k & 1;
         const uint32_t v = (uint32_t)(k >> 1);
@@ -448,21 +454,17 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
         if (!mbar_wait(smem_u32(&bars.d1_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
         fence_after();
         for (int t = 0; t < pr.nth; ++t) {
-          const long long u = (long long)k * pr.nth + t;
-          const int slot = (int)(u % ring);
-          const uint32_t use = (uint32_t)(u / ring);
-          if (!mbar_wait(smem_u32(&bars.full[slot]), use & 1, &abort_flag)) { ok = false; break; }
+          const int slot = b * pr.nth + t;
+          if (!mbar_wait(smem_u32(&bars.full[slot]), v & 1, &abort_flag)) { ok = false; break; }
           fence_after();
-          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+          const uint64_t da0 = desc_off(dring, (uint32_t)slot * SUP_BYTES);
+          const uint64_t db0 = desc_off(dq, (uint32_t)(2 * t) * QT2_CHUNK_BYTES);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t da = desc_sw128(sbase + h * (SUP_BYTES / 2) + kk * 32, 16, 1024);
-              const uint64_t db = desc_sw128(qbase + (2 * t + h) * QT2_CHUNK_BYTES + kk * 32, 16,
-                                             1024);
-              mma_bf16(d1, da, db, ID1, (t | h | kk) != 0);
-            }
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(d1, desc_off(da0, h * (SUP_BYTES / 2) + kk * 32),
+                       desc_off(db0, h * QT2_CHUNK_BYTES + kk * 32), ID1, (t | h | kk) != 0);
           }
         }
         if (!ok) break;
@@ -477,25 +479,22 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
     // ---------------- GEMM2 issuer: Y_tile += X_tile W ----------------
     if (lane == 0 && my_slabs > 0) {
       const uint32_t ID2 = idesc_bf16(128, NC2, 1, 1);
-      const uint32_t wbase = smem_u32(sW);
-      const uint32_t wlo = smem_u32(sWl);
+      const uint64_t dring = desc_sw128(smem_u32(sRing), SUP_BYTES / 2, 1024);
+      const uint64_t dwh = desc_sw128(smem_u32(sW), 1024, 1024);
+      const uint64_t dwl = desc_sw128(smem_u32(sWl), 1024, 1024);
       bool ok = true;
       for (int k = 0; k < my_slabs && ok; ++k) {
         if (!mbar_wait(smem_u32(&bars.w_full), k & 1, &abort_flag)) { ok = false; break; }
         fence_after();
         for (int t = 0; t < pr.nth; ++t) {
-          const long long u = (long long)k * pr.nth + t;
-          const int slot = (int)(u % ring);
-          const uint32_t sbase = smem_u32(sRing + slot * SUP_BYTES);
+          const int slot = (k & 1) * pr.nth + t;
+          const uint64_t da0 = desc_off(dring, (uint32_t)slot * SUP_BYTES);
           const uint32_t yt = tmem + (uint32_t)(t * NC2);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             // W = W_hi + W_lo (bfloat16 pair, ~16 bits): Y += X W_hi + X W_lo
-            const uint64_t da = desc_sw128(sbase + kk * 2048, SUP_BYTES / 2, 1024);
-            const uint64_t db = desc_sw128(wbase + kk * 2048, 1024, 1024);
-            const uint64_t dl = desc_sw128(wlo + kk * 2048, 1024, 1024);
-            mma_bf16(yt, da, db, ID2, (k | kk) != 0);
-            mma_bf16(yt, da, dl, ID2, 1);
+            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwh, kk * 2048), ID2, (k | kk) != 0);
+            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwl, kk * 2048), ID2, 1);
           }
           mma_commit(smem_u32(&bars.empty[slot]));
         }
@@ -532,14 +531,16 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
         ok = false;
         break;
       }
+      // chunk ch (four floats) of row j sits at chunk ch ^ (j & 15) of the row
       if (lane < 16) {
 #pragma unroll
         for (int c = 0; c < 32; c += 4)
-          st_async_v4(xrow_peer + c * 4, r0[c], r0[c + 1], r0[c + 2], r0[c + 3], peer_xfull);
+          st_async_v4(xrow_peer + (((c >> 2) ^ (j & 15)) << 4), r0[c], r0[c + 1], r0[c + 2],
+                      r0[c + 3], peer_xfull);
 #pragma unroll
         for (int c = 0; c < 32; c += 4)
-          st_async_v4(xrow_peer + (32 + c) * 4, r1[c], r1[c + 1], r1[c + 2], r1[c + 3],
-                      peer_xfull);
+          st_async_v4(xrow_peer + (((8 + (c >> 2)) ^ (j & 15)) << 4), r1[c], r1[c + 1], r1[c + 2],
+                      r1[c + 3], peer_xfull);
       }
       // the peer's partial for my rows (its 16 KB completes my xfull phase)
       if (!mbar_wait_cluster(smem_u32(&bars.xfull), k & 1, &abort_flag)) { ok = false; break; }
@@ -552,8 +553,9 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t* rr = ch < 4 ? r0 : r1;
           const int c0 = (ch & 3) * 8;
-          const float4 pa = *reinterpret_cast<const float4*>(px + ch * 8);
-          const float4 pb = *reinterpret_cast<const float4*>(px + ch * 8 + 4);
+          const float4 pa = *reinterpret_cast<const float4*>(px + (((2 * ch) ^ (j & 15)) << 2));
+          const float4 pb =
+              *reinterpret_cast<const float4*>(px + (((2 * ch + 1) ^ (j & 15)) << 2));
           // own partial + peer's, in the same order in both CTAs (identical W)
           uint4 ho, lo;
           split_bf16x2(__uint_as_float(rr[c0]) + pa.x, __uint_as_float(rr[c0 + 1]) + pa.y, ho.x,

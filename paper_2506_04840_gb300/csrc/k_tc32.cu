@@ -264,6 +264,8 @@ __device__ __forceinline__ void xtb_body(const Tc32XtbJob* jobs, const uint32_t*
     // ---------------- MMA issuer ----------------
     if (lane == 0 && my_units > 0) {
       const uint32_t ID = idesc_tf32(128, 64, 0, 0);
+      // stage 0's descriptors; the others are at constant offsets
+      const uint64_t dsm = desc_sw128(smem_u32(sm), 16, 1024);
       long long it = 0;
       bool ok = true;
       for (long long ul = 0; ul < my_units && ok; ++ul) {
@@ -280,16 +282,16 @@ __device__ __forceinline__ void xtb_body(const Tc32XtbJob* jobs, const uint32_t*
           const uint32_t use = (uint32_t)(it / X_NS);
           if (!mbar_wait(smem_u32(&bars.conv[s]), use & 1, &abort_flag)) { ok = false; break; }
           fence_after();
-          const uint32_t base = smem_u32(sm + s * X_STAGE);
+          const uint64_t d0 = desc_off(dsm, (uint32_t)s * X_STAGE);
 #pragma unroll
           for (int t = 0; t < X_TM; ++t) {
             const uint32_t d = tmem + (uint32_t)((b * X_TM + t) * 64);
             const uint32_t lo = tmem + X_LO0 + (uint32_t)((s * X_TM + t) * 32);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t da = desc_sw128(base + t * X_ATILE + kk * 32, 16, 1024);
-              const uint64_t dbh = desc_sw128(base + X_TM * X_ATILE + kk * 32, 16, 1024);
-              const uint64_t dbl = desc_sw128(base + X_TM * X_ATILE + X_BHALF + kk * 32, 16, 1024);
+              const uint64_t da = desc_off(d0, t * X_ATILE + kk * 32);
+              const uint64_t dbh = desc_off(d0, X_TM * X_ATILE + kk * 32);
+              const uint64_t dbl = desc_off(d0, X_TM * X_ATILE + X_BHALF + kk * 32);
               mma_tf32_ss(d, da, dbh, ID, (kc | kk) != 0);
               mma_tf32_ss(d, da, dbl, ID, 1);
               mma_tf32_ts(d, lo + (uint32_t)(kk * 8), dbh, ID, 1);
@@ -578,7 +580,10 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
     // ---------------- MMA issuer: A from TMEM, B (Omega) from shared memory ----------------
     if (lane == 0 && my_units > 0) {
       const uint32_t ID = idesc_tf32(128, 64, 0, 0);
-      long long it = 0;
+      // stage 0's Omega descriptor; the others are at constant offsets
+      const uint64_t dsm = desc_sw128(smem_u32(sm + 2 * S_ATILE), 16, 1024);
+      int s = S_NS - 1;
+      uint32_t use = ~0u;
       bool ok = true;
       for (long long ul = 0; ul < my_units && ok; ++ul) {
         int jb, rb, g, nst;
@@ -590,20 +595,20 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
           break;
         }
         fence_after();
-        for (int ks = 0; ks < nst; ++ks, ++it) {
-          const int s = (int)(it % S_NS);
-          const uint32_t use = (uint32_t)(it / S_NS);
+        for (int ks = 0; ks < nst; ++ks) {
+          if (++s == S_NS) { s = 0; }
+          if (s == 0) ++use;
           if (!mbar_wait(smem_u32(&bars.conv[s]), use & 1, &abort_flag)) { ok = false; break; }
           fence_after();
-          const uint32_t bb = smem_u32(sm + s * S_STAGE + 2 * S_ATILE);
+          const uint64_t d0 = desc_off(dsm, (uint32_t)s * S_STAGE);
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             const uint32_t d = tmem + (uint32_t)(t * 64);
             const uint32_t ah = tmem + S_A0 + (uint32_t)((s * 2 + t) * 64);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t dbh = desc_sw128(bb + kk * 32, 16, 1024);
-              const uint64_t dbl = desc_sw128(bb + S_BHALF + kk * 32, 16, 1024);
+              const uint64_t dbh = desc_off(d0, kk * 32);
+              const uint64_t dbl = desc_off(d0, S_BHALF + kk * 32);
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), dbh, ID, (ks | kk) != 0);
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), dbl, ID, 1);
               mma_tf32_ts(d, ah + 32u + (uint32_t)(kk * 8), dbh, ID, 1);

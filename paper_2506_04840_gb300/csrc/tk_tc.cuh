@@ -33,6 +33,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint
   return d;
 }
 
+// The descriptor of the matrix `off` bytes further on (off a multiple of 16,
+// address below 256 KB): the start-address field is the low 14 bits.
+__host__ __device__ constexpr uint64_t desc_off(uint64_t d, uint32_t off) {
+  return d + (uint64_t)(off >> 4);
+}
+
 // Instruction descriptor, kind::f16: bf16 A and B, FP32 accumulator.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
