@@ -295,8 +295,11 @@ __global__ void k_qt_bf16(const double* __restrict__ Q, int n, int l, int n_pad,
 // double-buffered half slab:
 //   GEMM1  D1_r[j, c] = sum_{i in half r} X[i, j] Q[i, c]   (M = 64, N = 64)
 //   the two partials are exchanged through distributed shared memory and
-//   summed (own + peer, the same order in both CTAs: identical W);
+//   summed (own + peer, the same order in both CTAs: identical W), then
+//   rounded to bfloat16 into one of two W buffers;
 //   GEMM2  Y[i, c] += sum_j X[i, j] W[j, c] for the CTA's rows (M = 128).
+// With two W buffers the epilogue prepares W for slab k + 1 while GEMM2 of
+// slab k still reads W for slab k.
 // GEMM1 and GEMM2 are issued from two different warps, so waiting for the
 // next slab's data never delays the current slab's GEMM2.
 // Roles: warp 0 TMA, warp 1 GEMM1 issuer + TMEM owner, warp 2 GEMM2 issuer,
@@ -305,17 +308,13 @@ __global__ void k_qt_bf16(const double* __restrict__ Q, int n, int l, int n_pad,
 constexpr int NC2 = 64;
 constexpr int THREADS2 = 224;
 constexpr int XBUF_BYTES = BJ * NC2 * 4;        // 64 x 64 FP32 partial = 16 KB
-constexpr int W2_BYTES = BJ * 128;              // 64 rows (j) x 64 c bf16 = 8 KB
+constexpr int W2_BYTES = BJ * 128;              // 64 rows (j) x 64 c bf16 = 8 KB per buffer
 constexpr int QT2_CHUNK_BYTES = NC2 * 128;      // 64 rows (c) x 64 i bf16 = 8 KB
 
-// (a, b) -> the bfloat16 pairs hi = (bf16(a), bf16(b)) and lo = the
-// bfloat16 roundings of the remainders, packed two per 32-bit word.
-__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+// (a, b) -> bfloat16 roundings (a in the low half), packed in one word.
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const __nv_bfloat162 l =
-      __floats2bfloat162_rn(__fsub_rn(a, __low2float(h)), __fsub_rn(b, __high2float(h)));
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 struct Params2 {
@@ -334,8 +333,8 @@ struct __align__(8) Bars2 {
   uint64_t qfull;
   uint64_t d1_full[2];
   uint64_t d1_empty[2];
-  uint64_t w_full;
-  uint64_t w_empty;
+  uint64_t w_full[2];
+  uint64_t w_empty[2];
   uint64_t xfull;       // peer's partial has landed in my exchange buffer
   uint64_t peer_free;   // the peer has consumed its exchange buffer
   uint64_t y_done;
@@ -354,9 +353,8 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
   const int ring = 2 * pr.nth;                         // two half-slab buffers
   unsigned char* sQ = sm;                              // nq x 8 KB
   unsigned char* sRing = sQ + nq * QT2_CHUNK_BYTES;    // ring x 16 KB
-  unsigned char* sW = sRing + ring * SUP_BYTES;        // W_hi: 8 KB
-  unsigned char* sWl = sW + W2_BYTES;                  // W_lo: 8 KB
-  float* sX = reinterpret_cast<float*>(sWl + W2_BYTES);  // 16 KB exchange buffer
+  unsigned char* sW = sRing + ring * SUP_BYTES;        // W: 2 x 8 KB
+  float* sX = reinterpret_cast<float*>(sW + 2 * W2_BYTES);  // 16 KB exchange buffer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -377,8 +375,10 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       mbar_init(smem_u32(&bars.d1_full[b]), 1);
       mbar_init(smem_u32(&bars.d1_empty[b]), 4);
     }
-    mbar_init(smem_u32(&bars.w_full), 4);
-    mbar_init(smem_u32(&bars.w_empty), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars.w_full[b]), 4);
+      mbar_init(smem_u32(&bars.w_empty[b]), 1);
+    }
     // xfull: one local arrival per phase carrying the expected 16 KB that the
     // peer's asynchronous stores complete
     mbar_init(smem_u32(&bars.xfull), 1);
@@ -480,25 +480,26 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
     if (lane == 0 && my_slabs > 0) {
       const uint32_t ID2 = idesc_bf16(128, NC2, 1, 1);
       const uint64_t dring = desc_sw128(smem_u32(sRing), SUP_BYTES / 2, 1024);
-      const uint64_t dwh = desc_sw128(smem_u32(sW), 1024, 1024);
-      const uint64_t dwl = desc_sw128(smem_u32(sWl), 1024, 1024);
+      const uint64_t dw = desc_sw128(smem_u32(sW), 1024, 1024);
       bool ok = true;
       for (int k = 0; k < my_slabs && ok; ++k) {
-        if (!mbar_wait(smem_u32(&bars.w_full), k & 1, &abort_flag)) { ok = false; break; }
+        const int b = k & 1;
+        if (!mbar_wait(smem_u32(&bars.w_full[b]), (uint32_t)(k >> 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
         fence_after();
+        const uint64_t dwb = desc_off(dw, (uint32_t)b * W2_BYTES);
         for (int t = 0; t < pr.nth; ++t) {
-          const int slot = (k & 1) * pr.nth + t;
+          const int slot = b * pr.nth + t;
           const uint64_t da0 = desc_off(dring, (uint32_t)slot * SUP_BYTES);
           const uint32_t yt = tmem + (uint32_t)(t * NC2);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            // W = W_hi + W_lo (bfloat16 pair, ~16 bits): Y += X W_hi + X W_lo
-            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwh, kk * 2048), ID2, (k | kk) != 0);
-            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwl, kk * 2048), ID2, 1);
-          }
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(yt, desc_off(da0, kk * 2048), desc_off(dwb, kk * 2048), ID2, (k | kk) != 0);
           mma_commit(smem_u32(&bars.empty[slot]));
         }
-        mma_commit(smem_u32(&bars.w_empty));
+        mma_commit(smem_u32(&bars.w_empty[b]));
       }
       mma_commit(smem_u32(&bars.y_done));
       mma_commit(smem_u32(&bars.drain2));
@@ -544,40 +545,45 @@ k_power_tc2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUt
       }
       // the peer's partial for my rows (its 16 KB completes my xfull phase)
       if (!mbar_wait_cluster(smem_u32(&bars.xfull), k & 1, &abort_flag)) { ok = false; break; }
-      if (!mbar_wait(smem_u32(&bars.w_empty), (k & 1) ^ 1, &abort_flag)) { ok = false; break; }
+      // own partial + peer's, in the same order in both CTAs (identical W)
       if (lane < 16) {
         const float* px = sX + j * NC2;
-        unsigned char* wrow = sW + j * 128;
-        unsigned char* lrow = sWl + j * 128;
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          uint32_t* rr = ch < 4 ? r0 : r1;
-          const int c0 = (ch & 3) * 8;
-          const float4 pa = *reinterpret_cast<const float4*>(px + (((2 * ch) ^ (j & 15)) << 2));
-          const float4 pb =
-              *reinterpret_cast<const float4*>(px + (((2 * ch + 1) ^ (j & 15)) << 2));
-          // own partial + peer's, in the same order in both CTAs (identical W)
-          uint4 ho, lo;
-          split_bf16x2(__uint_as_float(rr[c0]) + pa.x, __uint_as_float(rr[c0 + 1]) + pa.y, ho.x,
-                       lo.x);
-          split_bf16x2(__uint_as_float(rr[c0 + 2]) + pa.z, __uint_as_float(rr[c0 + 3]) + pa.w,
-                       ho.y, lo.y);
-          split_bf16x2(__uint_as_float(rr[c0 + 4]) + pb.x, __uint_as_float(rr[c0 + 5]) + pb.y,
-                       ho.z, lo.z);
-          split_bf16x2(__uint_as_float(rr[c0 + 6]) + pb.z, __uint_as_float(rr[c0 + 7]) + pb.w,
-                       ho.w, lo.w);
-          *reinterpret_cast<uint4*>(wrow + ((ch ^ (j & 7)) << 4)) = ho;
-          *reinterpret_cast<uint4*>(lrow + ((ch ^ (j & 7)) << 4)) = lo;
+        for (int ch = 0; ch < 16; ++ch) {
+          uint32_t* rr = ch < 8 ? r0 : r1;
+          const int c0 = (ch & 7) * 4;
+          const float4 pa = *reinterpret_cast<const float4*>(px + ((ch ^ (j & 15)) << 2));
+          rr[c0] = __float_as_uint(__uint_as_float(rr[c0]) + pa.x);
+          rr[c0 + 1] = __float_as_uint(__uint_as_float(rr[c0 + 1]) + pa.y);
+          rr[c0 + 2] = __float_as_uint(__uint_as_float(rr[c0 + 2]) + pa.z);
+          rr[c0 + 3] = __float_as_uint(__uint_as_float(rr[c0 + 3]) + pa.w);
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(smem_u32(&bars.w_full));
         // re-arm xfull for the next slab before the peer may send it
         if (q == 0 && k + 1 < my_slabs) mbar_expect_tx(smem_u32(&bars.xfull), (uint32_t)XBUF_BYTES);
         mbar_arrive_remote(peer_free);      // my exchange buffer may be refilled
       }
+      // W of this slab into buffer b once GEMM2 of slab k - 2 has read it
+      if (!mbar_wait(smem_u32(&bars.w_empty[b]), (v & 1) ^ 1, &abort_flag)) { ok = false; break; }
+      if (lane < 16) {
+        unsigned char* wrow = sW + b * W2_BYTES + j * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t* rr = ch < 4 ? r0 : r1;
+          const int c0 = (ch & 3) * 8;
+          uint4 w4;
+          w4.x = bf16x2_bits(__uint_as_float(rr[c0]), __uint_as_float(rr[c0 + 1]));
+          w4.y = bf16x2_bits(__uint_as_float(rr[c0 + 2]), __uint_as_float(rr[c0 + 3]));
+          w4.z = bf16x2_bits(__uint_as_float(rr[c0 + 4]), __uint_as_float(rr[c0 + 5]));
+          w4.w = bf16x2_bits(__uint_as_float(rr[c0 + 6]), __uint_as_float(rr[c0 + 7]));
+          *reinterpret_cast<uint4*>(wrow + ((ch ^ (j & 7)) << 4)) = w4;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.w_full[b]));
     }
     // write this CTA's rows of the Y partial
     const bool have = my_slabs > 0 && ok && mbar_wait(smem_u32(&bars.y_done), 0, &abort_flag);
@@ -704,7 +710,7 @@ bool tc2_shape(int64_t n, int l, Tc2Shape* s) {
   if (cols > 512 || s->ring > 12) return false;
   s->tmem_cols = cols;
   s->smem = (size_t)s->nq * tc::QT2_CHUNK_BYTES + (size_t)s->ring * tc::SUP_BYTES +
-            2 * tc::W2_BYTES + tc::XBUF_BYTES + 1024;
+            2 * tc::W2_BYTES + tc::XBUF_BYTES + 1024;   // two W buffers
   return s->smem <= 227 * 1024 - 2048;
 }
 
