@@ -1196,12 +1196,13 @@ k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
 }
 
 // TSQR root (m = Pb l <= 512): QR of the stacked R's, svd of the root R, and
-// Mout = Q_root U_R (m x l, ld m); sigma and the shift update.
+// Mout = Q_root U_R (m x l, ld m); sigma and the shift update.  With
+// basis_only, Mout = Q_root: an orthonormal basis of the same span (no svd).
 // smem: S (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l)
 template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mout,
-           double* __restrict__ sigma, int shift_rule, int update_shift,
+           double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
            double* __restrict__ alpha, double* __restrict__ alpha_hist,
            double* __restrict__ sigl_hist, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1221,9 +1222,17 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
   for (int e = tid; e < l * l; e += blockDim.x) J[e] = 0.f;
   __syncthreads();
   RegCols<CPW> R;
-  R.qr(S, md, l, ts, J, l, 1);   // J = R^T
+  R.qr(S, md, l, ts, basis_only ? nullptr : J, l, 1);   // J = R^T
   for (int e = tid; e < l * l; e += blockDim.x) Vp[e] = (e % l == e / l) ? 1.f : 0.f;
   __syncthreads();
+  if (basis_only) {
+    R.init_top(Vp, l, nullptr, l, l);
+    R.apply_back(S, md, l, ts, l);
+#pragma unroll
+    for (int s = 0; s < CPW; ++s)
+      if (R.col(s) < l) R.store_out(s, Mout, m, m, 1.f);
+    return;
+  }
   jacobi_pairs(J, Vp, l, nrm);
   sigma_perm(J, l, sg, perm, Vp);
   R.init_top(Vp, l, perm, l, l);
@@ -1390,8 +1399,8 @@ static cudaError_t reg_go(const SmallPlan& pl, const double* Y, int64_t n, doubl
   count_kernels(4);
   k_leaf_qr_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
   k_root_reg<CPW><<<1, kRegThreads, reg_one_smem((int64_t)Pb * l, l), st>>>(
-      Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, alpha, alpha_hist, sigl_hist,
-      status);
+      Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
+      alpha_hist, sigl_hist, status);
   k_leaf_q_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
                                                          colidx);
   k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
@@ -1748,19 +1757,50 @@ __global__ void __launch_bounds__(256) k_ritz_apply(float* __restrict__ W, int64
     Zs[e] = c < l ? Z[k + (int64_t)l * c] : 0.f;
   }
   const int64_t ntile = (cols + kRitzRows - 1) / kRitzRows;
+  // mode-major W with l a multiple of 4: a tile is 64 l contiguous floats,
+  // moved as float4, and the next tile is fetched while this one is rotated
+  const bool vec = P == 1 && (l & 3) == 0 && l <= kRegCols;
+  constexpr int NV = kRitzRows * kRegCols / 4 / 256;   // float4 per thread (l <= 64)
+  float4 pre[NV];
+  auto vload = [&](int64_t t0) {
+    const int64_t nel = (min(cols, t0 + kRitzRows) - t0) * l;
+    const float4* src = reinterpret_cast<const float4*>(W + t0 * l);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e4 = tid + q * 256;
+      pre[q] = 4 * (int64_t)e4 < nel ? src[e4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (vec && (int64_t)blockIdx.x < ntile) vload((int64_t)blockIdx.x * kRitzRows);
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t j0 = tile * kRitzRows;
     __syncthreads();
-    if (tid < kRitzRows) {
-      const int64_t j = j0 + tid;
-      offw[tid] = j < cols ? ritz_off(j, P, l) : -1;
-    }
-    __syncthreads();
-    for (int e = tid; e < kRitzRows * l; e += 256) {
-      int r, c;
-      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
-      const int64_t o = offw[r];
-      T[r * TS + c] = o >= 0 ? W[o + P * c] : 0.f;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int e4 = tid + q * 256;
+        if (4 * e4 < kRitzRows * l) {
+          const float v[4] = {pre[q].x, pre[q].y, pre[q].z, pre[q].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int e = 4 * e4 + k, r = e / l;
+            T[r * TS + (e - r * l)] = v[k];
+          }
+        }
+      }
+      if (tile + gridDim.x < ntile) vload((tile + gridDim.x) * kRitzRows);
+    } else {
+      if (tid < kRitzRows) {
+        const int64_t j = j0 + tid;
+        offw[tid] = j < cols ? ritz_off(j, P, l) : -1;
+      }
+      __syncthreads();
+      for (int e = tid; e < kRitzRows * l; e += 256) {
+        int r, c;
+        if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+        const int64_t o = offw[r];
+        T[r * TS + c] = o >= 0 ? W[o + P * c] : 0.f;
+      }
     }
     __syncthreads();
     float a0[CW], a1[CW];
@@ -1793,11 +1833,25 @@ __global__ void __launch_bounds__(256) k_ritz_apply(float* __restrict__ W, int64
       }
     }
     __syncthreads();
-    for (int e = tid; e < kRitzRows * l; e += 256) {
-      int r, c;
-      if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
-      const int64_t o = offw[r];
-      if (o >= 0) W[o + P * c] = T[r * TS + c];
+    if (vec) {
+      const int64_t nel = (min(cols, j0 + kRitzRows) - j0) * l;
+      float4* dst = reinterpret_cast<float4*>(W + j0 * l);
+      for (int e4 = tid; 4 * (int64_t)e4 < nel; e4 += 256) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = 4 * e4 + k, r = e / l;
+          v[k] = T[r * TS + (e - r * l)];
+        }
+        dst[e4] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    } else {
+      for (int e = tid; e < kRitzRows * l; e += 256) {
+        int r, c;
+        if (P == 1) { r = e / l; c = e - r * l; } else { r = e % kRitzRows; c = e / kRitzRows; }
+        const int64_t o = offw[r];
+        if (o >= 0) W[o + P * c] = T[r * TS + c];
+      }
     }
   }
 }

@@ -471,7 +471,9 @@ k_split_b_batch(const Tc32SplitJob* __restrict__ jobs, const uint32_t* __restric
 // Work unit: 256 rows (two M = 128 tiles) x one column group; stage: 32
 // columns (8 TMA boxes of 32 rows x 32 columns, 32 KB) + Omega hi/lo (16 KB),
 // three stages.  TMEM: the unit's accumulators (2 x 64 columns) and per stage
-// the two tiles' X_hi | X_lo (2 x 64 columns): 512.  Roles as k_tc32_xtb.
+// the two tiles' X_hi | X_lo (2 x 64 columns): 512.  Roles: warp 0 TMA, warp 1
+// MMA issue + TMEM, warps 2-5 X converters (and the bfloat16 copy), warps 6-9
+// Omega generation for each stage and, at the end of a unit, its partials.
 // ===========================================================================
 namespace tc {
 
@@ -516,7 +518,7 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
     abort_flag = 0;
     for (int s = 0; s < S_NS; ++s) {
       mbar_init(smem_u32(&bars.full[s]), 1);
-      mbar_init(smem_u32(&bars.conv[s]), 4);
+      mbar_init(smem_u32(&bars.conv[s]), 8);
       mbar_init(smem_u32(&bars.empty[s]), 1);
     }
     mbar_init(smem_u32(&bars.accf[0]), 1);
@@ -625,10 +627,9 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
       }
     }
   } else if (warp < 6) {
-    // ---------------- converters: X -> TMEM (hi | lo), Omega -> shared ----------------
+    // ---------------- converters: X -> TMEM (hi | lo) and the bfloat16 copy ----------------
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const int ctid = (warp - 2) * 32 + lane;     // 0..127
     long long it = 0;
     bool ok = true;
     for (long long ul = 0; ul < my_units && ok; ++ul) {
@@ -636,7 +637,12 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
       long long j0;
       sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
                     &j0, &nst);
+      // the job's fields in registers: the copy's stores below may not be
+      // assumed apart from the job table, which would reload them per store
       const Tc32SketchJob& J = jobs[jb];
+      __nv_bfloat16* const shadow = J.shadow;
+      const int jn = J.n;
+      const uint32_t jcols = (uint32_t)J.cols;
       for (int ks = 0; ks < nst; ++ks, ++it) {
         const int s = (int)(it % S_NS);
         const uint32_t use = (uint32_t)(it / S_NS);
@@ -658,43 +664,21 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
           const uint32_t ta = tmem + lane_off + S_A0 + (uint32_t)((s * 2 + t) * 64);
           tmem_st32(ta, hi);
           tmem_st32(ta + 32u, lo);
-          if (J.shadow != nullptr) {
+          if (shadow != nullptr) {
             // the precision form's bfloat16 copy of X, written as the pass reads X
             const int i = rb * 256 + t * 128 + q * 32 + lane;
             const long long jb0 = j0 + (long long)ks * 32;
-            if (i < J.n) {
+            if (i < jn) {
+              __nv_bfloat16* dst = shadow + jb0 * jn + i;
+              const int jmax = (int)min(32LL, (long long)jcols - jb0);
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                if (jb0 + j < J.cols)
-                  J.shadow[(jb0 + j) * J.n + i] =
+                if (j < jmax)
+                  dst[(long long)j * jn] =
                       __float2bfloat16_rn(__uint_as_float(hi[j]) + __uint_as_float(lo[j]));
             }
           }
         }
-        // Omega rows j0 + 32 ks + jj (layout order), groups of four columns
-        unsigned char* bt = st0 + 2 * S_ATILE;
-        const int jj = ctid & 31;
-        const long long jg = j0 + (long long)ks * 32 + jj;
-        // four independent generator chains per thread, interleaved (one
-        // converter warp per SM sub-partition: latency is hidden by ILP)
-#pragma unroll
-        for (int r4 = 0; r4 < 4; ++r4) {
-          const int gq = (ctid >> 5) + 4 * r4;    // 0..15
-          float w4[4] = {0.f, 0.f, 0.f, 0.f};
-          if (jg < J.cols && 4 * gq < J.l)
-            omega4((uint64_t)(jg / J.ka + J.kb * (jg % J.ka)), gq, J.mode, J.tag, J.seed, w4);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = 4 * gq + e;
-            const float w = c < J.l ? w4[e] : 0.f;
-            const float h = tf32_hi(w);
-            const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 +
-                                            ((((jj * 4) >> 4) ^ (c & 7)) << 4) + ((jj * 4) & 15));
-            *reinterpret_cast<float*>(bt + off) = h;
-            *reinterpret_cast<float*>(bt + S_BHALF + off) = __fsub_rn(w, h);
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tmem_st_wait();
         fence_before();
         __syncwarp();
@@ -702,15 +686,60 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
       }
     }
   } else {
-    // ---------------- epilogue: the unit's partial rows ----------------
+    // ---------------- Omega -> shared for each k-step, then the unit's partial rows ----------------
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    for (long long ul = 0; ul < my_units; ++ul) {
+    const int ctid = (warp - 6) * 32 + lane;     // 0..127
+    long long it = 0;
+    bool ok = true;
+    for (long long ul = 0; ul < my_units && ok; ++ul) {
       int jb, rb, g, nst;
       long long j0;
       sketch_locate(jobs, start, njobs, (long long)blockIdx.x + ul * gridDim.x, &jb, &rb, &g,
                     &j0, &nst);
       const Tc32SketchJob& J = jobs[jb];
+      {
+        const int jl = J.l, jmode = J.mode;
+        const uint32_t jcols = (uint32_t)J.cols, jka = (uint32_t)J.ka, jkb = (uint32_t)J.kb;
+        const uint32_t jtag = J.tag;
+        const uint64_t jseed = J.seed;
+        for (int ks = 0; ks < nst; ++ks, ++it) {
+          const int s = (int)(it % S_NS);
+          const uint32_t use = (uint32_t)(it / S_NS);
+          // stage s is free again (its copy has landed after the MMAs released it)
+          if (!mbar_wait(smem_u32(&bars.full[s]), use & 1, &abort_flag)) { ok = false; break; }
+          unsigned char* st0 = sm + s * S_STAGE;
+          // Omega rows j0 + 32 ks + jj (layout order), groups of four columns
+          unsigned char* bt = st0 + 2 * S_ATILE;
+          const int jj = ctid & 31;
+          // column of the unfolding and its Omega row (columns < 2^31)
+          const uint32_t jg = (uint32_t)(j0 + (long long)ks * 32 + jj);
+          const uint32_t jq = jg / jka;
+          const uint64_t orow = (uint64_t)jq + (uint64_t)jkb * (jg - jq * jka);
+          // four independent generator chains per thread, interleaved (one
+          // such warp per SM sub-partition: latency is hidden by ILP)
+#pragma unroll
+          for (int r4 = 0; r4 < 4; ++r4) {
+            const int gq = (ctid >> 5) + 4 * r4;    // 0..15
+            float w4[4] = {0.f, 0.f, 0.f, 0.f};
+            if (jg < jcols && 4 * gq < jl) omega4(orow, gq, jmode, jtag, jseed, w4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c = 4 * gq + e;
+              const float w = c < jl ? w4[e] : 0.f;
+              const float h = tf32_hi(w);
+              const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 +
+                                              ((((jj * 4) >> 4) ^ (c & 7)) << 4) + ((jj * 4) & 15));
+              *reinterpret_cast<float*>(bt + off) = h;
+              *reinterpret_cast<float*>(bt + S_BHALF + off) = __fsub_rn(w, h);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars.conv[s]));
+        }
+      }
+      if (!ok) break;
       if (!mbar_wait(smem_u32(&bars.accf[0]), (uint32_t)ul & 1, &abort_flag)) break;
       fence_after();
       uint32_t r0[32], r1[32], r2[32], r3[32];

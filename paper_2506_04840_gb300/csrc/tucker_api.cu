@@ -283,10 +283,16 @@ static tk_status factor_mode(const HosvdPlan& p, int k, const void* X, XType xt,
   TK_TRY(cudaMemsetAsync(w.alpha, 0, sizeof(double), st));
   {
     ProfScope ps(TK_K_SMALL_SVD, 2.0 * nl * 8.0, svd_flops, st);
-    // before a power step only span(Y) matters (alpha_0 = 0 needs no Sigma),
-    // so the sketch's svd reduces to an orthonormal basis
+    // before an FP32 (or FP64) power step only span(Y) matters (alpha_0 = 0
+    // needs no Sigma), so the sketch's svd reduces to an orthonormal basis.
+    // Before a bfloat16 power step the singular-vector basis is kept: its
+    // columns are graded by sigma, so rounding Q and W to bfloat16 perturbs
+    // each direction relative to its own size (an arbitrary basis of the span
+    // spreads the large directions' rounding into the small ones: measured at
+    // 1000^3, RE 1.0198e-6 against 1.0163e-6).
+    const bool basis_only = p.q >= 1 && !(p.bf16 && p.q >= 2);
     TK_TRY(launch_small_svd(fp64, p.sp[k], w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false,
-                            w.alpha, nullptr, nullptr, w.status, st, p.q >= 1));
+                            w.alpha, nullptr, nullptr, w.status, st, basis_only));
   }
   if (p.bf16 && p.q >= 2 && !shadow_ready && !fuse_shadow) {
     ProfScope ps(TK_K_CONVERT, N * 6.0, 0.0, st);
