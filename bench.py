@@ -109,10 +109,11 @@ DEFAULT_WORKLOAD = "invradius1000_bf16power_st"
 # it stands (summaries under profiles/); a launch's traffic is taken as this
 # ratio times its algorithmic bytes (traffic grows in proportion with the
 # columns a launch processes).  Absent = not measured for the current code.
-#  * power_fused: k_power_tc2 captured on the 512^3 precision form, mode 1
-#    (268.58 MB read + 3.80 MB written for 268.44 MB of bfloat16 copy).
+#  * power_fused: k_power_tc2 (two W buffers) captured on the 512^3 precision
+#    form, mode 1 (268.54 MB read + 3.79 MB written for 268.44 MB of
+#    bfloat16 copy).
 NCU_TRAFFIC_RATIO = {
-    "power_fused": (268.57984e6 + 3.802112e6) / 268.435456e6,
+    "power_fused": (268.539392e6 + 3.79136e6) / 268.435456e6,
 }
 
 

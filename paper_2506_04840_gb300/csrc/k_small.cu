@@ -910,8 +910,10 @@ struct RegCols {
   }
   // y(:, c) <- H_0 H_1 ... H_{l-1} y(:, c) for the owned columns c < nb
   // (full reflectors and tau of qr() in shared memory, read only)
-  __device__ void apply_back(const float* A, int md, int l, const float* tau, int nb) {
-    for (int j = l - 1; j >= 0; --j) apply(A + (int64_t)md * j, md, tau[j], -1, nb);
+  // (columns lo < c < nb only when lo >= 0)
+  __device__ void apply_back(const float* A, int md, int l, const float* tau, int nb,
+                             int lo = -1) {
+    for (int j = l - 1; j >= 0; --j) apply(A + (int64_t)md * j, md, tau[j], lo, nb);
   }
   // y(:, c) = B(r, c) for r < l (B(r, c) = src[r + ld c'] with c' = perm[c]
   // when perm is given), 0 below
@@ -1251,7 +1253,9 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
 
 // TSQR leaf Q: rows r0.. of Q = Q_leaf [M_b; 0] (M_b = rows b l.. of Mout),
 // written in FP64, with each column's entry of largest magnitude (and its
-// global row) for the sign pass.  smem: B (MB*l reflectors) | tau (l)
+// global row) for the sign pass.  The columns are independent: CTA
+// (b, blockIdx.y) takes columns 16 y .. 16 y + 15, one per warp, so a leaf's
+// columns spread over CPW CTAs.  smem: B (MB*l reflectors) | tau (l)
 template <int CPW>
 __global__ void __launch_bounds__(kRegThreads)
 k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
@@ -1268,12 +1272,13 @@ k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) B[e] = Vb[e];
   for (int j = threadIdx.x; j < l; j += blockDim.x) ts[j] = tau[(int64_t)b * l + j];
   __syncthreads();
+  const int c_lo = 16 * (int)blockIdx.y, c_hi = min(l, c_lo + 16);
   RegCols<CPW> R;
   R.init_top(Mout + (int64_t)b * l, m, nullptr, l, l);
-  R.apply_back(B, MB, l, ts, l);
+  R.apply_back(B, MB, l, ts, c_hi, c_lo - 1);
 #pragma unroll
   for (int s = 0; s < CPW; ++s)
-    if (R.col(s) < l) {
+    if (R.col(s) >= c_lo && R.col(s) < c_hi) {
       int bi = 0;
       const float bv = R.col_extreme(s, rows, &bi);
       R.store_out(s, Q + r0, n, rows, 1.f);
@@ -1401,8 +1406,8 @@ static cudaError_t reg_go(const SmallPlan& pl, const double* Y, int64_t n, doubl
   k_root_reg<CPW><<<1, kRegThreads, reg_one_smem((int64_t)Pb * l, l), st>>>(
       Rst, Pb, l, Mout, sigma, shift_rule, update_shift ? 1 : 0, basis_only ? 1 : 0, alpha,
       alpha_hist, sigl_hist, status);
-  k_leaf_q_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(V, tau, Mout, n, l, MB, Pb, Q, colmax,
-                                                         colidx);
+  k_leaf_q_reg<CPW><<<dim3(Pb, (l + 15) / 16), kRegThreads, leaf_smem, st>>>(
+      V, tau, Mout, n, l, MB, Pb, Q, colmax, colidx);
   k_sign<<<l, 256, 0, st>>>(Q, n, l, Pb, colmax, colidx);
   return cudaGetLastError();
 }
