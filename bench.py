@@ -93,8 +93,9 @@ WORKLOADS.update({
                                   "U[32,160], core ranks U[4,16] (clamped), N(0,1) core, Haar "
                                   "factors, 1e-3 relative noise; randomized ST-HOSVD r = core "
                                   "ranks, p=5, q=2, adaptive shifts, one launch per step kind "
-                                  "(work list) inside one CUDA graph", kind="batch", count=256,
-                             seed=4, s=5, q=2, dtype="f32"),
+                                  "(work list) inside one CUDA graph; split-K counts from the "
+                                  "autotuner", kind="batch", count=256,
+                             seed=4, s=5, q=2, dtype="f32", tune=True),
     "serve_poisson200": dict(desc="serving loop: Poisson arrivals at 200 req/s of FP32 3-way "
                                   "tensors, sides from {64,128,256,512,768} per mode, Hilbert-type "
                                   "or Tucker(+1e-3 noise) content 50/50, ranks U[5,40] (< side), "
@@ -487,6 +488,16 @@ def run_batch_workload(args, w, local, world):
                                    seed=0, tag=i))
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    tune = None
+    if w.get("tune"):
+        # split-K counts from the autotuner (the heuristic is one candidate)
+        api.tucker_tune_clear()
+        best_ms, heur_ms, shift = api.tucker_tune_batch(items, api.TK_SHIFT_PAPER, stream)
+        api.tucker_tune_enable(True)
+        tune = {"tuned_ms_per_run": best_ms, "heuristic_ms_per_run": heur_ms,
+                "split_scale": 2.0 ** (-shift), "classes": api.tucker_tune_entries(),
+                "heuristic_value": w["count"] * 1e3 / heur_ms if heur_ms > 0 else None,
+                "note": "tuner's own timing (3 graph runs per candidate); value is the tuned run"}
     h = api.tucker_batch_create(items, api.TK_SHIFT_PAPER, True)
     launches, dev_bytes = api.tucker_batch_info(h)
     for _ in range(args.warmup):
@@ -611,6 +622,9 @@ def run_batch_workload(args, w, local, world):
                     "overlap": "step k+1's host->device copy overlaps step k's compute "
                                "(two device input sets, two batches)"},
             "clocks": clk, "gpu_launches": launches * args.steps}
+    if tune is not None:
+        line["tune"] = tune
+        api.tucker_tune_enable(False)
     if world == 1 and not args.no_cpu_baseline:
         n, el, sample, re_o = _oracle_sample_batch(w, 15.0)
         line["cpu_baseline"] = {"value": n / el, "unit": "tensors/s", "cores": _cores(),

@@ -320,6 +320,34 @@ tk_status tucker_batch_destroy(tk_batch b);
 /* One-shot: create (no graph), run on `stream`, wait, destroy. */
 tk_status tucker_batch_rsthosvd(const tk_item* items, int count, tk_shift rule, void* stream);
 
+/* Autotuner of the split-K counts (the batching pattern's "tile shapes and
+ * split-K chosen by an autotuner"; the paper has no counterpart).  The FP32
+ * CUDA-core products split their contraction over CTAs: Y = X_(k) W over the
+ * unfolding's columns, the TTM over the rows when it has few column tiles.
+ * With tuning enabled, every call and batch takes these split counts from a
+ * process-wide table keyed by shape class (product kind, n_k, output width,
+ * column count rounded up to a power of two); classes missing from the table
+ * keep the fixed heuristic.  Single calls and batches read the same table,
+ * so a batch item's results stay bitwise equal to its single call.  Change
+ * the table or the switch only between calls (plans made under one setting
+ * size their partial buffers for it). */
+tk_status tucker_tune_enable(int on);          /* default: off */
+tk_status tucker_tune_clear(void);
+tk_status tucker_tune_entries(int* count);
+/* Text file: a header line, then one line per class.  Load merges into the
+ * table; TK_EINVAL on a missing or malformed file (table unchanged). */
+tk_status tucker_tune_save(const char* path);
+tk_status tucker_tune_load(const char* path);
+/* Plans and times the batch of `items` (CUDA graph, 2 warm-up + 3 timed
+ * runs on `stream`) once per candidate: the heuristic split counts scaled
+ * by 2, 1, 1/2, 1/4, 1/8 and 1/16.  Stores the fastest candidate's count for
+ * every shape class the batch uses.  Blocks until done.  Outputs (host,
+ * NULL = skip): the fastest run's ms, the heuristic's ms, the fastest
+ * scale as a shift (-1 = x2, 0 = x1, k = x2^-k).  The items' outputs are
+ * written by the timing runs. */
+tk_status tucker_tune_batch(const tk_item* items, int count, tk_shift rule, void* stream,
+                            double* best_ms, double* base_ms, int* best_shift);
+
 /* Serving loop.  A worker thread admits submitted requests in arrival order
  * while their workspace fits in a reserved device pool and fewer than
  * max_active are in flight, then advances every admitted request by one

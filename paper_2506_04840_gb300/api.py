@@ -131,6 +131,14 @@ SIGNATURES = {
     "tucker_server_drain": (c_int, [c_void_p, c_double]),
     "tucker_server_clock": (c_double, [c_void_p]),
     "tucker_server_destroy": (c_int, [c_void_p]),
+    "tucker_tune_enable": (c_int, [c_int]),
+    "tucker_tune_clear": (c_int, []),
+    "tucker_tune_entries": (c_int, [ctypes.POINTER(c_int)]),
+    "tucker_tune_save": (c_int, [ctypes.c_char_p]),
+    "tucker_tune_load": (c_int, [ctypes.c_char_p]),
+    "tucker_tune_batch": (c_int, [ctypes.POINTER(tk_item), c_int, c_int, c_void_p,
+                                  ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                  ctypes.POINTER(c_int)]),
     "tucker_profile_enable": (c_int, [c_int]),
     "tucker_profile_read": (c_int, [ctypes.POINTER(tk_profile)]),
 }
@@ -382,6 +390,38 @@ def tucker_batch_create(items, rule=TK_SHIFT_PAPER, use_graph=True):
     _check(load().tucker_batch_create(_items(items), len(items), int(rule), 1 if use_graph else 0,
                                       ctypes.byref(h)), "tucker_batch_create")
     return h
+
+
+def tucker_tune_enable(on=True):
+    _check(load().tucker_tune_enable(1 if on else 0), "tucker_tune_enable")
+
+
+def tucker_tune_clear():
+    _check(load().tucker_tune_clear(), "tucker_tune_clear")
+
+
+def tucker_tune_entries():
+    n = c_int()
+    _check(load().tucker_tune_entries(ctypes.byref(n)), "tucker_tune_entries")
+    return int(n.value)
+
+
+def tucker_tune_save(path):
+    _check(load().tucker_tune_save(str(path).encode()), "tucker_tune_save")
+
+
+def tucker_tune_load(path):
+    """Returns the status (TK_EINVAL for a missing or malformed file)."""
+    return load().tucker_tune_load(str(path).encode())
+
+
+def tucker_tune_batch(items, rule=TK_SHIFT_PAPER, stream=None):
+    """Returns (best ms, heuristic ms, best shift)."""
+    b, h, sh = c_double(), c_double(), c_int()
+    _check(load().tucker_tune_batch(_items(items), len(items), int(rule), _stream(stream),
+                                    ctypes.byref(b), ctypes.byref(h), ctypes.byref(sh)),
+           "tucker_tune_batch")
+    return float(b.value), float(h.value), int(sh.value)
 
 
 def tucker_batch_run(h, stream=None):

@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libtucker.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["k_contract.cu", "k_contract32.cu", "k_small.cu", "k_misc.cu", "k_power_tc.cu", "k_tc32.cu", "tucker_api.cu",
-           "tucker_noalloc.cu", "tk_program.cu", "tucker_batch.cu", "tucker_server.cu"]
+           "tucker_noalloc.cu", "tk_program.cu", "tucker_batch.cu", "tucker_server.cu", "tk_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]

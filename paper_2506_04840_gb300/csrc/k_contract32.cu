@@ -660,6 +660,7 @@ Xtb32Shape xtb32_shape(View v, int m, bool allow_split) {
     const int64_t want = (2LL * num_sms() + tiles - 1) / tiles;
     const int64_t maxk = std::max<int64_t>(1, v.n / 64);
     s.ks = (int)std::max<int64_t>(1, std::min(want, maxk));
+    s.ks = tune_splits(TUNE_XTB32, v.n, m, v.cols(), s.ks, (int)maxk);
   }
   int64_t kps = (v.n + s.ks - 1) / s.ks;
   kps = (kps + c32::KS - 1) / c32::KS * c32::KS;
@@ -694,6 +695,8 @@ Xb32Shape xb32_shape(View v, int l, int splits_req) {
     splits = (target + (int64_t)s.gx * s.gy - 1) / ((int64_t)s.gx * s.gy);
     const int64_t maxs = std::max<int64_t>(1, (v.cols() + 4 * c32::KS - 1) / (4 * c32::KS));
     splits = std::max<int64_t>(1, std::min(splits, maxs));
+    splits = tune_splits(TUNE_XB32, v.n, s.lc, v.cols(), (int)splits,
+                         (int)std::min<int64_t>(maxs, 1 << 20));
   }
   int64_t cps = (v.cols() + splits - 1) / splits;
   cps = (cps + c32::KS - 1) / c32::KS * c32::KS;

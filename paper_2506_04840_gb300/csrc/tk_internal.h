@@ -23,6 +23,13 @@ inline size_t xsize(XType t) { return t == X_F64 ? 8 : (t == X_F32 ? 4 : 2); }
 inline size_t asize(XType t) { return t == X_F64 ? 8 : 4; }  // accumulation type
 
 int num_sms();
+// Split-K count of an FP32 CUDA-core product of shape class (kind, n,
+// width, columns): the tuned value when tuning is on and the class is in the
+// table (or a tuning run's candidate), else `heuristic`; clamped to
+// [1, maxs].  kind: TUNE_XB32 (Y = X W splits columns), TUNE_XTB32 (the TTM
+// splits rows).
+enum { TUNE_XB32 = 0, TUNE_XTB32 = 1 };
+int tune_splits(int kind, int64_t n, int width, int64_t cols, int heuristic, int maxs);
 
 // ---- instrumentation (tucker_api.cu) --------------------------------------
 // Counts kernel launches always; when profiling is on, brackets the scope

@@ -46,7 +46,7 @@ def _instances(count, seed, dtype=np.float32):
     return out
 
 
-def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1):
+def _items(insts):
     dt = torch.float64 if insts[0][0].dtype == np.float64 else torch.float32
     keep, items = [], []
     for i, (A, r, s, q) in enumerate(insts):
@@ -54,6 +54,11 @@ def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1):
         core, U, rel = _alloc(A, r, dt)
         keep.append((Ad, core, U, rel))
         items.append(api.make_item(Ad, list(A.shape), r, s, q, core, U, rel, seed=0, tag=i))
+    return keep, items
+
+
+def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1):
+    keep, items = _items(insts)
     h = api.tucker_batch_create(items, rule, use_graph)
     try:
         outs = []
@@ -162,3 +167,27 @@ def test_batch_long_mode_register_svd_bitwise(lib):
     outs, _ = _run_batch(insts, True)
     for i, (A, r, s, q) in enumerate(insts):
         assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+
+
+def test_tuned_split_counts_keep_batch_equal_to_single_calls(lib):
+    """The split-K autotuner: tucker_tune_batch times the batch under each
+    candidate scale of the heuristic split counts and stores the fastest
+    candidate's counts per shape class.  With tuning on, the batch and the
+    single calls read the same table, so every item stays bitwise equal to
+    its single call; the stored choice is never slower than the heuristic
+    in the tuner's own timing."""
+    insts = _instances(14, seed=43)
+    keep, items = _items(insts)
+    api.tucker_tune_clear()
+    try:
+        best, base, shift = api.tucker_tune_batch(items)
+        assert 0.0 < best <= base, (best, base)
+        assert -1 <= shift <= 4
+        assert api.tucker_tune_entries() > 0
+        api.tucker_tune_enable(True)
+        outs, _ = _run_batch(insts, True)
+        for i, (A, r, s, q) in enumerate(insts):
+            assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+    finally:
+        api.tucker_tune_enable(False)
+        api.tucker_tune_clear()
