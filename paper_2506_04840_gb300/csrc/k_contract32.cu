@@ -47,8 +47,10 @@ __device__ __forceinline__ void xtb32_body(const float* __restrict__ X, int64_t 
   constexpr int MJ = 64 * WJ, MC = 16 * WC, T = 32 * WJ * WC;
   constexpr int XPT = KS * MJ / T;          // X elements each thread stages per slab
   constexpr int BPT = (KS * MC + T - 1) / T;
-  // slabs in flight in registers: two where the staging registers allow
-  constexpr int PF = XPT <= 8 ? 2 : 1;
+  // slabs in flight in registers: two where the staging registers allow;
+  // one with the compensated sums, which then fit two CTAs per SM (<= 128
+  // registers: 16 warps per SM instead of 8 to hide the FMA chains' latency)
+  constexpr int PF = XPT <= 8 && !COMP ? 2 : 1;
   __shared__ __align__(16) float Xs[2][KS][MJ + 4];
   __shared__ __align__(16) float Bs[2][KS][MC];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -388,7 +390,7 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
 }
 
 template <int WJ, int WC, typename BT, bool COMP = false>
-__global__ void __launch_bounds__(32 * WJ * WC)
+__global__ void __launch_bounds__(32 * WJ * WC, COMP ? 2 : 1)
 k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const BT* __restrict__ B,
         int64_t b_ri, int64_t b_cm, int m, float* __restrict__ out, int tout, int64_t kps,
         float* __restrict__ part) {
@@ -440,7 +442,7 @@ k_xb32(const float* __restrict__ X, int64_t n, int64_t cols, const float* __rest
 }
 
 template <int WJ, int WC, bool COMP>
-__global__ void __launch_bounds__(32 * WJ * WC)
+__global__ void __launch_bounds__(32 * WJ * WC, COMP ? 2 : 1)
 k_xtb32_batch(const Xtb32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
               uint32_t total) {
   for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
