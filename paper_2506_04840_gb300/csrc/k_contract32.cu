@@ -389,6 +389,163 @@ __device__ __forceinline__ void xb32_body(const float* __restrict__ X, int64_t n
   }
 }
 
+// Y = X_(k) W partials (W given, no bfloat16 copy) with X and W staged by
+// cp.async into a ring of XB_NS shared-memory slabs: the copies of slab
+// s + XB_NS - 1 are in flight while slab s is summed, and no registers hold
+// staged data.  Same slabs, same order and same arithmetic as xb32_body, so
+// the results are bitwise equal.  Needs n and l multiples of 4 (16-byte
+// aligned rows) and dynamic shared memory xb32_cpa_smem(WI, WC).
+constexpr int XB_NS = 3;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+template <int WI, int WC, bool COMP>
+__device__ __forceinline__ void xb32_cpa_body(const float* __restrict__ X, int64_t n,
+                                              int64_t cols, const float* __restrict__ W, int l,
+                                              int lc, int64_t cps, float* __restrict__ part,
+                                              unsigned bx, unsigned by, unsigned bz,
+                                              float* __restrict__ part_lo) {
+  constexpr int MI = 64 * WI, MC = 16 * WC, T = 32 * WI * WC;
+  extern __shared__ __align__(16) float xb_dsm[];
+  float* Xs = xb_dsm;                         // [XB_NS][KS][MI]
+  float* Bs = xb_dsm + XB_NS * KS * MI;       // [XB_NS][KS][MC]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wi = w % WI, wc = w / WI;
+  const int li = lane >> 2, lcn = lane & 3;
+  const int64_t i0 = (int64_t)bx * MI;
+  const int c0 = (int)by * MC;
+  const int64_t jb = (int64_t)bz * cps;
+  const int64_t je = min(cols, jb + cps);
+  const int ia = wi * 64 + li * 4;
+  const int cb = wc * 16 + lcn * 4;
+
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  float cmp[COMP ? 8 : 1][4];
+#pragma unroll
+  for (int a = 0; a < (COMP ? 8 : 1); ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cmp[a][q] = 0.f;
+
+  // slab at columns j0.. into ring slot st; entries past n, l or je are zero
+  auto issue = [&](int st, int64_t j0) {
+    constexpr int XC = KS * MI / 4, BC = KS * MC / 4;
+    float* xs = Xs + st * KS * MI;
+    float* bs = Bs + st * KS * MC;
+#pragma unroll
+    for (int e = tid; e < XC; e += T) {
+      const int jj = e / (MI / 4), q4 = e % (MI / 4);
+      const int64_t j = j0 + jj, i = i0 + 4 * q4;
+      const bool in = j < je && i < n;
+      cp_async16((uint32_t)__cvta_generic_to_shared(xs + jj * MI + 4 * q4),
+                 in ? (const void*)(X + j * n + i) : (const void*)X, in ? 16 : 0);
+    }
+#pragma unroll
+    for (int e = tid; e < BC; e += T) {
+      const int jj = e / (MC / 4), q4 = e % (MC / 4);
+      const int64_t j = j0 + jj;
+      const int c = c0 + 4 * q4;
+      const bool in = j < je && c < l;
+      cp_async16((uint32_t)__cvta_generic_to_shared(bs + jj * MC + 4 * q4),
+                 in ? (const void*)(W + (int64_t)l * j + c) : (const void*)W, in ? 16 : 0);
+    }
+  };
+
+  const int nsl = je > jb ? (int)((je - jb + KS - 1) / KS) : 0;
+#pragma unroll
+  for (int st = 0; st < XB_NS - 1; ++st) {
+    if (st < nsl) issue(st, jb + (int64_t)st * KS);
+    cp_async_commit();
+  }
+  for (int s = 0; s < nsl; ++s) {
+    cp_async_wait<XB_NS - 2>();
+    __syncthreads();     // slab s landed for every thread; slot (s - 1) % XB_NS is free
+    {
+      const int nx = s + XB_NS - 1;
+      if (nx < nsl) issue(nx % XB_NS, jb + (int64_t)nx * KS);
+      cp_async_commit();
+    }
+    const float* xs = Xs + (s % XB_NS) * KS * MI;
+    const float* bs = Bs + (s % XB_NS) * KS * MC;
+    float sl[COMP ? 8 : 1][4];
+    if constexpr (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sl[a][q] = 0.f;
+    }
+#pragma unroll
+    for (int jj = 0; jj < KS; ++jj) {
+      const float4 a0 = *reinterpret_cast<const float4*>(xs + jj * MI + ia);
+      const float4 a1 = *reinterpret_cast<const float4*>(xs + jj * MI + ia + 32);
+      const float4 b = *reinterpret_cast<const float4*>(bs + jj * MC + cb);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (COMP) sl[a][q] = fmaf(av[a], bv[q], sl[a][q]);
+          else acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+        }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float t = __fadd_rn(acc[a][q], sl[a][q]);
+          const float z = __fsub_rn(t, acc[a][q]);
+          const float se = __fadd_rn(__fsub_rn(acc[a][q], __fsub_rn(t, z)),
+                                     __fsub_rn(sl[a][q], z));
+          acc[a][q] = t;
+          cmp[a][q] = __fadd_rn(cmp[a][q], se);
+        }
+    }
+  }
+  cp_async_wait<0>();
+  float* dst = part + (int64_t)bz * n * lc;
+  float* dlo = COMP ? part_lo + (int64_t)bz * n * lc : nullptr;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + ia + (a < 4 ? a : 28 + a);
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + cb + q;
+      if (c >= lc) continue;
+      if constexpr (COMP) {
+        const float hi = __fadd_rn(acc[a][q], cmp[a][q]);
+        dst[i * lc + c] = hi;
+        dlo[i * lc + c] = __fadd_rn(__fsub_rn(acc[a][q], hi), cmp[a][q]);
+      } else {
+        dst[i * lc + c] = acc[a][q];
+      }
+    }
+  }
+}
+
+template <int WI, int WC, bool COMP>
+__global__ void __launch_bounds__(32 * WI * WC)
+k_xb32_cpa(const float* __restrict__ X, int64_t n, int64_t cols, const float* __restrict__ W,
+           int l, int lc, int64_t cps, float* __restrict__ part, float* __restrict__ part_lo) {
+  xb32_cpa_body<WI, WC, COMP>(X, n, cols, W, l, lc, cps, part, blockIdx.x, blockIdx.y,
+                              blockIdx.z, part_lo);
+}
+
 template <int WJ, int WC, typename BT, bool COMP = false>
 __global__ void __launch_bounds__(32 * WJ * WC, COMP ? 2 : 1)
 k_xtb32(const float* __restrict__ X, int64_t n, int64_t cols, const BT* __restrict__ B,
@@ -780,11 +937,38 @@ cudaError_t launch_xtb32(const void* X, View v, const double* B, int64_t b_ri, i
   return cudaGetLastError();
 }
 
+// the cp.async-staged form applies: W given, rows 16-byte aligned
+static bool xb32_cpa_ok(const float* X, View v, const float* W, int l,
+                        const __nv_bfloat16* shadow) {
+  return W != nullptr && shadow == nullptr && (v.n % 4) == 0 && (l % 4) == 0 &&
+         (((uintptr_t)X) & 15) == 0 && (((uintptr_t)W) & 15) == 0;
+}
+
+template <int WI, int WC, bool COMP>
+static void xb32_cpa_go(const float* X, View v, const float* W, int l, float* part,
+                        float* part_lo, const Xb32Shape& s, const dim3& grid, cudaStream_t st) {
+  const size_t smem =
+      (size_t)c32::XB_NS * c32::KS * (64 * WI + 16 * WC) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(c32::k_xb32_cpa<WI, WC, COMP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  c32::k_xb32_cpa<WI, WC, COMP><<<grid, 32 * WI * WC, smem, st>>>(X, v.n, v.cols(), W, l, s.lc,
+                                                                  s.cps, part, part_lo);
+}
+
 template <int WI, int WC>
 static void xb32_go(const float* X, View v, const float* W, int l, uint64_t seed, uint32_t tag,
                     int mode, float* part, int64_t ka, int64_t kb, const Xb32Shape& s,
                     cudaStream_t st, float* part_lo, __nv_bfloat16* shadow) {
   const dim3 grid(s.gx, s.gy, s.splits);
+  if (xb32_cpa_ok(X, v, W, l, shadow)) {
+    if (part_lo != nullptr) xb32_cpa_go<WI, WC, true>(X, v, W, l, part, part_lo, s, grid, st);
+    else xb32_cpa_go<WI, WC, false>(X, v, W, l, part, nullptr, s, grid, st);
+    return;
+  }
   if (W == nullptr && shadow != nullptr)
     c32::k_xb32<WI, WC, true, false, true><<<grid, 32 * WI * WC, 0, st>>>(
         X, v.n, v.cols(), nullptr, l, s.lc, seed, tag, mode, s.cps, ka, kb, part, nullptr,
