@@ -776,6 +776,18 @@ k_err32(const float* __restrict__ Tt, int64_t P, int K, const BT* __restrict__ B
   err32_body<BT>(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
+// The same tiles with the output blocks of one row tile adjacent in launch
+// order (grid x = output blocks, y = row tiles): they share the row tile of
+// T, which then comes from L2 instead of being read from HBM once per
+// output block.  Tiles, sums and partial slots are those of k_err32.
+template <typename BT>
+__global__ void __launch_bounds__(256)
+k_err32_t(const float* __restrict__ Tt, int64_t P, int K, const BT* __restrict__ Bm,
+          int64_t b_ri, int64_t b_cm, int m, const float* __restrict__ A,
+          double* __restrict__ err) {
+  err32_body<BT>(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.y, blockIdx.x, gridDim.y);
+}
+
 __global__ void __launch_bounds__(256)
 k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
               uint32_t total) {
@@ -783,9 +795,10 @@ k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ st
     const int j = batch_job(start, njobs, b);
     const Err32Job J = jobs[j];
     const uint32_t lb = b - __ldg(start + j);
+    // output blocks of one row tile adjacent (they share its rows of T)
+    const uint32_t gy = (uint32_t)((J.m + 63) / 64);
     err32_body<float>((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m, (const float*)J.A,
-                       J.err,
-               lb % (uint32_t)J.gx, lb / (uint32_t)J.gx, (uint32_t)J.gx);
+                       J.err, lb / gy, lb % gy, (uint32_t)J.gx);
   }
 }
 
@@ -1030,8 +1043,19 @@ cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, i
                          int m, const void* A, double* err_part, cudaStream_t st,
                          const float* B32) {
   if (v.P <= 0 || m <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((v.P + 127) / 128), (unsigned)((m + 63) / 64));
+  const unsigned gx = (unsigned)((v.P + 127) / 128), gy = (unsigned)((m + 63) / 64);
   count_kernels(1);
+  if (gx <= 65535u) {
+    // output blocks of a row tile adjacent: T's row tile is read from HBM once
+    if (B32 != nullptr)
+      c32::k_err32_t<float><<<dim3(gy, gx), 256, 0, st>>>(
+          (const float*)T, v.P, (int)v.n, B32, b_ri, b_cm, m, (const float*)A, err_part);
+    else
+      c32::k_err32_t<double><<<dim3(gy, gx), 256, 0, st>>>(
+          (const float*)T, v.P, (int)v.n, B, b_ri, b_cm, m, (const float*)A, err_part);
+    return cudaGetLastError();
+  }
+  const dim3 grid(gx, gy);
   if (B32 != nullptr)
     c32::k_err32<float><<<grid, 256, 0, st>>>((const float*)T, v.P, (int)v.n, B32, b_ri, b_cm, m,
                                               (const float*)A, err_part);
