@@ -713,8 +713,12 @@ __device__ __forceinline__ void err32_body(const float* __restrict__ Tt, int64_t
   for (int s = 0; s < nsl; ++s) {
     const int buf = s & 1;
     if (s + 1 < nsl) load((s + 1) * KS);
+    // rows past K in the last slab are zero: skipping them leaves every sum
+    // unchanged (K = r_d is often far from a multiple of KS)
+    const int rows = min(KS, K - s * KS);
 #pragma unroll
     for (int ii = 0; ii < KS; ++ii) {
+      if (ii >= rows) break;
       const float4 a0 = *reinterpret_cast<const float4*>(&Ts[buf][ii][pa]);
       const float4 a1 = *reinterpret_cast<const float4*>(&Ts[buf][ii][pa + 32]);
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][ii][cb]);
