@@ -641,8 +641,10 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
       // assumed apart from the job table, which would reload them per store
       const Tc32SketchJob& J = jobs[jb];
       __nv_bfloat16* const shadow = J.shadow;
-      const int jn = J.n;
-      const uint32_t jcols = (uint32_t)J.cols;
+      const int jn = J.n, jl = J.l, jmode = J.mode;
+      const uint32_t jcols = (uint32_t)J.cols, jka = (uint32_t)J.ka, jkb = (uint32_t)J.kb;
+      const uint32_t jtag = J.tag;
+      const uint64_t jseed = J.seed;
       for (int ks = 0; ks < nst; ++ks, ++it) {
         const int s = (int)(it % S_NS);
         const uint32_t use = (uint32_t)(it / S_NS);
@@ -679,6 +681,30 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
             }
           }
         }
+        {
+          // the last of Omega's four chains of this stage (groups 12..15;
+          // the Omega warps take 0..11): balances the two kinds of warps
+          unsigned char* bt = st0 + 2 * S_ATILE;
+          const int ctid = (warp - 2) * 32 + lane;
+          const int jj = lane;
+          const uint32_t jg = (uint32_t)(j0 + (long long)ks * 32 + jj);
+          const uint32_t jq = jg / jka;
+          const uint64_t orow = (uint64_t)jq + (uint64_t)jkb * (jg - jq * jka);
+          const int gq = (ctid >> 5) + 12;    // 12..15
+          float w4[4] = {0.f, 0.f, 0.f, 0.f};
+          if (jg < jcols && 4 * gq < jl) omega4(orow, gq, jmode, jtag, jseed, w4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 4 * gq + e;
+            const float w = c < jl ? w4[e] : 0.f;
+            const float h = tf32_hi(w);
+            const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 +
+                                            ((((jj * 4) >> 4) ^ (c & 7)) << 4) + ((jj * 4) & 15));
+            *reinterpret_cast<float*>(bt + off) = h;
+            *reinterpret_cast<float*>(bt + S_BHALF + off) = __fsub_rn(w, h);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tmem_st_wait();
         fence_before();
         __syncwarp();
@@ -719,8 +745,8 @@ __device__ __forceinline__ void sketch_body(const Tc32SketchJob* jobs, const uin
           // four independent generator chains per thread, interleaved (one
           // such warp per SM sub-partition: latency is hidden by ILP)
 #pragma unroll
-          for (int r4 = 0; r4 < 4; ++r4) {
-            const int gq = (ctid >> 5) + 4 * r4;    // 0..15
+          for (int r4 = 0; r4 < 3; ++r4) {
+            const int gq = (ctid >> 5) + 4 * r4;    // 0..11 (12..15: the converters)
             float w4[4] = {0.f, 0.f, 0.f, 0.f};
             if (jg < jcols && 4 * gq < jl) omega4(orow, gq, jmode, jtag, jseed, w4);
 #pragma unroll
