@@ -379,6 +379,10 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st) {
     case BK_SVD:
     case BK_GRAM:
     case BK_POLISH:
+    case BK_TSQR_LEAF:
+    case BK_TSQR_ROOT:
+    case BK_TSQR_LEAFQ:
+    case BK_TSQR_SIGN:
       return launch_batch_small(b, st);
     case BK_XTB32:
     case BK_XB32:

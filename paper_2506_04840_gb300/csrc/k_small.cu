@@ -17,6 +17,7 @@
 // tensors, matching the precision in which Y itself was formed.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "tk_common.cuh"
 #include "tk_batch.h"
@@ -505,13 +506,16 @@ __global__ void k_svd_one(const double* __restrict__ Y, int n, int l, double* __
 // ---------------------------------------------------------------------------
 // Two-level TSQR path.
 // ---------------------------------------------------------------------------
+// Each kernel of the chain is a body taking its block coordinates, called by
+// the single-problem kernel with blockIdx and by the work-list kernel with
+// the job's own block number, so both do the same work per block.
 template <typename T>
-__global__ void k_leaf_qr(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
-                          T* __restrict__ V, T* __restrict__ tau, T* __restrict__ Rst) {
+__device__ __forceinline__ void leaf_qr_body(const double* __restrict__ Y, int64_t n, int l,
+                                             int MB, int Pb, T* __restrict__ V,
+                                             T* __restrict__ tau, T* __restrict__ Rst, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* ts = A + (int64_t)MB * l;
-  const int b = blockIdx.x;
   const int64_t r0 = (int64_t)b * MB;
   const int64_t rows = min((int64_t)MB, n - r0);
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) {
@@ -530,12 +534,21 @@ __global__ void k_leaf_qr(const double* __restrict__ Y, int64_t n, int l, int MB
   for (int j = threadIdx.x; j < l; j += blockDim.x) tau[(int64_t)b * l + j] = ts[j];
 }
 
+template <typename T>
+__global__ void k_leaf_qr(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
+                          T* __restrict__ V, T* __restrict__ tau, T* __restrict__ Rst) {
+  leaf_qr_body<T>(Y, n, l, MB, Pb, V, tau, Rst, blockIdx.x);
+}
+
 // smem: S (m*l) | J (l*l) | Vp (l*l) | sg (l) | tau (l), m = Pb*l
 template <typename T>
-__global__ void k_root(const T* __restrict__ Rst, int Pb, int l, T* __restrict__ Mout,
-                       double* __restrict__ sigma, int shift_rule, int update_shift,
-                       double* __restrict__ alpha, double* __restrict__ alpha_hist,
-                       double* __restrict__ sigl_hist, int* __restrict__ status) {
+__device__ __forceinline__ void root_body(const T* __restrict__ Rst, int Pb, int l,
+                                          T* __restrict__ Mout, double* __restrict__ sigma,
+                                          int shift_rule, int update_shift,
+                                          double* __restrict__ alpha,
+                                          double* __restrict__ alpha_hist,
+                                          double* __restrict__ sigl_hist,
+                                          int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = Pb * l;
   T* S = reinterpret_cast<T*>(smem_raw);
@@ -575,17 +588,26 @@ __global__ void k_root(const T* __restrict__ Rst, int Pb, int l, T* __restrict__
     shift_update((double)sg[perm[l - 1]], shift_rule, alpha, alpha_hist, sigl_hist);
 }
 
+template <typename T>
+__global__ void k_root(const T* __restrict__ Rst, int Pb, int l, T* __restrict__ Mout,
+                       double* __restrict__ sigma, int shift_rule, int update_shift,
+                       double* __restrict__ alpha, double* __restrict__ alpha_hist,
+                       double* __restrict__ sigl_hist, int* __restrict__ status) {
+  root_body<T>(Rst, Pb, l, Mout, sigma, shift_rule, update_shift, alpha, alpha_hist, sigl_hist,
+               status);
+}
+
 // smem: B (MB*l) block reflectors -> block Q | M (l*l) | tau (l)
 template <typename T>
-__global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
-                         const T* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
-                         double* __restrict__ Q, double* __restrict__ colmax,
-                         int* __restrict__ colidx) {
+__device__ __forceinline__ void leaf_q_body(const T* __restrict__ V, const T* __restrict__ tau,
+                                            const T* __restrict__ Mout, int64_t n, int l, int MB,
+                                            int Pb, double* __restrict__ Q,
+                                            double* __restrict__ colmax,
+                                            int* __restrict__ colidx, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* B = reinterpret_cast<T*>(smem_raw);
   T* M = B + (int64_t)MB * l;
   T* ts = M + (int64_t)l * l;
-  const int b = blockIdx.x;
   const int m = Pb * l;
   const int64_t r0 = (int64_t)b * MB;
   const int64_t rows = min((int64_t)MB, n - r0);
@@ -628,10 +650,20 @@ __global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
   }
 }
 
-__global__ void k_sign(double* __restrict__ Q, int64_t n, int l, int Pb,
-                       const double* __restrict__ colmax, const int* __restrict__ colidx) {
+template <typename T>
+__global__ void k_leaf_q(const T* __restrict__ V, const T* __restrict__ tau,
+                         const T* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
+                         double* __restrict__ Q, double* __restrict__ colmax,
+                         int* __restrict__ colidx) {
+  leaf_q_body<T>(V, tau, Mout, n, l, MB, Pb, Q, colmax, colidx, blockIdx.x);
+}
+
+// column c of Q takes the sign that makes its largest entry (over all leaves)
+// positive
+__device__ __forceinline__ void sign_body(double* __restrict__ Q, int64_t n, int l, int Pb,
+                                          const double* __restrict__ colmax,
+                                          const int* __restrict__ colidx, int c) {
   __shared__ double sgn;
-  const int c = blockIdx.x;
   if (threadIdx.x == 0) {
     double best = -1.0;
     int idx = 0;
@@ -644,6 +676,11 @@ __global__ void k_sign(double* __restrict__ Q, int64_t n, int l, int Pb,
   __syncthreads();
   if (sgn < 0.0)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Q[i + n * c] = -Q[i + n * c];
+}
+
+__global__ void k_sign(double* __restrict__ Q, int64_t n, int l, int Pb,
+                       const double* __restrict__ colmax, const int* __restrict__ colidx) {
+  sign_body(Q, n, l, Pb, colmax, colidx, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1169,13 +1206,13 @@ k_svd_reg(const double* __restrict__ Y, int n, int l, double* __restrict__ Q,
 // TSQR leaf (MB <= 512 rows, a multiple of 32): reflectors to V (ld MB), tau,
 // R into the stack Rst (Pb l x l, ld Pb l)
 template <int CPW>
-__global__ void __launch_bounds__(kRegThreads)
-k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
-              float* __restrict__ V, float* __restrict__ tau, float* __restrict__ Rst) {
+__device__ __forceinline__ void leaf_qr_reg_body(const double* __restrict__ Y, int64_t n, int l,
+                                                 int MB, int Pb, float* __restrict__ V,
+                                                 float* __restrict__ tau,
+                                                 float* __restrict__ Rst, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);
   float* ts = A + (int64_t)MB * l;
-  const int b = blockIdx.x;
   const int64_t r0 = (int64_t)b * MB;
   const int64_t rows = min((int64_t)MB, n - r0);
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) {
@@ -1197,16 +1234,26 @@ k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
   for (int j = threadIdx.x; j < l; j += blockDim.x) tau[(int64_t)b * l + j] = ts[j];
 }
 
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_leaf_qr_reg(const double* __restrict__ Y, int64_t n, int l, int MB, int Pb,
+              float* __restrict__ V, float* __restrict__ tau, float* __restrict__ Rst) {
+  leaf_qr_reg_body<CPW>(Y, n, l, MB, Pb, V, tau, Rst, blockIdx.x);
+}
+
 // TSQR root (m = Pb l <= 512): QR of the stacked R's, svd of the root R, and
 // Mout = Q_root U_R (m x l, ld m); sigma and the shift update.  With
 // basis_only, Mout = Q_root: an orthonormal basis of the same span (no svd).
 // smem: S (md*l) | J (l*l) | Vp (l*l) | sg (l) | ts (l) | nrm (l)
 template <int CPW>
-__global__ void __launch_bounds__(kRegThreads)
-k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mout,
-           double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
-           double* __restrict__ alpha, double* __restrict__ alpha_hist,
-           double* __restrict__ sigl_hist, int* __restrict__ status) {
+__device__ __forceinline__ void root_reg_body(const float* __restrict__ Rst, int Pb, int l,
+                                              float* __restrict__ Mout,
+                                              double* __restrict__ sigma, int shift_rule,
+                                              int update_shift, int basis_only,
+                                              double* __restrict__ alpha,
+                                              double* __restrict__ alpha_hist,
+                                              double* __restrict__ sigl_hist,
+                                              int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = Pb * l, md = reg_ld(m);
   float* S = reinterpret_cast<float*>(smem_raw);
@@ -1251,20 +1298,31 @@ k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mou
     shift_update((double)sg[perm[l - 1]], shift_rule, alpha, alpha_hist, sigl_hist);
 }
 
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_root_reg(const float* __restrict__ Rst, int Pb, int l, float* __restrict__ Mout,
+           double* __restrict__ sigma, int shift_rule, int update_shift, int basis_only,
+           double* __restrict__ alpha, double* __restrict__ alpha_hist,
+           double* __restrict__ sigl_hist, int* __restrict__ status) {
+  root_reg_body<CPW>(Rst, Pb, l, Mout, sigma, shift_rule, update_shift, basis_only, alpha,
+                     alpha_hist, sigl_hist, status);
+}
+
 // TSQR leaf Q: rows r0.. of Q = Q_leaf [M_b; 0] (M_b = rows b l.. of Mout),
 // written in FP64, with each column's entry of largest magnitude (and its
 // global row) for the sign pass.  The columns are independent: CTA
 // (b, blockIdx.y) takes columns 16 y .. 16 y + 15, one per warp, so a leaf's
 // columns spread over CPW CTAs.  smem: B (MB*l reflectors) | tau (l)
 template <int CPW>
-__global__ void __launch_bounds__(kRegThreads)
-k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
-             const float* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
-             double* __restrict__ Q, double* __restrict__ colmax, int* __restrict__ colidx) {
+__device__ __forceinline__ void leaf_q_reg_body(const float* __restrict__ V,
+                                                const float* __restrict__ tau,
+                                                const float* __restrict__ Mout, int64_t n, int l,
+                                                int MB, int Pb, double* __restrict__ Q,
+                                                double* __restrict__ colmax,
+                                                int* __restrict__ colidx, int b, int by) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* B = reinterpret_cast<float*>(smem_raw);
   float* ts = B + (int64_t)MB * l;
-  const int b = blockIdx.x;
   const int m = Pb * l;
   const int64_t r0 = (int64_t)b * MB;
   const int rows = (int)min((int64_t)MB, n - r0);
@@ -1272,7 +1330,7 @@ k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
   for (int64_t e = threadIdx.x; e < (int64_t)MB * l; e += blockDim.x) B[e] = Vb[e];
   for (int j = threadIdx.x; j < l; j += blockDim.x) ts[j] = tau[(int64_t)b * l + j];
   __syncthreads();
-  const int c_lo = 16 * (int)blockIdx.y, c_hi = min(l, c_lo + 16);
+  const int c_lo = 16 * by, c_hi = min(l, c_lo + 16);
   RegCols<CPW> R;
   R.init_top(Mout + (int64_t)b * l, m, nullptr, l, l);
   R.apply_back(B, MB, l, ts, c_hi, c_lo - 1);
@@ -1287,6 +1345,14 @@ k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
         colidx[(int64_t)b * l + R.col(s)] = (int)(r0 + bi);
       }
     }
+}
+
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_leaf_q_reg(const float* __restrict__ V, const float* __restrict__ tau,
+             const float* __restrict__ Mout, int64_t n, int l, int MB, int Pb,
+             double* __restrict__ Q, double* __restrict__ colmax, int* __restrict__ colidx) {
+  leaf_q_reg_body<CPW>(V, tau, Mout, n, l, MB, Pb, Q, colmax, colidx, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1369,6 +1435,28 @@ SmallPlan small_plan(int64_t n, int l, bool fp64) {
   return p;
 }
 
+// TSQR scratch of Pb leaves of MB rows (es: bytes per solver entry): leaf
+// reflectors, tau, stacked R's, root result, per-leaf column maxima.
+struct TsqrScratch {
+  void* V;
+  void* tau;
+  void* Rst;
+  void* Mout;
+  double* colmax;
+  int* colidx;
+};
+static TsqrScratch tsqr_carve(void* scratch, int Pb, int MB, int l, size_t es) {
+  TsqrScratch t;
+  unsigned char* w = (unsigned char*)scratch;
+  t.V = w;                    w += align256((size_t)Pb * MB * l * es);
+  t.tau = w;                  w += align256((size_t)Pb * l * es);
+  t.Rst = w;                  w += align256((size_t)Pb * l * l * es);
+  t.Mout = w;                 w += align256((size_t)Pb * l * l * es);
+  t.colmax = (double*)w;      w += align256((size_t)Pb * l * 8);
+  t.colidx = (int*)w;
+  return t;
+}
+
 // Register-resident kernels with CPW columns per warp (16 warps hold l <= 16 CPW
 // columns; CPW = 2 for l <= 32 keeps no idle column slots).
 template <int CPW>
@@ -1393,13 +1481,13 @@ static cudaError_t reg_go(const SmallPlan& pl, const double* Y, int64_t n, doubl
         alpha_hist, sigl_hist, status);
     return cudaGetLastError();
   }
-  unsigned char* w = (unsigned char*)scratch;
-  float* V = (float*)w;        w += align256((size_t)Pb * MB * l * 4);
-  float* tau = (float*)w;      w += align256((size_t)Pb * l * 4);
-  float* Rst = (float*)w;      w += align256((size_t)Pb * l * l * 4);
-  float* Mout = (float*)w;     w += align256((size_t)Pb * l * l * 4);
-  double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
-  int* colidx = (int*)w;
+  const TsqrScratch t = tsqr_carve(scratch, Pb, MB, l, sizeof(float));
+  float* V = (float*)t.V;
+  float* tau = (float*)t.tau;
+  float* Rst = (float*)t.Rst;
+  float* Mout = (float*)t.Mout;
+  double* colmax = t.colmax;
+  int* colidx = t.colidx;
   const size_t leaf_smem = ((size_t)MB * l + l) * sizeof(float);
   count_kernels(4);
   k_leaf_qr_reg<CPW><<<Pb, kRegThreads, leaf_smem, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
@@ -1453,13 +1541,13 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
                                                           alpha_hist, sigl_hist, status);
     return cudaGetLastError();
   }
-  unsigned char* w = (unsigned char*)scratch;
-  T* V = (T*)w;            w += align256((size_t)Pb * MB * l * es);
-  T* tau = (T*)w;          w += align256((size_t)Pb * l * es);
-  T* Rst = (T*)w;          w += align256((size_t)Pb * l * l * es);
-  T* Mout = (T*)w;         w += align256((size_t)Pb * l * l * es);
-  double* colmax = (double*)w; w += align256((size_t)Pb * l * 8);
-  int* colidx = (int*)w;
+  const TsqrScratch t = tsqr_carve(scratch, Pb, MB, l, es);
+  T* V = (T*)t.V;
+  T* tau = (T*)t.tau;
+  T* Rst = (T*)t.Rst;
+  T* Mout = (T*)t.Mout;
+  double* colmax = t.colmax;
+  int* colidx = t.colidx;
   count_kernels(4);
   k_leaf_qr<T><<<Pb, 512, ((size_t)MB * l + l) * es, st>>>(Y, n, l, MB, Pb, V, tau, Rst);
   k_root<T><<<1, 1024, root_smem(Pb, l, es), st>>>(Rst, Pb, l, Mout, sigma, shift_rule,
@@ -1474,9 +1562,12 @@ static cudaError_t small_go(const SmallPlan& pl, const double* Y, int64_t n, dou
 // ---------------------------------------------------------------------------
 // Work-list launches (one CTA per svd job; polish as in launch_polish).
 // ---------------------------------------------------------------------------
+// up to 1024 threads (svd_threads): the bound keeps the FP64 body within the
+// 64 registers a thread such a launch allows
 template <typename T>
-__global__ void k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start,
-                            int njobs, uint32_t total) {
+__global__ void __launch_bounds__(1024)
+k_svd_batch(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
+            uint32_t total) {
   for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
     const SvdJob J = jobs[batch_job(start, njobs, b)];
     svd_one_body<T>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift, J.basis_only,
@@ -1493,6 +1584,91 @@ k_svd_batch_reg(const SvdJob* __restrict__ jobs, const uint32_t* __restrict__ st
     const SvdJob J = jobs[batch_job(start, njobs, b)];
     svd_reg_body<CPW, RK>(J.Y, J.n, J.l, J.Q, J.sigma, J.shift_rule, J.update_shift,
                           J.basis_only, J.alpha, J.ahist, J.shist, J.status);
+    __syncthreads();
+  }
+}
+
+// The TSQR chain over a work list: each job's blocks as the single call's grid
+// (leaf Q, register-resident: block b + Pb y of the job is leaf b, columns
+// 16 y ..).  T = the solver's type.
+template <typename T>
+__global__ void __launch_bounds__(512) k_tsqr_leaf_batch(const TsqrJob* __restrict__ jobs,
+                                  const uint32_t* __restrict__ start, int njobs,
+                                  uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const TsqrJob J = jobs[j];
+    leaf_qr_body<T>(J.Y, J.n, J.l, J.MB, J.Pb, (T*)J.V, (T*)J.tau, (T*)J.Rst,
+                    (int)(b - __ldg(start + j)));
+    __syncthreads();
+  }
+}
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tsqr_root_batch(const TsqrJob* __restrict__ jobs,
+                                  const uint32_t* __restrict__ start, int njobs,
+                                  uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const TsqrJob J = jobs[batch_job(start, njobs, b)];
+    root_body<T>((const T*)J.Rst, J.Pb, J.l, (T*)J.Mout, J.sigma, J.shift_rule, J.update_shift,
+                 J.alpha, J.ahist, J.shist, J.status);
+    __syncthreads();
+  }
+}
+template <typename T>
+__global__ void __launch_bounds__(512) k_tsqr_leafq_batch(const TsqrJob* __restrict__ jobs,
+                                   const uint32_t* __restrict__ start, int njobs,
+                                   uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const TsqrJob J = jobs[j];
+    leaf_q_body<T>((const T*)J.V, (const T*)J.tau, (const T*)J.Mout, J.n, J.l, J.MB, J.Pb, J.Q,
+                   J.colmax, J.colidx, (int)(b - __ldg(start + j)));
+    __syncthreads();
+  }
+}
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_tsqr_leaf_batch_reg(const TsqrJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                      int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const TsqrJob J = jobs[j];
+    leaf_qr_reg_body<CPW>(J.Y, J.n, J.l, J.MB, J.Pb, (float*)J.V, (float*)J.tau, (float*)J.Rst,
+                          (int)(b - __ldg(start + j)));
+    __syncthreads();
+  }
+}
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_tsqr_root_batch_reg(const TsqrJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                      int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const TsqrJob J = jobs[batch_job(start, njobs, b)];
+    root_reg_body<CPW>((const float*)J.Rst, J.Pb, J.l, (float*)J.Mout, J.sigma, J.shift_rule,
+                       J.update_shift, J.basis_only, J.alpha, J.ahist, J.shist, J.status);
+    __syncthreads();
+  }
+}
+template <int CPW>
+__global__ void __launch_bounds__(kRegThreads)
+k_tsqr_leafq_batch_reg(const TsqrJob* __restrict__ jobs, const uint32_t* __restrict__ start,
+                       int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const TsqrJob J = jobs[j];
+    const int lb = (int)(b - __ldg(start + j));
+    leaf_q_reg_body<CPW>((const float*)J.V, (const float*)J.tau, (const float*)J.Mout, J.n, J.l,
+                         J.MB, J.Pb, J.Q, J.colmax, J.colidx, lb % J.Pb, lb / J.Pb);
+    __syncthreads();
+  }
+}
+__global__ void __launch_bounds__(256) k_tsqr_sign_batch(const TsqrJob* __restrict__ jobs,
+                                  const uint32_t* __restrict__ start, int njobs,
+                                  uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const TsqrJob J = jobs[j];
+    sign_body(J.Q, J.n, J.l, J.Pb, J.colmax, J.colidx, (int)(b - __ldg(start + j)));
     __syncthreads();
   }
 }
@@ -1533,6 +1709,48 @@ int svd_threads(int64_t n, int l, bool fp64) {
 size_t svd_smem(int64_t n, int l, bool fp64) {
   return svd_reg_fits(n, l, fp64) ? reg_one_smem(n, l) : one_smem(n, l, fp64 ? 8 : 4);
 }
+int tsqr_job(const SmallPlan& pl, bool fp64, const double* Y, int64_t n, double* Q,
+             double* sigma, void* scratch, int shift_rule, bool update_shift, bool basis_only,
+             double* alpha, double* ahist, double* shist, int* status, TsqrJob* job,
+             TsqrStage stages[4]) {
+  const int l = pl.l, MB = pl.MB, Pb = pl.Pb;
+  // the single call's choice (small_go): register-resident for FP32 plans
+  // marked reg, with 2 columns per warp up to l = 32
+  const int flag = (pl.reg && !fp64) ? (l <= 32 ? 2 : 4) : 0;
+  const size_t es = flag ? sizeof(float) : (fp64 ? sizeof(double) : sizeof(float));
+  const TsqrScratch t = tsqr_carve(scratch, Pb, MB, l, es);
+  TsqrJob& J = *job;
+  std::memset(&J, 0, sizeof(J));
+  J.Y = Y;
+  J.Q = Q;
+  J.sigma = sigma;
+  J.alpha = alpha;
+  J.ahist = ahist;
+  J.shist = shist;
+  J.status = status;
+  J.V = t.V;
+  J.tau = t.tau;
+  J.Rst = t.Rst;
+  J.Mout = t.Mout;
+  J.colmax = t.colmax;
+  J.colidx = t.colidx;
+  J.n = n;
+  J.l = l;
+  J.MB = MB;
+  J.Pb = Pb;
+  J.shift_rule = shift_rule;
+  J.update_shift = update_shift ? 1 : 0;
+  J.basis_only = basis_only ? 1 : 0;
+  const size_t leaf = ((size_t)MB * l + l) * es;
+  stages[0] = TsqrStage{BK_TSQR_LEAF, (uint32_t)Pb, leaf};
+  stages[1] = TsqrStage{BK_TSQR_ROOT, 1u,
+                        flag ? reg_one_smem((int64_t)Pb * l, l) : root_smem(Pb, l, es)};
+  stages[2] = TsqrStage{BK_TSQR_LEAFQ, (uint32_t)(flag ? Pb * ((l + 15) / 16) : Pb),
+                        flag ? leaf : leafq_smem(MB, l, es)};
+  stages[3] = TsqrStage{BK_TSQR_SIGN, (uint32_t)l, 0};
+  return flag;
+}
+
 int polish_blocks(int64_t n) { return (int)((n + kPolishRows - 1) / kPolishRows); }
 size_t gram_smem(int r) { return (size_t)kPolishRows * r * sizeof(double); }
 size_t polish_smem(int r) {
@@ -1553,6 +1771,24 @@ void batch_kernels_init() {
                        mx);
   cudaFuncSetAttribute(k_gram_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_polish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_leaf_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_leaf_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
+  cudaFuncSetAttribute(k_tsqr_root_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_root_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
+  cudaFuncSetAttribute(k_tsqr_leafq_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
+  cudaFuncSetAttribute(k_tsqr_leafq_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
+  cudaFuncSetAttribute(k_tsqr_leaf_batch_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_leaf_batch_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_root_batch_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_root_batch_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_tsqr_leafq_batch_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
+  cudaFuncSetAttribute(k_tsqr_leafq_batch_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       mx);
   attr = true;
 }
 
@@ -1573,6 +1809,25 @@ cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st) {
       return run_batch(k_gram_batch, b, 256, st);
     case BK_POLISH:
       return run_batch(k_polish_batch, b, 256, st);
+    // the TSQR chain with the single call's thread counts (register-resident:
+    // 512 throughout; shared-memory: 512, root 1024, 512; sign 256)
+    case BK_TSQR_LEAF:
+      if (b.flag == 2) return run_batch(k_tsqr_leaf_batch_reg<2>, b, kRegThreads, st);
+      if (b.flag == 4) return run_batch(k_tsqr_leaf_batch_reg<4>, b, kRegThreads, st);
+      if (b.xt == X_F64) return run_batch(k_tsqr_leaf_batch<double>, b, 512, st);
+      return run_batch(k_tsqr_leaf_batch<float>, b, 512, st);
+    case BK_TSQR_ROOT:
+      if (b.flag == 2) return run_batch(k_tsqr_root_batch_reg<2>, b, kRegThreads, st);
+      if (b.flag == 4) return run_batch(k_tsqr_root_batch_reg<4>, b, kRegThreads, st);
+      if (b.xt == X_F64) return run_batch(k_tsqr_root_batch<double>, b, 1024, st);
+      return run_batch(k_tsqr_root_batch<float>, b, 1024, st);
+    case BK_TSQR_LEAFQ:
+      if (b.flag == 2) return run_batch(k_tsqr_leafq_batch_reg<2>, b, kRegThreads, st);
+      if (b.flag == 4) return run_batch(k_tsqr_leafq_batch_reg<4>, b, kRegThreads, st);
+      if (b.xt == X_F64) return run_batch(k_tsqr_leafq_batch<double>, b, 512, st);
+      return run_batch(k_tsqr_leafq_batch<float>, b, 512, st);
+    case BK_TSQR_SIGN:
+      return run_batch(k_tsqr_sign_batch, b, 256, st);
     default:
       return cudaErrorInvalidValue;
   }

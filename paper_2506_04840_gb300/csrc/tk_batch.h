@@ -53,6 +53,29 @@ struct SvdJob {
   int n, l, shift_rule, update_shift, basis_only;
 };
 
+// svd of an n x l iterate too long for one CTA: the two-level TSQR chain of
+// the single call (leaf QR, root QR + svd + shift update, leaf Q, sign), one
+// job per problem in each of four launches, on the single call's scratch
+// carve.  Blocks: leaf QR Pb; root 1; leaf Q Pb (register-resident: Pb x
+// ceil(l / 16)); sign l.
+struct TsqrJob {
+  const double* Y;
+  double* Q;
+  double* sigma;
+  double* alpha;
+  double* ahist;
+  double* shist;
+  int* status;
+  void* V;              // leaf reflectors (solver type: FP32 or FP64)
+  void* tau;
+  void* Rst;            // stacked leaf R's
+  void* Mout;           // root result
+  double* colmax;       // per leaf and column: largest |entry| and its row
+  int* colidx;
+  int64_t n;
+  int l, MB, Pb, shift_rule, update_shift, basis_only;
+};
+
 // out = X x_k B^T (EPI 0) or the fused error expansion (EPI 1), grid gx x gy.
 struct XtbJob {
   const void* X;
@@ -176,7 +199,8 @@ struct Tc32SplitJob {
 
 enum BatchKind {
   BK_XB = 0, BK_REDUCE, BK_SVD, BK_XTB, BK_GRAM, BK_POLISH, BK_COPY, BK_ERRFIN, BK_XTB32,
-  BK_XB32, BK_XTB32RED, BK_ERR32, BK_TC32SPLIT, BK_TC32XTB, BK_TC32SKETCH
+  BK_XB32, BK_XTB32RED, BK_ERR32, BK_TC32SPLIT, BK_TC32XTB, BK_TC32SKETCH,
+  BK_TSQR_LEAF, BK_TSQR_ROOT, BK_TSQR_LEAFQ, BK_TSQR_SIGN
 };
 
 constexpr size_t kJobBytes = 384;   // every job struct fits (two tensor maps + sizes)
@@ -186,7 +210,9 @@ struct BatchLaunch {
   int xt;             // XType of the data (copy: of the destination)
   int tile;           // xb / xtb: column tile LC; svd: threads per CTA
   int flag;           // xb: 1 = Omega; xtb: EPI; copy: 1 = round through FP32;
-                      // xb32 / xtb32: (Omega) | (warps along rows) << 1
+                      // xb32 / xtb32: (Omega) | (warps along rows) << 1;
+                      // tsqr: 2 or 4 = register-resident kernels with that
+                      // many columns per warp, 0 = shared-memory kernels
   const void* jobs;   // device array of njobs job structs
   const uint32_t* start;   // device: first block of each job
   int njobs;
@@ -241,6 +267,18 @@ int svd_threads(int64_t n, int l, bool fp64);
 // 0: shared-memory svd; 2 or 4: register-resident svd with that many columns per warp
 int svd_variant(int64_t n, int l, bool fp64);
 size_t svd_smem(int64_t n, int l, bool fp64);
+// The TSQR chain of one svd (plan with Pb > 1) as a job and its four stages
+// (kind, blocks, dynamic shared memory), in launch order; returns the flag
+// of its launches.
+struct TsqrStage {
+  int kind;
+  uint32_t blocks;
+  size_t smem;
+};
+int tsqr_job(const SmallPlan& pl, bool fp64, const double* Y, int64_t n, double* Q,
+             double* sigma, void* scratch, int shift_rule, bool update_shift, bool basis_only,
+             double* alpha, double* ahist, double* shist, int* status, TsqrJob* job,
+             TsqrStage stages[4]);
 int polish_blocks(int64_t n);
 size_t gram_smem(int r);
 size_t polish_smem(int r);

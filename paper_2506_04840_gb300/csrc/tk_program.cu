@@ -45,6 +45,10 @@ size_t job_size(int kind) {
     case BK_TC32SPLIT: return sizeof(Tc32SplitJob);
     case BK_TC32XTB: return sizeof(Tc32XtbJob);
     case BK_TC32SKETCH: return sizeof(Tc32SketchJob);
+    case BK_TSQR_LEAF:
+    case BK_TSQR_ROOT:
+    case BK_TSQR_LEAFQ:
+    case BK_TSQR_SIGN: return sizeof(TsqrJob);
     default: return sizeof(ErrFinalJob);
   }
 }
@@ -115,6 +119,34 @@ Op xb_op(int pos, int prof, XType xt, const void* X, View v, const void* W, int 
                  flops, j);
 }
 
+// [Q, Sigma] = svd(Y) (+ shift update) as launch_small_svd runs it, at
+// positions pos.. of the phase: one CTA (one op), or the TSQR chain (four ops
+// at pos .. pos + 3 on the svd scratch).
+void svd_ops(Phase& ph, int pos, const SmallPlan& pl, XType xt, const double* Y, int64_t n,
+             double* Q, double* sigma, void* scratch, int rule, bool update_shift,
+             bool basis_only, double* alpha, double* ahist, double* shist, int* status) {
+  const bool fp64 = xt == X_F64;
+  const int l = pl.l;
+  const double nl = (double)n * l;
+  const double flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
+  if (pl.Pb == 1) {
+    SvdJob sv{Y, Q, sigma, alpha, ahist, shist, status, (int)n, l, rule,
+              update_shift ? 1 : 0, basis_only ? 1 : 0};
+    ph.push_back(make_op(pos, TK_K_SMALL_SVD, BK_SVD, xt, svd_threads(n, l, fp64),
+                         svd_variant(n, l, fp64), svd_smem(n, l, fp64), 1, 2.0 * nl * 8.0,
+                         flops, sv));
+    return;
+  }
+  TsqrJob tj;
+  TsqrStage stg[4];
+  const int flag = tsqr_job(pl, fp64, Y, n, Q, sigma, scratch, rule, update_shift, basis_only,
+                            alpha, ahist, shist, status, &tj, stg);
+  for (int i = 0; i < 4; ++i)
+    ph.push_back(make_op(pos + i, TK_K_SMALL_SVD, stg[i].kind, xt, 0, flag, stg[i].smem,
+                         stg[i].blocks, i == 0 ? 2.0 * nl * 8.0 : 0.0, i == 0 ? flops : 0.0,
+                         tj));
+}
+
 // Extra per-problem buffers beyond the single-call workspace.
 struct Extras {
   size_t state, qd[TK_MAX_D], tb[2], ep;
@@ -167,8 +199,6 @@ tk_status problem_plan(const tk_item& it, tk_shift rule, Problem* pr) {
   o.order[0] = -1;
   tk_status s = make_plan(&it.A, it.r, &o, true, pr->p);
   if (s != TK_OK) return s;
-  for (int k = 0; k < pr->p.d; ++k)
-    if (pr->p.sp[k].Pb != 1) return TK_ENOTIMPL;   // one-CTA svd only
   Extras ex;
   pr->ws_bytes = layout(it, pr->p, &ex);
   return TK_OK;
@@ -208,13 +238,9 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
     const double N = (double)v.P * (double)v.n * (double)v.S;
     const double nl = (double)v.n * l;
     const double red_bytes = (double)splits * v.n * lc * asize(xt) + nl * 8.0;
-    const double svd_flops = 4.0 * nl * l + 2.0 * (double)l * l * l;
     const XType acc = fp64 ? X_F64 : X_F32;
     double* sig = stt->sig + (size_t)k * TK_MAX_L;
     double* alpha = stt->alpha + k;
-    const int sthreads = svd_threads(v.n, l, fp64);
-    const int svar = svd_variant(v.n, l, fp64);
-    const size_t ssmem = svd_smem(v.n, l, fp64);
 
     // ---- sketch phase
     {
@@ -235,10 +261,8 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       ReduceJob rd{w.part, v.n, nullptr, nullptr, w.Y, sp, l, slc, nullptr};
       ph.push_back(make_op(1, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
-      SvdJob sv{w.Y, w.Q, sig, alpha, nullptr, nullptr, w.status, (int)v.n, l, (int)p.rule,
-                0, p.q >= 1 ? 1 : 0};
-      ph.push_back(make_op(2, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, svar, ssmem, 1,
-                           2.0 * nl * 8.0, svd_flops, sv));
+      svd_ops(ph, 2, p.sp[k], acc, w.Y, v.n, w.Q, sig, w.small, (int)p.rule, false, p.q >= 1,
+              alpha, nullptr, nullptr, w.status);
       prog.push_back(ph);
       pr->slot.push_back(step * per_step);
     }
@@ -266,11 +290,9 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       ReduceJob rd{w.part, v.n, w.Q, alpha, w.Y, splits, l, lc, plo};
       ph.push_back(make_op(4, TK_K_CONVERT, BK_REDUCE, acc, 0, 0, 0, cdiv(v.n * l, 32),
                            red_bytes, (double)splits * nl, rd));
-      SvdJob sv{w.Y, w.Q, sig, alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
-                stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status, (int)v.n, l,
-                (int)p.rule, 1, 0};
-      ph.push_back(make_op(5, TK_K_SMALL_SVD, BK_SVD, acc, sthreads, svar, ssmem, 1,
-                           2.0 * nl * 8.0, svd_flops, sv));
+      svd_ops(ph, 5, p.sp[k], acc, w.Y, v.n, w.Q, sig, w.small, (int)p.rule, true, false,
+              alpha, stt->ahist + (size_t)k * TK_MAX_Q + (t - 1),
+              stt->shist + (size_t)k * TK_MAX_Q + (t - 1), w.status);
       prog.push_back(ph);
       pr->slot.push_back(step * per_step + t);
     }

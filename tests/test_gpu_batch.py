@@ -169,6 +169,44 @@ def test_batch_long_mode_register_svd_bitwise(lib):
         assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
 
 
+def _tucker_items(cases, seed0, dtype, s, q):
+    insts = []
+    for i, (shape, r) in enumerate(cases):
+        core_r = [min(rk + 4, n - 1) for rk, n in zip(r, shape)]
+        A = I.tucker_plus_noise(list(shape), core_r, seed0 + i, noise=1e-3,
+                                noise_mode="relative", dtype=dtype)
+        insts.append((A, r, s, q))
+    return insts
+
+
+def test_batch_tsqr_svd_bitwise(lib):
+    """Items whose first mode is too long for a one-CTA svd: the batch runs
+    the two-level TSQR chain (leaf QR, root QR + svd + shift update, leaf Q,
+    sign) as four work-list launches, bitwise as the single calls.  Cases:
+    register-resident leaves with 4 columns per warp (n = 1000, l = 60, two
+    leaves) and 2 (n = 2000, l = 30, four leaves), and the shared-memory
+    chain of an FP32 mode with l = 70 > 64; a one-CTA item shares the
+    launches."""
+    cases = [((1000, 60, 48), [50, 10, 8]), ((2000, 40, 30), [20, 8, 6]),
+             ((600, 80, 72), [60, 10, 8]), ((40, 30, 20), [6, 5, 4])]
+    insts = _tucker_items(cases, 80, np.float32, 10, 2)
+    outs, _ = _run_batch(insts, True)
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i)), i
+
+
+def test_batch_fp64_tsqr_and_wide_one_cta_svd_bitwise(lib):
+    """FP64 items: a 1000-row first mode takes the shared-memory TSQR chain,
+    and a 300-row mode with l = 18 the one-CTA svd at 1024 threads (n l >=
+    4096); q = 0 runs the sketch's svd only, q = 1 the power step's."""
+    cases = [((1000, 300, 8), [20, 8, 4]), ((1000, 40, 30), [20, 8, 6])]
+    for q in (0, 1):
+        insts = _tucker_items(cases, 90, np.float64, 10, q)
+        outs, _ = _run_batch(insts, True)
+        for i, (A, r, s, qq) in enumerate(insts):
+            assert _same(outs[0][i], _single(A, r, s, qq, tag=i)), (q, i)
+
+
 def test_tuned_split_counts_keep_batch_equal_to_single_calls(lib):
     """The split-K autotuner: tucker_tune_batch times the batch under each
     candidate scale of the heuristic split counts and stores the fastest
