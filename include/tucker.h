@@ -279,8 +279,8 @@ tk_status tucker_error(const tk_tensor* A, const void* core, const int* r, const
 
 /* ---- many independent problems: batched launches and a serving loop ------
  * The paper treats one tensor at a time; these entry points run Algorithm 3
- * (shifted randomized ST-HOSVD, modes in natural order, plain precision) on
- * many tensors at once.  Each step kind runs as ONE launch over a work list
+ * (shifted randomized ST-HOSVD, modes in natural or descending order, plain
+ * precision) on many tensors at once.  Each step kind runs as ONE launch over a work list
  * holding every problem's blocks of that step (a persistent grid strides over
  * them), so uneven shapes share the GPU.  A problem's blocks do exactly the
  * work the single-problem call does, in the same order: its results are
@@ -297,6 +297,9 @@ typedef struct {
   void* U[TK_MAX_D];       /* out: U[k] n_k x r_k, A's dtype (device) */
   double* rel_err;         /* out: RE of (core, U) as tucker_error computes
                               it (one FP64, device), or NULL = not computed */
+  int order;               /* processing order: 0 = natural (modes 1..d),
+                              TK_ORDER_DESCENDING = non-increasing n_k
+                              (Section 3.2); other values: TK_EINVAL */
 } tk_item;
 
 typedef struct tk_batch_s* tk_batch;

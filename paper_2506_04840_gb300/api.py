@@ -60,7 +60,7 @@ class tk_profile(ctypes.Structure):
 class tk_item(ctypes.Structure):
     _fields_ = [("A", tk_tensor), ("r", c_int * TK_MAX_D), ("s", c_int * TK_MAX_D), ("q", c_int),
                 ("seed", c_uint64), ("tag", c_uint32), ("core", c_void_p),
-                ("U", c_void_p * TK_MAX_D), ("rel_err", c_void_p)]
+                ("U", c_void_p * TK_MAX_D), ("rel_err", c_void_p), ("order", c_int)]
 
 
 class tk_server_opts(ctypes.Structure):
@@ -360,8 +360,9 @@ def tucker_to_bf16(x, out, stream=None):
            "tucker_to_bf16")
 
 
-def make_item(A, dims, r, s, q, core, U, rel_err=None, seed=0, tag=0):
-    """tk_item for one problem of a batch or one serving request."""
+def make_item(A, dims, r, s, q, core, U, rel_err=None, seed=0, tag=0, order=None):
+    """tk_item for one problem of a batch or one serving request (order:
+    None = natural, "descending" = Section 3.2's order)."""
     it = tk_item()
     it.A = tensor_desc(A, dims)
     d = len(dims)
@@ -375,6 +376,12 @@ def make_item(A, dims, r, s, q, core, U, rel_err=None, seed=0, tag=0):
     it.tag = int(tag)
     it.core = int(core.data_ptr())
     it.rel_err = None if rel_err is None else int(rel_err.data_ptr())
+    if order is None:
+        it.order = 0
+    elif order == "descending":
+        it.order = TK_ORDER_DESCENDING
+    else:
+        raise ValueError(order)
     return it
 
 

@@ -196,7 +196,8 @@ tk_status problem_plan(const tk_item& it, tk_shift rule, Problem* pr) {
   o.tag = it.tag;
   o.shift = rule;
   o.prec = TK_PREC_PLAIN;
-  o.order[0] = -1;
+  if (it.order != 0 && it.order != TK_ORDER_DESCENDING) return TK_EINVAL;
+  o.order[0] = it.order == TK_ORDER_DESCENDING ? TK_ORDER_DESCENDING : -1;
   tk_status s = make_plan(&it.A, it.r, &o, true, pr->p);
   if (s != TK_OK) return s;
   Extras ex;

@@ -60,8 +60,8 @@ struct Problem {
   ItemState* state = nullptr;   // device, inside the workspace
 };
 
-// Validates `it` (ST-HOSVD in natural mode order, plain precision) and sizes
-// its workspace.  Returns TK_OK and fills pr->p and pr->ws_bytes.
+// Validates `it` (ST-HOSVD in natural or descending mode order, plain
+// precision) and sizes its workspace.  Returns TK_OK and fills pr->p and pr->ws_bytes.
 tk_status problem_plan(const tk_item& it, tk_shift rule, Problem* pr);
 // Lays the problem out at `base` (pr->ws_bytes bytes, 256-aligned) and builds
 // its program; pr->state points at its ItemState.

@@ -40,9 +40,9 @@ def test_ctypes_structs_match_header():
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tk_tensor), sizeof(tk_opts), sizeof(tk_stats),
          offsetof(tk_opts, seed), offsetof(tk_opts, workspace), offsetof(tk_stats, sigma));
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tk_item), offsetof(tk_item, q),
-         offsetof(tk_item, core), offsetof(tk_item, rel_err), sizeof(tk_server_opts),
-         sizeof(tk_completion), offsetof(tk_completion, done_s));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tk_item), offsetof(tk_item, q),
+         offsetof(tk_item, core), offsetof(tk_item, rel_err), offsetof(tk_item, order),
+         sizeof(tk_server_opts), sizeof(tk_completion), offsetof(tk_completion, done_s));
   return 0;
 }
 """
@@ -55,7 +55,8 @@ int main(void) {
     want = [ctypes.sizeof(api.tk_tensor), ctypes.sizeof(api.tk_opts), ctypes.sizeof(api.tk_stats),
             api.tk_opts.seed.offset, api.tk_opts.workspace.offset, api.tk_stats.sigma.offset,
             ctypes.sizeof(api.tk_item), api.tk_item.q.offset, api.tk_item.core.offset,
-            api.tk_item.rel_err.offset, ctypes.sizeof(api.tk_server_opts),
+            api.tk_item.rel_err.offset, api.tk_item.order.offset,
+            ctypes.sizeof(api.tk_server_opts),
             ctypes.sizeof(api.tk_completion), api.tk_completion.done_s.offset]
     assert [int(x) for x in out] == want
 
@@ -187,7 +188,8 @@ def test_workspace_size_is_host_only_and_monotone():
 
 def test_batch_validation_before_allocation():
     """A batch with an invalid item is rejected on the host (nothing is
-    allocated or launched): rank >= size, mixed dtypes, bad shift rule."""
+    allocated or launched): rank >= size, mixed dtypes, bad shift rule, an
+    unknown processing order."""
     lib = api.load()
 
     def item(dims, r, dtype=api.TK_F32):
@@ -205,7 +207,10 @@ def test_batch_validation_before_allocation():
     good = item([10, 9, 8], [3, 3, 3])
     bad_rank = item([10, 9, 8], [3, 9, 3])
     other = item([10, 9, 8], [3, 3, 3], api.TK_F64)
-    for items, rule in (([good, bad_rank], 0), ([good, other], 0), ([good], 7)):
+    bad_order = item([10, 9, 8], [3, 3, 3])
+    bad_order.order = 1
+    for items, rule in (([good, bad_rank], 0), ([good, other], 0), ([good], 7),
+                        ([good, bad_order], 0)):
         arr = (api.tk_item * len(items))(*items)
         assert lib.tucker_batch_create(arr, len(items), rule, 0, ctypes.byref(h)) == api.TK_EINVAL
         assert not h.value

@@ -27,11 +27,11 @@ def _alloc(A, r, dtype):
     return core, U, rel
 
 
-def _single(A, r, s, q, tag, rule=api.TK_SHIFT_PAPER):
+def _single(A, r, s, q, tag, rule=api.TK_SHIFT_PAPER, order=None):
     dt = torch.float64 if A.dtype == np.float64 else torch.float32
     Ad = api.to_device(A)
     core, U, rel = _alloc(A, r, dt)
-    opts = api.make_opts(A.ndim, q, s, seed=0, tag=tag, shift=rule)
+    opts = api.make_opts(A.ndim, q, s, seed=0, tag=tag, shift=rule, order=order)
     api.tucker_rsthosvd(Ad, list(A.shape), r, opts, core, U)
     api.tucker_error(Ad, list(A.shape), core, r, U, rel)
     torch.cuda.synchronize()
@@ -46,19 +46,20 @@ def _instances(count, seed, dtype=np.float32):
     return out
 
 
-def _items(insts):
+def _items(insts, order=None):
     dt = torch.float64 if insts[0][0].dtype == np.float64 else torch.float32
     keep, items = [], []
     for i, (A, r, s, q) in enumerate(insts):
         Ad = api.to_device(A)
         core, U, rel = _alloc(A, r, dt)
         keep.append((Ad, core, U, rel))
-        items.append(api.make_item(Ad, list(A.shape), r, s, q, core, U, rel, seed=0, tag=i))
+        items.append(api.make_item(Ad, list(A.shape), r, s, q, core, U, rel, seed=0, tag=i,
+                                   order=order))
     return keep, items
 
 
-def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1):
-    keep, items = _items(insts)
+def _run_batch(insts, use_graph, rule=api.TK_SHIFT_PAPER, runs=1, order=None):
+    keep, items = _items(insts, order)
     h = api.tucker_batch_create(items, rule, use_graph)
     try:
         outs = []
@@ -205,6 +206,20 @@ def test_batch_fp64_tsqr_and_wide_one_cta_svd_bitwise(lib):
         outs, _ = _run_batch(insts, True)
         for i, (A, r, s, qq) in enumerate(insts):
             assert _same(outs[0][i], _single(A, r, s, qq, tag=i)), (q, i)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batch_descending_order_bitwise(lib, dtype):
+    """Section 3.2's processing order (modes by non-increasing n_k) in a
+    batch: unsorted shapes take strided views of the middle modes (no
+    rotated layout), sorted ones keep the natural order; every item bitwise
+    as the single call with the same order."""
+    cases = [((30, 60, 45), [5, 7, 6]), ((20, 16, 36, 24), [4, 5, 6, 4]),
+             ((50, 40, 30), [6, 5, 4]), ((24, 70, 18), [5, 8, 4])]
+    insts = _tucker_items(cases, 100, dtype, 5, 2)
+    outs, _ = _run_batch(insts, True, order="descending")
+    for i, (A, r, s, q) in enumerate(insts):
+        assert _same(outs[0][i], _single(A, r, s, q, tag=i, order="descending")), i
 
 
 def test_tuned_split_counts_keep_batch_equal_to_single_calls(lib):
