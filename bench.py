@@ -881,7 +881,7 @@ def main():
     # to NB - 1 steps ahead of the compute, so a copy that is slow now and
     # then (the host side of the link is shared) does not stall the steps;
     # every step's copy and result read-back lie inside the timed region
-    NB = 3
+    NB = 4
     Ae = [torch.empty_like(Ad) for _ in range(NB)]
     cstream = torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(NB)]
@@ -963,8 +963,8 @@ def main():
             "latency": _latency(prof, args.steps, ms / args.steps), "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "tensors/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
-                    "overlap": "host->device copies run up to two steps ahead of the "
-                               "compute (three device input buffers)"},
+                    "overlap": "host->device copies run up to three steps ahead of the "
+                               "compute (four device input buffers)"},
             "clocks": clk, "gpu_launches": launches}
     if plain is not None:
         line["plain_form"] = plain
