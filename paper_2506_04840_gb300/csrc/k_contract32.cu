@@ -792,6 +792,153 @@ k_err32_t(const float* __restrict__ Tt, int64_t P, int K, const BT* __restrict__
   err32_body<BT>(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.y, blockIdx.x, gridDim.y);
 }
 
+// The same residual sums with one CTA per row tile and ERR_CT consecutive
+// output tiles (K <= ERR_KMAX): T's row tile (K x 128) and B's rows for the
+// CTA's 256 outputs are staged in shared memory once, and each output tile's
+// A block is loaded into registers while the previous tile is summed.  Every
+// residual entry and every per-thread FP32 sum of squares is formed exactly
+// as in err32_body (same terms, same order); only the FP64 sums over the
+// output tiles are grouped per CTA.  Block lb of the launch is row tile
+// lb / groups, output group lb % groups (groups = ceil(m / (64 ERR_CT))).
+// Dynamic shared memory: err32c_smem(K).
+constexpr int ERR_CT = 4;
+constexpr int ERR_KMAX = 64;
+
+template <typename BT>
+__device__ __forceinline__ void err32c_body(const float* __restrict__ Tt, int64_t P, int K,
+                                            const BT* __restrict__ Bm, int64_t b_ri,
+                                            int64_t b_cm, int m, const float* __restrict__ A,
+                                            double* __restrict__ err, uint32_t lb) {
+  constexpr int MP = 128, MC = 64, T = 256, TS = MP + 4, BW = ERR_CT * MC;
+  extern __shared__ __align__(16) float err_dsm[];
+  float* Ts = err_dsm;                // [K][TS]
+  float* Bs = err_dsm + K * TS;       // [K][BW]
+  __shared__ double red[2][8];
+  const int groups = (m + BW - 1) / BW;
+  const int64_t ptile = lb / (uint32_t)groups;
+  const int g = (int)(lb % (uint32_t)groups);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wp = w & 1, wc = w >> 1;
+  const int lp = lane >> 2, lcn = lane & 3;
+  const int64_t p0 = ptile * MP;
+  const int cg0 = g * BW;
+  const int pa = wp * 64 + lp * 4;
+  const int cb = wc * 16 + lcn * 4;
+
+  // A block of output tile ct, as err32_body's accumulator starts
+  float an[8][4];
+  auto load_a = [&](int ct) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t p = p0 + pa + (a < 4 ? a : 28 + a);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = cg0 + ct * MC + cb + q;
+        an[a][q] = (p < P && c < m) ? __ldg(A + p + P * c) : 0.f;
+      }
+    }
+  };
+  load_a(0);
+  for (int e = tid; e < K * MP; e += T) {
+    const int i = e / MP, pp = e % MP;
+    const int64_t p = p0 + pp;
+    Ts[i * TS + pp] = p < P ? __ldg(Tt + p + P * i) : 0.f;
+  }
+  for (int e = tid; e < K * BW; e += T) {
+    const int i = e / BW, cc = e % BW;
+    const int c = cg0 + cc;
+    Bs[i * BW + cc] = c < m ? (float)Bm[(int64_t)i * b_ri + (int64_t)c * b_cm] : 0.f;
+  }
+  __syncthreads();
+  double e2 = 0.0, a2 = 0.0;
+  for (int ct = 0; ct < ERR_CT; ++ct) {
+    const int cbase = cg0 + ct * MC;
+    if (cbase >= m) break;             // uniform over the CTA
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][q] = an[a][q];
+    if (ct + 1 < ERR_CT && cbase + MC < m) load_a(ct + 1);
+    // squares of a over the tile, in the order of err32_body's second read
+    float a2t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (cbase + cb + q >= m) continue;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (p0 + pa + (a < 4 ? a : 28 + a) >= P) continue;
+        a2t = fmaf(acc[a][q], acc[a][q], a2t);
+      }
+    }
+    // the running residual a - sum_{i<t} T(p,i) B(i,c), terms in ascending i
+    const float* bcol = Bs + ct * MC + cb;
+#pragma unroll 4
+    for (int i = 0; i < K; ++i) {
+      const float4 a0 = *reinterpret_cast<const float4*>(Ts + i * TS + pa);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ts + i * TS + pa + 32);
+      const float4 b = *reinterpret_cast<const float4*>(bcol + i * BW);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {-b.x, -b.y, -b.z, -b.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(av[a], bv[q], acc[a][q]);
+    }
+    float e2t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (cbase + cb + q >= m) continue;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (p0 + pa + (a < 4 ? a : 28 + a) >= P) continue;
+        e2t = fmaf(acc[a][q], acc[a][q], e2t);
+      }
+    }
+    e2 += (double)e2t;
+    a2 += (double)a2t;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    red[0][w] = e2;
+    red[1][w] = a2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double se = 0.0, sa = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      se += red[0][k];
+      sa += red[1][k];
+    }
+    err[2 * (int64_t)lb] = se;
+    err[2 * (int64_t)lb + 1] = sa;
+  }
+  __syncthreads();
+}
+
+template <typename BT>
+__global__ void __launch_bounds__(256, 2)
+k_err32c(const float* __restrict__ Tt, int64_t P, int K, const BT* __restrict__ Bm,
+         int64_t b_ri, int64_t b_cm, int m, const float* __restrict__ A,
+         double* __restrict__ err) {
+  err32c_body<BT>(Tt, P, K, Bm, b_ri, b_cm, m, A, err, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_err32c_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ start,
+               int njobs, uint32_t total) {
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int j = batch_job(start, njobs, b);
+    const Err32Job J = jobs[j];
+    err32c_body<float>((const float*)J.T, J.P, J.K, J.B, J.b_ri, J.b_cm, J.m,
+                       (const float*)J.A, J.err, b - __ldg(start + j));
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k_err32_batch(const Err32Job* __restrict__ jobs, const uint32_t* __restrict__ start, int njobs,
               uint32_t total) {
@@ -1039,14 +1186,50 @@ cudaError_t launch_xb32(const void* X, View v, const void* W, int l, uint64_t se
 
 bool err32_ok(XType xt, View v) { return xt == X_F32 && v.S == 1 && v.P >= 1; }
 
+// the row-tile form (err32c) for K = n_k <= ERR_KMAX
+bool err32c_ok(View v) { return v.n >= 1 && v.n <= c32::ERR_KMAX; }
+size_t err32c_smem(int K) {
+  return (size_t)K * ((128 + 4) + c32::ERR_CT * 64) * sizeof(float);
+}
+
 int err32_blocks(View v, int m) {
+  if (err32c_ok(v))
+    return (int)(((v.P + 127) / 128) * ((m + 64 * c32::ERR_CT - 1) / (64 * c32::ERR_CT)));
   return (int)(((v.P + 127) / 128) * ((m + 63) / 64));
+}
+
+void c32_batch_init() {
+  static bool attr = false;
+  if (attr) return;
+  cudaFuncSetAttribute(c32::k_err32c_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)err32c_smem(c32::ERR_KMAX));
+  attr = true;
 }
 
 cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, const void* A, double* err_part, cudaStream_t st,
                          const float* B32) {
   if (v.P <= 0 || m <= 0) return cudaSuccess;
+  if (err32c_ok(v)) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(c32::k_err32c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)err32c_smem(c32::ERR_KMAX));
+      cudaFuncSetAttribute(c32::k_err32c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)err32c_smem(c32::ERR_KMAX));
+      attr = true;
+    }
+    const unsigned nb = (unsigned)err32_blocks(v, m);
+    const size_t smem = err32c_smem((int)v.n);
+    count_kernels(1);
+    if (B32 != nullptr)
+      c32::k_err32c<float><<<nb, 256, smem, st>>>((const float*)T, v.P, (int)v.n, B32, b_ri,
+                                                  b_cm, m, (const float*)A, err_part);
+    else
+      c32::k_err32c<double><<<nb, 256, smem, st>>>((const float*)T, v.P, (int)v.n, B, b_ri,
+                                                   b_cm, m, (const float*)A, err_part);
+    return cudaGetLastError();
+  }
   const unsigned gx = (unsigned)((v.P + 127) / 128), gy = (unsigned)((m + 63) / 64);
   count_kernels(1);
   if (gx <= 65535u) {
@@ -1075,7 +1258,11 @@ cudaError_t launch_batch_c32(const BatchLaunch& b, cudaStream_t st) {
   const int wc = b.tile, wx = (b.flag >> 1) & 7, omega = b.flag & 1;
   const bool comp_y = (b.flag >> 4) & 1;
   if (b.kind == BK_XTB32RED) return run_batch(c32::k_xtb32_red_batch, b, 256, st);
-  if (b.kind == BK_ERR32) return run_batch(c32::k_err32_batch, b, 256, st);
+  if (b.kind == BK_ERR32) {
+    // flag 1: the row-tile form (err32c_ok), dynamic shared memory in smem
+    if (b.flag == 1) return run_batch(c32::k_err32c_batch, b, 256, st);
+    return run_batch(c32::k_err32_batch, b, 256, st);
+  }
   if (b.kind == BK_XTB32) {
     const bool comp = (b.flag & 1) != 0;
     if (wc == 1)

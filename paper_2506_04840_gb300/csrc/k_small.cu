@@ -1762,6 +1762,7 @@ size_t polish_smem(int r) {
 void batch_kernels_init() {
   static bool attr = false;
   if (attr) return;
+  c32_batch_init();
   const int mx = (int)kSmemBudget + 4096;
   cudaFuncSetAttribute(k_svd_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_svd_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

@@ -222,6 +222,7 @@ struct BatchLaunch {
 
 cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t st);
 void batch_kernels_init();
+void c32_batch_init();   // part of batch_kernels_init (k_contract32.cu)
 // per-file dispatchers
 cudaError_t launch_batch_contract(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_small(const BatchLaunch& b, cudaStream_t st);

@@ -83,6 +83,10 @@ size_t xtb32_b32_offset(View v, int m);
 // err32_blocks(v, m) (e^2, a^2) pairs.
 bool err32_ok(XType xt, View v);
 int err32_blocks(View v, int m);
+// the row-tile error pass applies (K = v.n small enough) and its dynamic
+// shared memory
+bool err32c_ok(View v);
+size_t err32c_smem(int K);
 cudaError_t launch_err32(const void* T, View v, const double* B, int64_t b_ri, int64_t b_cm,
                          int m, const void* A, double* err_part, cudaStream_t st,
                          const float* B32 = nullptr);

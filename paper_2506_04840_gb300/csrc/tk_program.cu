@@ -357,8 +357,11 @@ tk_status problem_build(const tk_item& it, unsigned char* base, Problem* pr) {
       const int gx = (int)cdiv(vl.P, 128);
       Err32Job ej{Xe, vl.P, (const float*)it.U[d - 1], p.n[d - 1], 1, it.A.data, ep, (int)vl.n,
                   m, gx};
-      ph.push_back(make_op(d - 1, TK_K_ERROR, BK_ERR32, xt, 0, 0, 0,
-                           (uint32_t)gx * cdiv(m, 64), Nf * es + (double)vl.P * vl.n * es,
+      // the same kernel body and blocks as the single call (err32_blocks)
+      const bool rowtile = err32c_ok(vl);
+      ph.push_back(make_op(d - 1, TK_K_ERROR, BK_ERR32, xt, 0, rowtile ? 1 : 0,
+                           rowtile ? err32c_smem((int)vl.n) : 0,
+                           (uint32_t)err32_blocks(vl, m), Nf * es + (double)vl.P * vl.n * es,
                            2.0 * Nf * vl.n, ej));
     } else {
       XtbJob ej{Xe, vl.P, vl.n, vl.S, qd[d - 1], p.n[d - 1], 1, nullptr, it.A.data, ep, m, egx};
