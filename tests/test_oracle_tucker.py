@@ -178,6 +178,75 @@ def test_randomized_matches_dense_algorithm_1_with_many_powers():
         assert abs(T.rel_error(A, G, Us) - T.rel_error(A, Gd, Ud)) < 1e-10
 
 
+def test_matrix_case_reaches_eckart_young():
+    """d = 2: with r_1 = r_2 = r, Algorithms 2 and 3 return a rank-r
+    approximation U_1 U_1^T A U_2 U_2^T of a matrix; with many power steps
+    its error reaches the truncated SVD's, sqrt(sum_{i>r} s_i^2) / ||A||
+    (Eckart-Young), and U_1, U_2 span A's leading singular subspaces."""
+    rng = np.random.default_rng(31)
+    Ua, _ = np.linalg.qr(rng.standard_normal((60, 40)))
+    Va, _ = np.linalg.qr(rng.standard_normal((45, 40)))
+    sv = 0.8 ** np.arange(40)
+    A = (Ua * sv) @ Va.T
+    r = 7
+    opt = float(np.sqrt(np.sum(sv[r:] ** 2) / np.sum(sv ** 2)))
+    for f in (T.rthosvd, T.rsthosvd):
+        G, Us, _ = f(A, [r, r], 3, 40)
+        assert abs(T.rel_error(A, G, Us) - opt) < 1e-10 * opt
+        assert T.principal_sines(Us[0], Ua[:, :r]).max() < 1e-8
+        assert T.principal_sines(Us[1], Va[:, :r]).max() < 1e-8
+
+
+def test_largest_order_recovers_exact_low_rank():
+    """d = 8 (the library's largest order): a tensor of exact multilinear
+    rank 2 in every mode is recovered to rounding by both algorithms."""
+    shape = [4, 3, 4, 3, 3, 4, 3, 3]
+    A = I.tucker_plus_noise(shape, [2] * 8, seed=32, noise=0.0, dtype=np.float64)
+    for f in (T.rthosvd, T.rsthosvd):
+        G, Us, st = f(A, [2] * 8, 1, 1)
+        assert [x["l"] for x in st] == [3] * 8
+        assert T.rel_error(A, G, Us) < 1e-13
+
+
+def test_rank_one_without_oversampling_is_the_power_method():
+    """l = 1 (r = 1, s = 0): each mode's iteration is the power method on
+    A_(k) A_(k)^T - alpha I with one vector.  Unshifted (Algorithm A.1), U_1
+    converges to A_(1)'s leading left singular vector.  With the paper's
+    rule, Sigma(1, 1) estimates sigma_1^2 - alpha, so alpha climbs toward
+    sigma_1^2 / 2, the edge of condition (a) of Section 3.1, and stays below
+    it.  A rank-one tensor is recovered exactly."""
+    A = I.tucker_plus_noise([20, 15, 12], [3, 3, 3], seed=33, noise=0.0, decay=0.5,
+                            dtype=np.float64)
+    sig = np.linalg.svd(T.unfold(A, 0), compute_uv=False)
+    u1 = np.linalg.svd(T.unfold(A, 0), full_matrices=False)[0][:, :1]
+    G, Us, st = T.rsthosvd(A, [1, 1, 1], 0, 60, rule=T.SHIFT_NONE)
+    assert [x["l"] for x in st] == [1, 1, 1]
+    assert T.principal_sines(Us[0], u1).max() < 1e-10
+    G, Us, st = T.rsthosvd(A, [1, 1, 1], 0, 60)
+    a = [0.0] + st[0]["alpha"]
+    assert all(a[t] <= a[t + 1] for t in range(60))
+    assert sig[0] ** 2 / 2 * (1 - 1e-3) < a[-1] <= sig[0] ** 2 / 2 * (1 + 1e-12)
+    rng = np.random.default_rng(34)
+    a, b, c = rng.standard_normal(20), rng.standard_normal(15), rng.standard_normal(12)
+    R1 = np.einsum("i,j,k->ijk", a, b, c)
+    for f in (T.rthosvd, T.rsthosvd):
+        G, Us, _ = f(R1, [1, 1, 1], 0, 2)
+        assert T.rel_error(R1, G, Us) < 1e-13
+
+
+def test_shift_invariants_hold_over_the_largest_power_count():
+    """q = 32: the shift sequence stays nondecreasing and below
+    sigma_l(A_(k) A_(k)^T) / 2 over all steps (Section 3.1, condition (a))."""
+    A = I.tucker_plus_noise([24, 20, 16], [6, 5, 4], seed=35, noise=0.05, dtype=np.float64)
+    G, Us, st = T.rthosvd(A, [5, 4, 3], 4, 32)
+    for k in range(3):
+        sig = np.linalg.svd(T.unfold(A, k), compute_uv=False)
+        a = [0.0] + st[k]["alpha"]
+        assert len(a) == 33
+        assert all(a[t] <= a[t + 1] for t in range(32))
+        assert a[-1] <= sig[st[k]["l"] - 1] ** 2 / 2 * (1 + 1e-12)
+
+
 def _closed_form(v, r):
     return float(np.sqrt(np.sum(v[r:] ** 2) / np.sum(v ** 2)))
 
