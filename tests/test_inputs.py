@@ -45,13 +45,16 @@ def test_inverse_radius_entries_and_noise_level():
     assert np.array_equal(S, W[:, :, :7])
 
 
-def test_haar_factors_are_orthonormal_with_positive_r_diagonal():
+def test_haar_factors_are_orthonormal_and_sign_normalised():
     rng = np.random.default_rng(0)
     U = I.haar(rng, 50, 7)
     assert np.abs(U.T @ U - np.eye(7)).max() < 1e-13
-    # the signs of diag(R) were moved into Q: QR of U gives R = I
-    _, R = np.linalg.qr(U)
-    assert np.allclose(np.abs(np.diag(R)), 1.0, atol=1e-12)
+    # U = Q diag(sign(diag R)) for the QR of the same Gaussian draw
+    Z = np.random.default_rng(0).standard_normal((50, 7))
+    Q, R = np.linalg.qr(Z)
+    assert np.allclose(U, Q * np.sign(np.diag(R)), rtol=0, atol=1e-14)
+    assert np.allclose(U.T @ Z, np.triu(U.T @ Z), atol=1e-12)      # U^T Z = |R|-signed R
+    assert np.all(np.diag(U.T @ Z) > 0)
 
 
 def test_tucker_plus_noise_ranks_and_noise_modes():
